@@ -1,0 +1,221 @@
+/* gsct.h -- C ABI of the GB300 (sm_103a) Gaussian-splatting CT hot path.
+ *
+ * Implements the two passes every optimisation step of FaCT-GS (arXiv 2604.01844) runs over a
+ * set of 3D anisotropic Gaussians, forward and backward:
+ *   - the X-ray rasterizer: cone- or parallel-beam projection of each Gaussian to a 2D
+ *     detector footprint (Sec. 3.2, Eq. 3 and Eq. 4), culled to its 3-sigma ellipse and binned
+ *     into (view, tile) keys with axis-aligned bounding boxes (Sec. 3.5), radix-sorted on the
+ *     device and summed additively per tile (no depth order, Sec. 3.5);
+ *   - the voxelizer: the same Gaussians sampled on a regular grid (Sec. 3.3, Eq. 2), binned
+ *     into bricks.
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument named d_* is a DEVICE pointer owned by the caller; h_* and plain
+ *     struct pointers are HOST pointers read during the call only.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  They launch kernels only: no allocation, no host<->device copy, no
+ *     synchronisation, unless the entry point says otherwise.
+ *   - Scratch memory is a caller-provided workspace `d_ws` of `ws_bytes` bytes, sized by the
+ *     matching *_workspace_size function.  Its first 256 bytes hold a device status block
+ *     (gs_status) that gs_read_status() copies back.
+ *   - Return value: GS_OK, or a negative GS_ERR_* for errors found on the host before any
+ *     launch (bad arguments, workspace too small, launch failure).  Errors found on the
+ *     device (pair capacity exceeded) are recorded in the status block; the kernels that
+ *     follow the failing step do no work and the outputs are left undefined until the call
+ *     is repeated with a larger workspace.
+ *
+ * Gaussian parameter arrays (Sec. 5: 11 values per Gaussian), each float4[n], 16-byte aligned:
+ *   d_mean_rho = (x, y, z, rho)    centre p_i and density rho_i of Eq. 1
+ *   d_scale    = (sx, sy, sz, -)   per-axis standard deviations (> 0), already activated
+ *   d_quat     = (w, x, y, z)      rotation; any non-zero length, normalised inside (the
+ *                                  gradient flows through the normalisation); a zero
+ *                                  quaternion culls the Gaussian
+ *   Sigma_i = R(q/|q|) diag(s^2) R(q/|q|)^T.
+ *
+ * Image layout: float [view][row][col].  Volume layout: float [z][y][x] (x fastest).
+ */
+#ifndef GSCT_H
+#define GSCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_OK 0
+#define GS_ERR_ARG (-1)      /* invalid argument (null pointer, bad size, misalignment) */
+#define GS_ERR_CAPACITY (-2) /* workspace or pair capacity too small */
+#define GS_ERR_CUDA (-3)     /* a CUDA runtime call failed */
+
+#define GS_CONE 0
+#define GS_PARALLEL 1
+
+/* Geometry of one view (Sec. 3.2: parallel beam or cone beam with a pinhole model).
+ * Pixel (col i, row j) centre = det_center + (i + 1/2 - W/2) u + (j + 1/2 - H/2) v.
+ * Cone: rays leave `src`; the detector plane is perpendicular to det_center - src, and u, v
+ * must be perpendicular to it and to each other.  Parallel: rays run along u x v; `src` is
+ * ignored.  64 bytes. */
+typedef struct gs_view {
+  float src[3];        /* cone: X-ray source position (world units) */
+  float det_center[3]; /* centre of the flat detector */
+  float u[3];          /* detector column axis; its length is the pixel pitch along a row */
+  float v[3];          /* detector row axis; its length is the pixel pitch along a column */
+  int32_t mode;        /* GS_CONE or GS_PARALLEL */
+  int32_t pad[3];
+} gs_view;
+
+/* Regular voxel grid: voxel (ix, iy, iz) centre = origin + (idx + 1/2) * voxel.  36 bytes. */
+typedef struct gs_grid {
+  int32_t dims[3];   /* nx, ny, nz */
+  float origin[3];
+  float voxel[3];
+} gs_grid;
+
+/* Options of both passes.  cut: truncation radius in standard deviations; the paper's
+ * "3 lambda_max" rule (Sec. 3.2) is read as the 3-sigma ellipse/ellipsoid q < cut^2.
+ * eps: factored-in density (Sec. 3.5): the cut shrinks to min(cut^2, 2 ln(|A|/eps)) and a pair
+ * whose amplitude |A| <= eps is culled; 0 disables it.  znear: cone-beam pairs whose depth
+ * along the central ray is <= znear are culled.  tile: raster tile side (8, 16 or 32).
+ * brick: voxel brick side (16). */
+typedef struct gs_opts {
+  float cut;
+  float eps;
+  float znear;
+  int32_t tile;
+  int32_t brick;
+  int32_t pad[3];
+} gs_opts;
+
+/* Device status block at the start of every workspace. */
+typedef struct gs_status {
+  int32_t code;         /* GS_OK or GS_ERR_CAPACITY */
+  int32_t pad;
+  int64_t pairs;        /* number of (key, Gaussian) pairs the last binning produced */
+  int64_t capacity;     /* pair capacity of the workspace */
+  int64_t evals;        /* in-cut evaluations counted by the last counting call */
+  int64_t reserved[28];
+} gs_status;
+
+/* ---------------------------------------------------------------------------------------
+ * Library information
+ * ------------------------------------------------------------------------------------- */
+
+/* Version string and the compute capability the library was built for (e.g. 103). */
+const char* gs_version(void);
+int gs_build_arch(void);
+
+/* Copy the status block of workspace d_ws to *h_out.  Synchronises `stream` first.
+ * Returns GS_OK, GS_ERR_ARG (null pointer) or GS_ERR_CUDA. */
+int gs_read_status(const void* d_ws, void* stream, gs_status* h_out);
+
+/* Last CUDA error string recorded by a failing call of this library (thread-local). */
+const char* gs_last_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * X-ray rasterizer (Sec. 3.2, 3.5; Eq. 3, Eq. 4)
+ * ------------------------------------------------------------------------------------- */
+
+/* Bytes of workspace for projecting n Gaussians to n_views views of W x H pixels with room
+ * for max_pairs (view, tile) pairs, including what gs_project_backward needs.  Returns 0 for
+ * invalid sizes. */
+size_t gs_project_workspace_size(int n, int n_views, int W, int H, const gs_opts* opts,
+                                 int64_t max_pairs);
+
+/* Number of (view, tile) pairs the current parameters produce, computed on the device and
+ * copied back (SYNCHRONOUS: waits for `stream`).  d_ws needs gs_project_workspace_size(...,
+ * max_pairs = 0) bytes at least.  Writes the count to *h_pairs. */
+int gs_project_count_pairs(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                           int n, const gs_view* d_views, int n_views, int W, int H,
+                           const gs_opts* opts, void* d_ws, size_t ws_bytes, void* stream,
+                           int64_t* h_pairs);
+
+/* Forward projection, Eq. 4: d_img[v][row][col] = sum over Gaussians i with q < Q of
+ * A_iv exp(-q/2), A_iv = rho_i mu_iv, q the pixel offset's quadratic form in the conic of the
+ * projected covariance.  Overwrites d_img (n_views*H*W floats).  The workspace keeps the
+ * sorted (view, tile) lists so that gs_project_backward(reuse = 1) can skip rebuilding them. */
+int gs_project(const float* d_mean_rho, const float* d_scale, const float* d_quat, int n,
+               const gs_view* d_views, int n_views, int W, int H, const gs_opts* opts,
+               float* d_img, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Backward of gs_project: given dL/dimg (d_dimg, n_views*H*W), writes dL/d(mean_rho, scale,
+ * quat) (float4[n] each; the 4th component of scale's gradient is 0).  accumulate = 1 adds to
+ * the gradient arrays instead of overwriting them.  reuse = 1: the workspace still holds the
+ * lists of a gs_project call with the same parameters and geometry; reuse = 0 rebuilds them
+ * (recompute, no stored lists needed).  The truncation mask is held constant (its boundary is
+ * not differentiated).  Per-Gaussian backward (Sec. 3.5): one warp per (Gaussian, tile) pair,
+ * reduced with warp shuffles before one set of atomics per pair. */
+int gs_project_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                        int n, const gs_view* d_views, int n_views, int W, int H,
+                        const gs_opts* opts, const float* d_dimg, float* d_g_mean_rho,
+                        float* d_g_scale, float* d_g_quat, int accumulate, int reuse,
+                        void* d_ws, size_t ws_bytes, void* stream);
+
+/* Counts the (pixel, Gaussian) evaluations inside the cut of the current parameters (the
+ * algorithmic work of one forward) into the status block's `evals` field; uses and rebuilds
+ * the workspace lists like gs_project.  Asynchronous; read it with gs_read_status. */
+int gs_project_count_evals(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                           int n, const gs_view* d_views, int n_views, int W, int H,
+                           const gs_opts* opts, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Voxelizer (Sec. 3.3, Eq. 2)
+ * ------------------------------------------------------------------------------------- */
+
+/* Bytes of workspace for voxelizing n Gaussians into the region of interest roi_lo ..
+ * roi_lo + roi_dim - 1 of `grid` with room for max_pairs (brick, Gaussian) pairs. */
+size_t gs_voxelize_workspace_size(int n, const gs_grid* grid, const int32_t roi_lo[3],
+                                  const int32_t roi_dim[3], const gs_opts* opts,
+                                  int64_t max_pairs);
+
+/* Pair count of the voxelizer binning (SYNCHRONOUS, like gs_project_count_pairs). */
+int gs_voxelize_count_pairs(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                            int n, const gs_grid* grid, const int32_t roi_lo[3],
+                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
+                            size_t ws_bytes, void* stream, int64_t* h_pairs);
+
+/* Forward voxelization: d_vol[z][y][x] over the region of interest (roi_dim[2] x roi_dim[1] x
+ * roi_dim[0] floats, overwritten) = sum_i rho_i exp(-q/2) for q = (x_v - p_i)^T Sigma_i^-1
+ * (x_v - p_i) < Q at voxel centres x_v. */
+int gs_voxelize(const float* d_mean_rho, const float* d_scale, const float* d_quat, int n,
+                const gs_grid* grid, const int32_t roi_lo[3], const int32_t roi_dim[3],
+                const gs_opts* opts, float* d_vol, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Backward of gs_voxelize: dL/dvol in, dL/d(mean_rho, scale, quat) out; accumulate and reuse
+ * as in gs_project_backward. */
+int gs_voxelize_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                         int n, const gs_grid* grid, const int32_t roi_lo[3],
+                         const int32_t roi_dim[3], const gs_opts* opts, const float* d_dvol,
+                         float* d_g_mean_rho, float* d_g_scale, float* d_g_quat, int accumulate,
+                         int reuse, void* d_ws, size_t ws_bytes, void* stream);
+
+/* In-cut (voxel, Gaussian) evaluation count into the status block (asynchronous). */
+int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                            int n, const gs_grid* grid, const int32_t roi_lo[3],
+                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
+                            size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Binning internals exposed for testing: the sorted (key, Gaussian) lists of the last
+ * binning in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).
+ * ------------------------------------------------------------------------------------- */
+int gs_read_pairs(const void* d_ws, size_t ws_bytes, void* stream, int64_t cap,
+                  uint32_t* h_keys, uint32_t* h_vals, int64_t* h_pairs);
+
+/* ---------------------------------------------------------------------------------------
+ * Kernel timing (for measurement): when enabled, every kernel launch of this library
+ * records CUDA events on its stream; gs_timing_read synchronises the device and returns, per
+ * kernel name, the number of launches and the summed milliseconds since the last reset.
+ * ------------------------------------------------------------------------------------- */
+void gs_timing_enable(int on);
+void gs_timing_reset(void);
+/* Writes up to `cap` entries; returns the number of distinct kernels (may exceed cap). */
+int gs_timing_read(int cap, const char** h_names, int64_t* h_launches, double* h_ms);
+/* Total number of kernel launches issued by this library since the last reset (always on). */
+int64_t gs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSCT_H */

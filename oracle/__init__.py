@@ -55,6 +55,8 @@ def lib():
                 "orc_project_pixels": (None, [i, P, i, P, i, i, d, d, d, i, P, P, i]),
                 "orc_project_ambiguity": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i]),
                 "orc_project_exact": (None, [i, P, i, P, i, i, P, i]),
+                "orc_pair_flags": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i]),
+                "orc_voxel_flags": (None, [i, P, P, P, P, d, d, d, P]),
                 "orc_pixel_ray": (None, [P, i, i, i, i, P, P]),
                 "orc_keys": (ll, [i, P, i, P, i, i, d, d, d, i, ll, P, P, P]),
                 "orc_project_grad": (None, [i, P, i, P, i, i, d, d, d, P, P, i]),
@@ -150,6 +152,23 @@ def project_ambiguity(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0):
     lib().orc_project_ambiguity(P.shape[0], _p(P), V.shape[0], _p(V), W, H, opts.cut, opts.eps,
                                 opts.znear, rel_band, px_band, _p(allow), nthreads)
     return allow
+
+
+def pair_flags(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0):
+    """Guard-band flags per (view, Gaussian), (V, N) int32 (see gs_oracle.cpp)."""
+    flags = np.zeros((V.shape[0], P.shape[0]), dtype=np.int32)
+    lib().orc_pair_flags(P.shape[0], _p(P), V.shape[0], _p(V), W, H, opts.cut, opts.eps,
+                         opts.znear, rel_band, px_band, _p(flags), nthreads)
+    return flags
+
+
+def voxel_flags(P, grid, roi_lo, roi_dim, rel_band, idx_band, cut=3.0):
+    G = grid64(grid)
+    lo, dim = _i3(roi_lo), _i3(roi_dim)
+    flags = np.zeros(P.shape[0], dtype=np.int32)
+    lib().orc_voxel_flags(P.shape[0], _p(P), _p(G), _p(lo), _p(dim), cut, rel_band, idx_band,
+                          _p(flags))
+    return flags
 
 
 def project_exact(P, V, W, H, nthreads=0):

@@ -459,6 +459,86 @@ void orc_project_ambiguity(int n, const double* g, int nv, const double* views, 
   }
 }
 
+// Guard-band flags per (view, Gaussian) pair, view-major (nv*n ints), for comparing an FP32
+// implementation with this FP64 definition:
+//   1: a box edge lies within px_band of an integer (the clipped pixel range may differ)
+//   2: some pixel of the box has |q - Q| <= rel_band * Q (its in/out decision may differ)
+//   4: cone depth within 1e-5 (relative) of the near plane
+//   8: density cut active and |A| within rel_band of eps or Q within rel_band of cut^2
+void orc_pair_flags(int n, const double* g, int nv, const double* views, int W, int H,
+                    double cut, double eps, double znear, double rel_band, double px_band,
+                    int* flags, int nthreads) {
+  Opts o{cut, eps, znear};
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < nv; ++k) {
+    View vw = make_view(views + 13 * k);
+    for (int i = 0; i < n; ++i) {
+      double p[3], s[3], q[4], rho;
+      unpack(g + 11 * i, p, s, q, rho);
+      Footprint<double> f = footprint(p, s, q, rho, vw, W, H, o);
+      int fl = 0;
+      if (vw.mode == 0 && f.why != 1 && std::fabs(f.zc - znear) <= 1e-5 * std::max(1.0, znear))
+        fl |= 4;
+      if (f.why == 0 || f.why == 4) {
+        const double e[4] = {f.lo_x, f.hi_x, f.lo_y, f.hi_y};
+        for (double x : e)
+          if (std::fabs(x - std::nearbyint(x)) <= px_band) fl |= 1;
+      }
+      if (eps > 0.0 && f.why != 1 && f.why != 2) {
+        double aa = std::fabs(val(f.A));
+        if (std::fabs(aa - eps) <= rel_band * eps) fl |= 8;
+        if (f.Q > 0.0 && std::fabs(f.Q - cut * cut) <= rel_band * cut * cut) fl |= 8;
+      }
+      if (!f.culled) {
+        int x0 = std::max(0, f.ix0 - 1), x1 = std::min(W - 1, f.ix1 + 1);
+        int y0 = std::max(0, f.iy0 - 1), y1 = std::min(H - 1, f.iy1 + 1);
+        for (int y = y0; y <= y1 && !(fl & 2); ++y)
+          for (int x = x0; x <= x1; ++x) {
+            double qq = quad2(f, (double)x - f.px, (double)y - f.py);
+            if (std::fabs(qq - f.Q) <= rel_band * f.Q) { fl |= 2; break; }
+          }
+      }
+      flags[(size_t)k * n + i] = fl;
+    }
+  }
+}
+
+// Guard-band flags per Gaussian for the voxelizer: 1 box edge within idx_band of an integer
+// index, 2 some voxel of the box with |q - Q| <= rel_band * Q.
+void orc_voxel_flags(int n, const double* g, const double* grid, const int* roi_lo,
+                     const int* roi_dim, double cut, double rel_band, double idx_band,
+                     int* flags) {
+  Grid gr = make_grid(grid);
+  for (int i = 0; i < n; ++i) {
+    double p[3], s[3], q[4], rho;
+    unpack(g + 11 * i, p, s, q, rho);
+    int fl = 0;
+    double R[3][3], S[3][3];
+    if (rotation(q, R)) {
+      covariance(R, s, false, S);
+      for (int k = 0; k < 3; ++k) {
+        double r = std::sqrt(cut * cut * S[k][k]);
+        double a = (p[k] - r - gr.o[k]) / gr.h[k] - 0.5, b = (p[k] + r - gr.o[k]) / gr.h[k] - 0.5;
+        if (std::fabs(a - std::nearbyint(a)) <= idx_band || std::fabs(b - std::nearbyint(b)) <= idx_band)
+          fl |= 1;
+      }
+    }
+    VoxFoot<double> fr = vox_footprint(p, s, q, gr, roi_lo, roi_dim, cut);
+    if (!fr.culled) {
+      for (int z = std::max(roi_lo[2], fr.lo[2] - 1); z <= std::min(roi_lo[2] + roi_dim[2] - 1, fr.hi[2] + 1) && !(fl & 2); ++z)
+        for (int y = std::max(roi_lo[1], fr.lo[1] - 1); y <= std::min(roi_lo[1] + roi_dim[1] - 1, fr.hi[1] + 1) && !(fl & 2); ++y)
+          for (int x = std::max(roi_lo[0], fr.lo[0] - 1); x <= std::min(roi_lo[0] + roi_dim[0] - 1, fr.hi[0] + 1); ++x) {
+            double d[3] = {gr.o[0] + (x + 0.5) * gr.h[0] - p[0], gr.o[1] + (y + 0.5) * gr.h[1] - p[1],
+                           gr.o[2] + (z + 0.5) * gr.h[2] - p[2]};
+            double qq = quad3(fr.Si, d);
+            if (std::fabs(qq - fr.Q) <= rel_band * fr.Q) { fl |= 2; break; }
+          }
+    }
+    flags[i] = fl;
+  }
+}
+
 // (A) Exact line integral of every Gaussian along the ray through each pixel centre (Eq. 3),
 // no truncation:  int rho exp(-1/2 (o + t d - p)^T Sigma^-1 (o + t d - p)) dt over all t
 //               = rho sqrt(2 pi / a) exp(-1/2 (c - b^2 / a)),

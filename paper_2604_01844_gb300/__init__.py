@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) Gaussian-splatting CT hot path of FaCT-GS (arXiv 2604.01844).
+
+The compute runs in libgsct (C ABI: include/gsct.h, CUDA sources under csrc/); this package is
+its thin Python binding.  Build it with paper_2604_01844_gb300.build.build() (or
+__graft_entry__.build()).
+"""
+from . import binding
+from .binding import GsError
+from .projector import Projector, ProjectFunction, project, views_to_device
+from .voxelizer import Voxelizer, VoxelizeFunction, voxelize
+
+__all__ = ["binding", "GsError", "Projector", "ProjectFunction", "project", "views_to_device",
+           "Voxelizer", "VoxelizeFunction", "voxelize"]

@@ -1,0 +1,570 @@
+// Loss terms of the reconstruction objective (Eq. 5) and the volume fit (Eq. 6), fused
+// forward + backward, plus the Adam update with the parameter activations.
+//
+//   l1       mean |a - b| and its gradient sign(a - b) / n, one pass, float4 loads
+//   tv3d     anisotropic TV with forward differences / n_vox and its sub-gradient, one pass
+//   ssim2d   Wang et al. 2004 SSIM, 11x11 Gaussian window (sigma 1.5), zero-padded 'same'
+//            filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2; loss term weight * (1 - mean SSIM).
+//            Two tiled kernels with separable filtering in shared memory: (1) the five local
+//            moments, SSIM and three per-pixel partial-derivative maps; (2) the same window
+//            applied to the three maps, combined into dL/dx.
+//   ssim3d   the same with an 11^3 window over a volume (Eq. 6): each thread owns one z-row
+//            and walks it with a ring buffer of filtered xy-planes.
+//   adam     Adam on raw parameters (log-scale, softplus-density, raw quaternion) with the
+//            activations applied in the same pass.
+#include <algorithm>
+#include <cmath>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) - (x < 0.f); }
+
+template <typename T>
+__device__ __forceinline__ void block_add(T v, T* target) {
+  __shared__ T part[32];
+  v = gsd::warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  (void)lane;
+  (void)w;
+  // linear thread id for multi-dimensional blocks
+  const int l2 = tid & 31, w2 = tid >> 5;
+  if (l2 == 0) part[w2] = v;
+  __syncthreads();
+  if (tid == 0) {
+    T s = 0;
+    for (int i = 0; i < (nthreads + 31) / 32; ++i) s += part[i];
+    if (s != (T)0) atomicAdd(target, s);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// L1
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+    k_l1(const float* __restrict__ a, const float* __restrict__ b, int64_t n, float scale,
+         float* __restrict__ loss, float* __restrict__ grad, int accumulate) {
+  float s = 0.f;
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  float4* g4 = reinterpret_cast<float4*>(grad);
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += stride) {
+    const float4 x = a4[i], y = b4[i];
+    const float d0 = x.x - y.x, d1 = x.y - y.y, d2 = x.z - y.z, d3 = x.w - y.w;
+    s += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+    if (grad) {
+      float4 g = make_float4(scale * sgnf(d0), scale * sgnf(d1), scale * sgnf(d2), scale * sgnf(d3));
+      if (accumulate) {
+        const float4 p = g4[i];
+        g.x += p.x; g.y += p.y; g.z += p.z; g.w += p.w;
+      }
+      g4[i] = g;
+    }
+  }
+  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+    const float d = a[i] - b[i];
+    s += fabsf(d);
+    if (grad) grad[i] = (accumulate ? grad[i] : 0.f) + scale * sgnf(d);
+  }
+  if (loss) block_add(s * scale, loss);
+}
+
+// ------------------------------------------------------------------------------------------
+// TV 3D
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+    k_tv3d(const float* __restrict__ v, int nx, int ny, int nz, float scale,
+           float* __restrict__ loss, float* __restrict__ grad, int accumulate) {
+  const int64_t total = (int64_t)nx * ny * nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  float s = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * kThreads) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / sz);
+    const float c = v[i];
+    float g = 0.f;
+    if (x + 1 < nx) { const float d = v[i + 1] - c; s += fabsf(d); g -= sgnf(d); }
+    if (x > 0) g += sgnf(c - v[i - 1]);
+    if (y + 1 < ny) { const float d = v[i + sy] - c; s += fabsf(d); g -= sgnf(d); }
+    if (y > 0) g += sgnf(c - v[i - sy]);
+    if (z + 1 < nz) { const float d = v[i + sz] - c; s += fabsf(d); g -= sgnf(d); }
+    if (z > 0) g += sgnf(c - v[i - sz]);
+    if (grad) grad[i] = (accumulate ? grad[i] : 0.f) + scale * g;
+  }
+  if (loss) block_add(s * scale, loss);
+}
+
+// ------------------------------------------------------------------------------------------
+// SSIM 2D
+// ------------------------------------------------------------------------------------------
+constexpr int kR = 5;            // window radius (11 taps)
+constexpr int kTile = 16;        // output tile side
+constexpr int kIn = kTile + 2 * kR;  // 26
+
+__device__ __forceinline__ void window_weights(float* w) {
+  // normalised 11-tap Gaussian, sigma 1.5
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    float s = 0.f;
+    for (int k = 0; k < 2 * kR + 1; ++k) {
+      const float d = (float)(k - kR);
+      w[k] = expf(-d * d / (2.f * 1.5f * 1.5f));
+      s += w[k];
+    }
+    for (int k = 0; k < 2 * kR + 1; ++k) w[k] /= s;
+  }
+}
+
+// Kernel 1: moments, SSIM, and the maps m1 = dS/dmu_x - 2 mu_x dS/dsxx - mu_y dS/dsxy,
+// m2 = dS/dsxx, m3 = dS/dsxy, all multiplied by -weight / N (the loss is weight * (1 - SSIM)).
+__global__ void __launch_bounds__(kTile * kTile)
+    k_ssim2d_fwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W, float C1,
+                 float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
+                 int64_t plane) {
+  __shared__ float w[2 * kR + 1];
+  __shared__ float sx[kIn][kIn + 1], sy[kIn][kIn + 1];
+  __shared__ float hm[5][kIn][kTile + 1];
+  window_weights(w);
+  const int img = blockIdx.z;
+  const int x0 = blockIdx.x * kTile - kR, y0 = blockIdx.y * kTile - kR;
+  const float* Xi = X + (size_t)img * H * W;
+  const float* Yi = Y + (size_t)img * H * W;
+  const int tid = threadIdx.y * kTile + threadIdx.x;
+  for (int p = tid; p < kIn * kIn; p += kTile * kTile) {
+    const int r = p / kIn, c = p % kIn, y = y0 + r, x = x0 + c;
+    const bool in = x >= 0 && x < W && y >= 0 && y < H;
+    sx[r][c] = in ? Xi[(size_t)y * W + x] : 0.f;
+    sy[r][c] = in ? Yi[(size_t)y * W + x] : 0.f;
+  }
+  __syncthreads();
+  for (int p = tid; p < kIn * kTile; p += kTile * kTile) {
+    const int r = p / kTile, c = p % kTile;
+    float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) {
+      const float u = sx[r][c + k], v = sy[r][c + k], wk = w[k];
+      a = fmaf(wk, u, a);
+      b = fmaf(wk, v, b);
+      aa = fmaf(wk, u * u, aa);
+      bb = fmaf(wk, v * v, bb);
+      ab = fmaf(wk, u * v, ab);
+    }
+    hm[0][r][c] = a; hm[1][r][c] = b; hm[2][r][c] = aa; hm[3][r][c] = bb; hm[4][r][c] = ab;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k) {
+    const float wk = w[k];
+    mx = fmaf(wk, hm[0][ty + k][tx], mx);
+    my = fmaf(wk, hm[1][ty + k][tx], my);
+    exx = fmaf(wk, hm[2][ty + k][tx], exx);
+    eyy = fmaf(wk, hm[3][ty + k][tx], eyy);
+    exy = fmaf(wk, hm[4][ty + k][tx], exy);
+  }
+  const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+  const float A = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
+  const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
+  const float S = (A * Bn) / (C * D);
+  const int x = blockIdx.x * kTile + tx, y = blockIdx.y * kTile + ty;
+  const bool valid = x < W && y < H;
+  float contrib = 0.f;
+  if (valid) {
+    const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
+    const float dsxx = -S / D;
+    const float dsxy = 2.f * A / (C * D);
+    const size_t o = (size_t)img * H * W + (size_t)y * W + x;
+    maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
+    maps[plane + o] = gscale * dsxx;
+    maps[2 * plane + o] = gscale * dsxy;
+    contrib = 1.f - S;
+  }
+  if (loss) block_add(contrib * (-gscale), loss);
+}
+
+// Kernel 2: dL/dx = w * m1 + 2 x (w * m2) + y (w * m3).
+__global__ void __launch_bounds__(kTile * kTile)
+    k_ssim2d_bwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W,
+                 const float* __restrict__ maps, int64_t plane, float* __restrict__ grad,
+                 int accumulate) {
+  __shared__ float w[2 * kR + 1];
+  __shared__ float sm[3][kIn][kIn + 1];
+  __shared__ float hm[3][kIn][kTile + 1];
+  window_weights(w);
+  const int img = blockIdx.z;
+  const int x0 = blockIdx.x * kTile - kR, y0 = blockIdx.y * kTile - kR;
+  const int tid = threadIdx.y * kTile + threadIdx.x;
+  const size_t base = (size_t)img * H * W;
+  for (int p = tid; p < kIn * kIn; p += kTile * kTile) {
+    const int r = p / kIn, c = p % kIn, y = y0 + r, x = x0 + c;
+    const bool in = x >= 0 && x < W && y >= 0 && y < H;
+    const size_t o = base + (size_t)y * W + x;
+    sm[0][r][c] = in ? maps[o] : 0.f;
+    sm[1][r][c] = in ? maps[plane + o] : 0.f;
+    sm[2][r][c] = in ? maps[2 * plane + o] : 0.f;
+  }
+  __syncthreads();
+  for (int p = tid; p < kIn * kTile; p += kTile * kTile) {
+    const int r = p / kTile, c = p % kTile;
+    float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) {
+      const float wk = w[k];
+      a = fmaf(wk, sm[0][r][c + k], a);
+      b = fmaf(wk, sm[1][r][c + k], b);
+      d = fmaf(wk, sm[2][r][c + k], d);
+    }
+    hm[0][r][c] = a; hm[1][r][c] = b; hm[2][r][c] = d;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * kTile + tx, y = blockIdx.y * kTile + ty;
+  if (x >= W || y >= H) return;
+  float f1 = 0.f, f2 = 0.f, f3 = 0.f;
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k) {
+    const float wk = w[k];
+    f1 = fmaf(wk, hm[0][ty + k][tx], f1);
+    f2 = fmaf(wk, hm[1][ty + k][tx], f2);
+    f3 = fmaf(wk, hm[2][ty + k][tx], f3);
+  }
+  const size_t o = base + (size_t)y * W + x;
+  const float g = f1 + 2.f * X[o] * f2 + Y[o] * f3;
+  grad[o] = accumulate ? grad[o] + g : g;
+}
+
+// ------------------------------------------------------------------------------------------
+// SSIM 3D: each thread owns one (x, y) column and walks z.  The xy-filtered moments of each
+// z-plane come from shared memory (tile 16x16 with a 5-voxel halo); the z filter uses an
+// 11-deep ring buffer of those filtered planes held in registers per thread.
+// ------------------------------------------------------------------------------------------
+constexpr int kT3 = 16;
+constexpr int kIn3 = kT3 + 2 * kR;
+
+template <int NM>
+__device__ __forceinline__ void filter_plane_xy(float (*src)[kIn3][kIn3 + 1],
+                                                float (*tmp)[kIn3][kT3 + 1], const float* w,
+                                                int tid, float out[NM]) {
+  // horizontal pass over kIn3 rows x kT3 columns, then the vertical tap for this thread
+  for (int p = tid; p < kIn3 * kT3; p += kT3 * kT3) {
+    const int r = p / kT3, c = p % kT3;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      float a = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * kR; ++k) a = fmaf(w[k], src[m][r][c + k], a);
+      tmp[m][r][c] = a;
+    }
+  }
+  __syncthreads();
+  const int tx = tid % kT3, ty = tid / kT3;
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) a = fmaf(w[k], tmp[m][ty + k][tx], a);
+    out[m] = a;
+  }
+}
+
+// Pass 1: moments -> SSIM -> maps (m1, m2, m3) like the 2D kernel.
+__global__ void __launch_bounds__(kT3 * kT3)
+    k_ssim3d_fwd(const float* __restrict__ X, const float* __restrict__ Y, int nx, int ny, int nz,
+                 float C1, float C2, float gscale, float* __restrict__ loss,
+                 float* __restrict__ maps, int64_t plane) {
+  __shared__ float w[2 * kR + 1];
+  __shared__ float src[5][kIn3][kIn3 + 1];
+  __shared__ float tmp[5][kIn3][kT3 + 1];
+  window_weights(w);
+  const int tid = threadIdx.y * kT3 + threadIdx.x;
+  const int x0 = blockIdx.x * kT3 - kR, y0 = blockIdx.y * kT3 - kR;
+  const int x = blockIdx.x * kT3 + threadIdx.x, y = blockIdx.y * kT3 + threadIdx.y;
+  const size_t sxy = (size_t)nx * ny;
+  float ring[2 * kR + 1][5];
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k)
+#pragma unroll
+    for (int m = 0; m < 5; ++m) ring[k][m] = 0.f;
+  float contrib = 0.f;
+  // plane zi enters the ring; output z = zi - kR is produced once its 11 planes are in
+  for (int zi = 0; zi < nz + kR; ++zi) {
+    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (zi < nz) {
+      __syncthreads();
+      for (int p = tid; p < kIn3 * kIn3; p += kT3 * kT3) {
+        const int r = p / kIn3, c = p % kIn3, yy = y0 + r, xx = x0 + c;
+        const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny;
+        const size_t o = (size_t)zi * sxy + (size_t)yy * nx + xx;
+        const float u = in ? X[o] : 0.f, v = in ? Y[o] : 0.f;
+        src[0][r][c] = u; src[1][r][c] = v; src[2][r][c] = u * u; src[3][r][c] = v * v;
+        src[4][r][c] = u * v;
+      }
+      __syncthreads();
+      filter_plane_xy<5>(src, tmp, w, tid, f);
+    }
+    // shift the ring (static indices keep it in registers)
+#pragma unroll
+    for (int k = 0; k < 2 * kR; ++k)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) ring[k][m] = ring[k + 1][m];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) ring[2 * kR][m] = f[m];
+    const int z = zi - kR;
+    if (z < 0) continue;
+    float mo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) mo[m] = fmaf(w[k], ring[k][m], mo[m]);
+    const float mx = mo[0], my = mo[1];
+    const float sxx = mo[2] - mx * mx, syy = mo[3] - my * my, sxy2 = mo[4] - mx * my;
+    const float A = 2.f * mx * my + C1, Bn = 2.f * sxy2 + C2;
+    const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
+    const float S = (A * Bn) / (C * D);
+    if (x < nx && y < ny) {
+      const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
+      const float dsxx = -S / D;
+      const float dsxy = 2.f * A / (C * D);
+      const size_t o = (size_t)z * sxy + (size_t)y * nx + x;
+      maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
+      maps[plane + o] = gscale * dsxx;
+      maps[2 * plane + o] = gscale * dsxy;
+      contrib += 1.f - S;
+    }
+  }
+  if (loss) block_add(contrib * (-gscale), loss);
+}
+
+// Pass 2: filter the three maps with the 11^3 window; dL/dx = f1 + 2 x f2 + y f3.
+__global__ void __launch_bounds__(kT3 * kT3)
+    k_ssim3d_bwd(const float* __restrict__ X, const float* __restrict__ Y, int nx, int ny, int nz,
+                 const float* __restrict__ maps, int64_t plane, float* __restrict__ grad,
+                 int accumulate) {
+  __shared__ float w[2 * kR + 1];
+  __shared__ float src[3][kIn3][kIn3 + 1];
+  __shared__ float tmp[3][kIn3][kT3 + 1];
+  window_weights(w);
+  const int tid = threadIdx.y * kT3 + threadIdx.x;
+  const int x0 = blockIdx.x * kT3 - kR, y0 = blockIdx.y * kT3 - kR;
+  const int x = blockIdx.x * kT3 + threadIdx.x, y = blockIdx.y * kT3 + threadIdx.y;
+  const size_t sxy = (size_t)nx * ny;
+  float ring[2 * kR + 1][3];
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) ring[k][m] = 0.f;
+  for (int zi = 0; zi < nz + kR; ++zi) {
+    float f[3] = {0.f, 0.f, 0.f};
+    if (zi < nz) {
+      __syncthreads();
+      for (int p = tid; p < kIn3 * kIn3; p += kT3 * kT3) {
+        const int r = p / kIn3, c = p % kIn3, yy = y0 + r, xx = x0 + c;
+        const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny;
+        const size_t o = (size_t)zi * sxy + (size_t)yy * nx + xx;
+        src[0][r][c] = in ? maps[o] : 0.f;
+        src[1][r][c] = in ? maps[plane + o] : 0.f;
+        src[2][r][c] = in ? maps[2 * plane + o] : 0.f;
+      }
+      __syncthreads();
+      filter_plane_xy<3>(src, tmp, w, tid, f);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * kR; ++k)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) ring[k][m] = ring[k + 1][m];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) ring[2 * kR][m] = f[m];
+    const int z = zi - kR;
+    if (z < 0 || x >= nx || y >= ny) continue;
+    float g3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) g3[m] = fmaf(w[k], ring[k][m], g3[m]);
+    const size_t o = (size_t)z * sxy + (size_t)y * nx + x;
+    const float g = g3[0] + 2.f * X[o] * g3[1] + Y[o] * g3[2];
+    grad[o] = accumulate ? grad[o] + g : g;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Adam with activations: mean raw, density softplus(raw), scale exp(raw), quaternion raw.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + expf(-x)); }
+
+__device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float lr, float b1,
+                                       float b2, float c1, float c2, float eps) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  p -= lr * (m * c1) / (sqrtf(v * c2) + eps);
+  return p;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_adam(float4* __restrict__ raw_mr, float4* __restrict__ raw_sc, float4* __restrict__ raw_q,
+           float4* __restrict__ m, float4* __restrict__ v, const float4* __restrict__ g_mr,
+           const float4* __restrict__ g_sc, const float4* __restrict__ g_q,
+           float4* __restrict__ mr, float4* __restrict__ sc, float4* __restrict__ q, int n,
+           const int* __restrict__ step, gs_adam_opts o) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const int t = *step + 1;
+  const float c1 = 1.f / (1.f - powf(o.beta1, (float)t));
+  const float c2 = 1.f / (1.f - powf(o.beta2, (float)t));
+  float4 pm = raw_mr[i], ps = raw_sc[i], pq = raw_q[i];
+  float4 m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
+  float4 v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+  const float4 gm = g_mr[i], gsc = g_sc[i], gq = g_q[i];
+  // gradients with respect to the raw parameters
+  const float grho = gm.w * sigmoidf(pm.w);
+  const float gs0 = gsc.x * expf(ps.x), gs1 = gsc.y * expf(ps.y), gs2 = gsc.z * expf(ps.z);
+  adam1(pm.x, gm.x, m0.x, v0.x, o.lr_mean, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pm.y, gm.y, m0.y, v0.y, o.lr_mean, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pm.z, gm.z, m0.z, v0.z, o.lr_mean, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pm.w, grho, m0.w, v0.w, o.lr_rho, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(ps.x, gs0, m1.x, v1.x, o.lr_scale, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(ps.y, gs1, m1.y, v1.y, o.lr_scale, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(ps.z, gs2, m1.z, v1.z, o.lr_scale, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pq.x, gq.x, m2.x, v2.x, o.lr_quat, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pq.y, gq.y, m2.y, v2.y, o.lr_quat, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pq.z, gq.z, m2.z, v2.z, o.lr_quat, o.beta1, o.beta2, c1, c2, o.eps);
+  adam1(pq.w, gq.w, m2.w, v2.w, o.lr_quat, o.beta1, o.beta2, c1, c2, o.eps);
+  // keep scales within [min_log_scale, max_log_scale]
+  ps.x = fminf(fmaxf(ps.x, o.min_log_scale), o.max_log_scale);
+  ps.y = fminf(fmaxf(ps.y, o.min_log_scale), o.max_log_scale);
+  ps.z = fminf(fmaxf(ps.z, o.min_log_scale), o.max_log_scale);
+  raw_mr[i] = pm; raw_sc[i] = ps; raw_q[i] = pq;
+  m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
+  v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
+  mr[i] = make_float4(pm.x, pm.y, pm.z, softplusf(pm.w));
+  sc[i] = make_float4(expf(ps.x), expf(ps.y), expf(ps.z), 0.f);
+  q[i] = pq;
+}
+
+__global__ void k_step_incr(int* step) { *step += 1; }
+
+__global__ void __launch_bounds__(kThreads)
+    k_activate(const float4* __restrict__ raw_mr, const float4* __restrict__ raw_sc,
+               const float4* __restrict__ raw_q, float4* __restrict__ mr,
+               float4* __restrict__ sc, float4* __restrict__ q, int n) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 pm = raw_mr[i], ps = raw_sc[i];
+  mr[i] = make_float4(pm.x, pm.y, pm.z, softplusf(pm.w));
+  sc[i] = make_float4(expf(ps.x), expf(ps.y), expf(ps.z), 0.f);
+  q[i] = raw_q[i];
+}
+
+int grid_for(int64_t n) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 8 * (int64_t)num_sms()));
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, float* d_loss,
+               float* d_grad, int accumulate, void* stream) {
+  if (n < 0 || (n > 0 && (!d_a || !d_b))) return GS_ERR_ARG;
+  if (!al16(d_a) || !al16(d_b) || !al16(d_grad)) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  return launch("l1_loss", k_l1, dim3(grid_for(n / 4 + 1)), dim3(kThreads), 0,
+                (cudaStream_t)stream, d_a, d_b, n, weight / (float)n, d_loss, d_grad, accumulate);
+}
+
+int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,
+                 float* d_grad, int accumulate, void* stream) {
+  if (!d_vol || nx < 1 || ny < 1 || nz < 1) return GS_ERR_ARG;
+  const int64_t total = (int64_t)nx * ny * nz;
+  return launch("tv3d_loss", k_tv3d, dim3(grid_for(total)), dim3(kThreads), 0,
+                (cudaStream_t)stream, d_vol, nx, ny, nz, weight / (float)total, d_loss, d_grad,
+                accumulate);
+}
+
+size_t gs_ssim_workspace_size(int64_t n_elems) { return (size_t)(3 * n_elems) * sizeof(float) + 256; }
+
+int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, float data_range,
+                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
+                   size_t ws_bytes, void* stream) {
+  if (!d_x || !d_y || !d_grad || !d_ws || n_img < 1 || H < 1 || W < 1 || !(data_range > 0.f))
+    return GS_ERR_ARG;
+  if (n_img > 65535) return GS_ERR_ARG;
+  const int64_t plane = (int64_t)n_img * H * W;
+  if (ws_bytes < gs_ssim_workspace_size(plane)) return GS_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float C1 = (0.01f * data_range) * (0.01f * data_range);
+  const float C2 = (0.03f * data_range) * (0.03f * data_range);
+  const float gscale = -weight / (float)plane;
+  dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, n_img), block(kTile, kTile);
+  float* maps = (float*)d_ws;
+  GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
+                d_loss, maps, plane));
+  return launch("ssim2d_bwd", k_ssim2d_bwd, grid, block, 0, s, d_x, d_y, H, W,
+                (const float*)maps, plane, d_grad, accumulate);
+}
+
+int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
+                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
+                   size_t ws_bytes, void* stream) {
+  if (!d_x || !d_y || !d_grad || !d_ws || nx < 1 || ny < 1 || nz < 1 || !(data_range > 0.f))
+    return GS_ERR_ARG;
+  const int64_t plane = (int64_t)nx * ny * nz;
+  if (ws_bytes < gs_ssim_workspace_size(plane)) return GS_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float C1 = (0.01f * data_range) * (0.01f * data_range);
+  const float C2 = (0.03f * data_range) * (0.03f * data_range);
+  const float gscale = -weight / (float)plane;
+  dim3 grid((nx + kT3 - 1) / kT3, (ny + kT3 - 1) / kT3), block(kT3, kT3);
+  float* maps = (float*)d_ws;
+  GS_TRY(launch("ssim3d_fwd", k_ssim3d_fwd, grid, block, 0, s, d_x, d_y, nx, ny, nz, C1, C2,
+                gscale, d_loss, maps, plane));
+  return launch("ssim3d_bwd", k_ssim3d_bwd, grid, block, 0, s, d_x, d_y, nx, ny, nz,
+                (const float*)maps, plane, d_grad, accumulate);
+}
+
+int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, float* d_m,
+                 float* d_v, const float* d_g_mean_rho, const float* d_g_scale,
+                 const float* d_g_quat, float* d_mean_rho, float* d_scale, float* d_quat, int n,
+                 int* d_step, const gs_adam_opts* opts, void* stream) {
+  if (n < 0 || !opts || !d_step) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  const void* ps[] = {d_raw_mean_rho, d_raw_scale, d_raw_quat, d_m, d_v, d_g_mean_rho,
+                      d_g_scale, d_g_quat, d_mean_rho, d_scale, d_quat};
+  for (const void* p : ps)
+    if (!p || !al16(p)) return GS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_TRY(launch("adam", k_adam, dim3((n + kThreads - 1) / kThreads), dim3(kThreads), 0, s,
+                (float4*)d_raw_mean_rho, (float4*)d_raw_scale, (float4*)d_raw_quat, (float4*)d_m,
+                (float4*)d_v, (const float4*)d_g_mean_rho, (const float4*)d_g_scale,
+                (const float4*)d_g_quat, (float4*)d_mean_rho, (float4*)d_scale, (float4*)d_quat,
+                n, (const int*)d_step, *opts));
+  return launch("step_incr", k_step_incr, dim3(1), dim3(1), 0, s, d_step);
+}
+
+int gs_activate(const float* d_raw_mean_rho, const float* d_raw_scale, const float* d_raw_quat,
+                float* d_mean_rho, float* d_scale, float* d_quat, int n, void* stream) {
+  if (n < 0) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  return launch("activate", k_activate, dim3((n + kThreads - 1) / kThreads), dim3(kThreads), 0,
+                (cudaStream_t)stream, (const float4*)d_raw_mean_rho, (const float4*)d_raw_scale,
+                (const float4*)d_raw_quat, (float4*)d_mean_rho, (float4*)d_scale,
+                (float4*)d_quat, n);
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+"""X-ray rasterizer (Sec. 3.2, 3.5; Eq. 4) over libgsct, with workspace planning and a
+torch.autograd.Function whose backward is the library's per-Gaussian backward kernels."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _f4(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 4):
+        raise ValueError(f"{name} must be a CUDA float32 (N, 4) tensor")
+    return t.contiguous()
+
+
+def views_to_device(views, device) -> torch.Tensor:
+    """gs_view records (numpy VIEW_DTYPE array) -> (V, 64) uint8 tensor on `device`."""
+    v = np.ascontiguousarray(np.asarray(views).astype(B.VIEW_DTYPE, copy=False))
+    raw = torch.from_numpy(v.view(np.uint8).reshape(len(v), 64).copy())
+    return raw.to(device)
+
+
+class Projector:
+    """Projects Gaussians to a fixed set of views of a W x H detector.
+
+    The workspace (device scratch owned by this object) is sized by counting the (view, tile)
+    pairs of the parameters first seen, times `headroom`; `ensure_capacity` re-plans it.
+    """
+
+    def __init__(self, views, W: int, H: int, cut: float = 3.0, eps: float = 0.0,
+                 znear: float = 0.1, tile: int = 16, device="cuda", headroom: float = 1.5):
+        self.device = torch.device(device)
+        self.views = views if isinstance(views, torch.Tensor) else views_to_device(views, self.device)
+        self.n_views = int(self.views.shape[0])
+        self.W, self.H = int(W), int(H)
+        self.opts = B.opts(cut=cut, eps=eps, znear=znear, tile=tile)
+        self.headroom = float(headroom)
+        self.ws = None
+        self.ws_n = -1
+        self.capacity = 0
+        self._fwd_token = None
+
+    # -- workspace -----------------------------------------------------------------------
+    def workspace_bytes(self, n: int, pairs: int) -> int:
+        b = B.lib().gs_project_workspace_size(n, self.n_views, self.W, self.H,
+                                              ctypes.byref(self.opts), int(pairs))
+        if b == 0:
+            raise B.GsError("invalid projector sizes")
+        return int(b)
+
+    def _alloc(self, n: int, pairs: int):
+        nbytes = self.workspace_bytes(n, pairs)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ws_n = n
+        self.capacity = pairs
+
+    def count_pairs(self, mean_rho, scale, quat) -> int:
+        """Exact number of (view, tile) pairs (synchronises the stream)."""
+        n = mean_rho.shape[0]
+        if self.ws is None or self.ws_n != n:
+            self._alloc(n, 0)
+        out = ctypes.c_int64(0)
+        B.check(B.lib().gs_project_count_pairs(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
+            self.W, self.H, ctypes.byref(self.opts), B.ptr(self.ws), self.ws.numel(),
+            B.stream_handle(), ctypes.byref(out)), "gs_project_count_pairs")
+        return int(out.value)
+
+    def ensure_capacity(self, mean_rho, scale, quat) -> int:
+        """Re-plans the workspace if the current parameters need more pairs; returns the count."""
+        pairs = self.count_pairs(mean_rho, scale, quat)
+        n = mean_rho.shape[0]
+        if self.ws_n != n or pairs > self.capacity:
+            self._alloc(n, int(pairs * self.headroom) + 1024)
+        return pairs
+
+    def status(self) -> B.GsStatus:
+        return B.read_status(self.ws)
+
+    # -- passes --------------------------------------------------------------------------
+    def forward(self, mean_rho, scale, quat, out: torch.Tensor | None = None) -> torch.Tensor:
+        mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
+        n = mean_rho.shape[0]
+        if self.ws is None or self.ws_n != n or self.capacity == 0:
+            self.ensure_capacity(mean_rho, scale, quat)
+        if out is None:
+            out = torch.empty((self.n_views, self.H, self.W), dtype=torch.float32, device=self.device)
+        B.check(B.lib().gs_project(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
+            self.W, self.H, ctypes.byref(self.opts), B.ptr(out), B.ptr(self.ws), self.ws.numel(),
+            B.stream_handle()), "gs_project")
+        self._fwd_token = self._token(mean_rho, scale, quat)
+        return out
+
+    def backward(self, mean_rho, scale, quat, dimg, grads=None, accumulate: bool = False,
+                 reuse: bool | None = None):
+        mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
+        dimg = dimg.contiguous()
+        n = mean_rho.shape[0]
+        if self.ws is None or self.ws_n != n or self.capacity == 0:
+            self.ensure_capacity(mean_rho, scale, quat)
+        if reuse is None:
+            reuse = self._fwd_token == self._token(mean_rho, scale, quat)
+        if grads is None:
+            grads = tuple(torch.empty_like(t) for t in (mean_rho, scale, quat))
+            accumulate = False
+        g_mr, g_sc, g_q = grads
+        B.check(B.lib().gs_project_backward(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
+            self.W, self.H, ctypes.byref(self.opts), B.ptr(dimg), B.ptr(g_mr), B.ptr(g_sc),
+            B.ptr(g_q), 1 if accumulate else 0, 1 if reuse else 0, B.ptr(self.ws),
+            self.ws.numel(), B.stream_handle()), "gs_project_backward")
+        return g_mr, g_sc, g_q
+
+    def count_evals(self, mean_rho, scale, quat) -> int:
+        """In-cut (pixel, Gaussian) evaluations of one forward (synchronises)."""
+        n = mean_rho.shape[0]
+        self.ensure_capacity(mean_rho, scale, quat)
+        B.check(B.lib().gs_project_count_evals(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
+            self.W, self.H, ctypes.byref(self.opts), B.ptr(self.ws), self.ws.numel(),
+            B.stream_handle()), "gs_project_count_evals")
+        self._fwd_token = None
+        return int(self.status().evals)
+
+    def read_pairs(self):
+        """Sorted (key, Gaussian) lists of the last binning (synchronises)."""
+        st = self.status()
+        n = int(st.pairs)
+        keys = np.zeros(max(n, 1), dtype=np.uint32)
+        vals = np.zeros(max(n, 1), dtype=np.uint32)
+        cnt = ctypes.c_int64(0)
+        B.check(B.lib().gs_read_pairs(B.ptr(self.ws), self.ws.numel(), B.stream_handle(), n,
+                                      keys.ctypes.data_as(ctypes.c_void_p),
+                                      vals.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)),
+                "gs_read_pairs")
+        return keys[:n], vals[:n]
+
+    @staticmethod
+    def _token(*ts):
+        return tuple((t.data_ptr(), t._version) for t in ts)
+
+
+class ProjectFunction(torch.autograd.Function):
+    """img = Project(mean_rho, scale, quat) with the hand-written backward kernels."""
+
+    @staticmethod
+    def forward(ctx, mean_rho, scale, quat, projector: Projector):
+        img = projector.forward(mean_rho, scale, quat)
+        ctx.save_for_backward(mean_rho, scale, quat)
+        ctx.projector = projector
+        return img
+
+    @staticmethod
+    def backward(ctx, dimg):
+        mean_rho, scale, quat = ctx.saved_tensors
+        g = ctx.projector.backward(mean_rho, scale, quat, dimg)
+        return g[0], g[1], g[2], None
+
+
+def project(mean_rho, scale, quat, projector: Projector):
+    return ProjectFunction.apply(mean_rho, scale, quat, projector)

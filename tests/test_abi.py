@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads, and
+exports every function include/*.h declares; struct layouts agree; argument errors are caught
+on the host before any launch."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2604_01844_gb300 import build
+
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(gs_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(built):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(built)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_binding_covers_header(built):
+    from paper_2604_01844_gb300 import binding
+
+    assert declared_functions() <= set(binding.SIGNATURES)
+
+
+def test_build_arch_and_version(built):
+    from paper_2604_01844_gb300 import binding
+
+    L = binding.lib()
+    assert L.gs_build_arch() == 103
+    assert b"sm_103a" in L.gs_version()
+
+
+def test_struct_layouts():
+    import numpy as np
+
+    import synth
+    from paper_2604_01844_gb300 import binding
+
+    assert binding.VIEW_DTYPE.itemsize == 64 and synth.VIEW_DTYPE == binding.VIEW_DTYPE
+    assert np.dtype(synth.GRID_DTYPE).itemsize == ctypes.sizeof(binding.GsGrid)
+
+
+def test_workspace_size_arithmetic(built):
+    from paper_2604_01844_gb300 import binding
+
+    L = binding.lib()
+    o = binding.opts(tile=16)
+    a = L.gs_project_workspace_size(1000, 8, 64, 64, ctypes.byref(o), 0)
+    b = L.gs_project_workspace_size(1000, 8, 64, 64, ctypes.byref(o), 100000)
+    assert a > 0 and b >= a + 100000 * 16
+    bad = binding.opts(tile=12)
+    assert L.gs_project_workspace_size(1000, 8, 64, 64, ctypes.byref(bad), 0) == 0
+    g = binding.GsGrid()
+    for k in range(3):
+        g.dims[k], g.origin[k], g.voxel[k] = 64, -1.0, 2 / 64
+    lo, dim = binding.i3((0, 0, 0)), binding.i3((64, 64, 64))
+    assert L.gs_voxelize_workspace_size(1000, ctypes.byref(g), lo, dim, ctypes.byref(o), 0) > 0
+    dim_bad = binding.i3((65, 64, 64))
+    assert L.gs_voxelize_workspace_size(1000, ctypes.byref(g), lo, dim_bad, ctypes.byref(o), 0) == 0
+
+
+def test_argument_errors_are_host_side(built):
+    from paper_2604_01844_gb300 import binding
+
+    L = binding.lib()
+    o = binding.opts()
+    # null parameter pointers with n > 0
+    rc = L.gs_project(None, None, None, 10, None, 1, 8, 8, ctypes.byref(o), None, None, 0, None)
+    assert rc == binding.GS_ERR_ARG
+    # misaligned workspace pointer
+    rc = L.gs_project(16, 16, 16, 10, 16, 1, 8, 8, ctypes.byref(o), 16, 17, 1 << 20, None)
+    assert rc == binding.GS_ERR_ARG
