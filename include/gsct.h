@@ -113,6 +113,9 @@ int gs_read_status(const void* d_ws, void* stream, gs_status* h_out);
 /* Last CUDA error string recorded by a failing call of this library (thread-local). */
 const char* gs_last_error(void);
 
+/* Asynchronous byte fill of a device buffer (e.g. zeroing a loss accumulator). */
+int gs_memset(void* d_ptr, int value, size_t bytes, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * X-ray rasterizer (Sec. 3.2, 3.5; Eq. 3, Eq. 4)
  * ------------------------------------------------------------------------------------- */
@@ -195,6 +198,64 @@ int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const
                             int n, const gs_grid* grid, const int32_t roi_lo[3],
                             const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
                             size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Loss terms of the reconstruction objective (Eq. 5) and of the volume fit (Eq. 6), each a
+ * fused forward + backward.  d_loss (one device float) is INCREMENTED by the weighted loss
+ * value (atomics; the caller zeroes it); d_grad is overwritten with weight * dL/d(first
+ * input), or incremented when accumulate = 1.  All arrays are device float arrays.
+ * ------------------------------------------------------------------------------------- */
+
+/* L1 term: weight * mean |a - b| over n elements; gradient weight * sign(a - b) / n
+ * (sign(0) = 0).  a, b, grad 16-byte aligned.  d_loss or d_grad may be NULL. */
+int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, float* d_loss,
+               float* d_grad, int accumulate, void* stream);
+
+/* 3D total variation of Eq. 5: weight * (sum of |forward differences| along x, y and z where
+ * the neighbour exists) / (nx ny nz), volume [z][y][x]; sub-gradient with sign(0) = 0. */
+int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,
+                 float* d_grad, int accumulate, void* stream);
+
+/* Scratch bytes of the SSIM losses for n_elems image pixels or volume voxels. */
+size_t gs_ssim_workspace_size(int64_t n_elems);
+
+/* D-SSIM term of Eq. 5: weight * (1 - mean SSIM(x, y)) over n_img images of H x W, SSIM of
+ * Wang et al. 2004 with an 11 x 11 Gaussian window (sigma 1.5), zero-padded 'same'
+ * filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = data_range.  Gradient w.r.t. x. */
+int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, float data_range,
+                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
+                   size_t ws_bytes, void* stream);
+
+/* 3D SSIM term of Eq. 6 over a volume [z][y][x] with an 11 x 11 x 11 window; each thread
+ * walks one z-row with a ring buffer of filtered planes (Sec. 3.5). */
+int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
+                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
+                   size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Optimiser.  The paper names none; Adam on raw parameters with activations: mean raw,
+ * density = softplus(raw), scale = exp(raw) (log-scale clamped to [min, max]), quaternion raw.
+ * ------------------------------------------------------------------------------------- */
+typedef struct gs_adam_opts {
+  float lr_mean, lr_rho, lr_scale, lr_quat;
+  float beta1, beta2, eps;
+  float min_log_scale, max_log_scale;
+  float pad[3];
+} gs_adam_opts;
+
+/* One Adam step.  Raw parameters (float4[n] each) are updated in place; d_m, d_v hold the
+ * moments (3 float4 per Gaussian each, zero-initialised by the caller); gradients are those of
+ * the activated parameters (as produced by the backward calls); the activated arrays are
+ * rewritten.  d_step (device int, 0 before the first step) supplies the bias-correction step
+ * count and is incremented on the device, so the call can be replayed in a CUDA graph. */
+int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, float* d_m,
+                 float* d_v, const float* d_g_mean_rho, const float* d_g_scale,
+                 const float* d_g_quat, float* d_mean_rho, float* d_scale, float* d_quat, int n,
+                 int* d_step, const gs_adam_opts* opts, void* stream);
+
+/* Activated parameters from raw ones (same activations as gs_adam_step). */
+int gs_activate(const float* d_raw_mean_rho, const float* d_raw_scale, const float* d_raw_quat,
+                float* d_mean_rho, float* d_scale, float* d_quat, int n, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Binning internals exposed for testing: the sorted (key, Gaussian) lists of the last

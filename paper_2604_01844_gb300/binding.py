@@ -39,7 +39,16 @@ class GsStatus(ctypes.Structure):
                 ("reserved", ctypes.c_int64 * 28)]
 
 
+class GsAdamOpts(ctypes.Structure):
+    _fields_ = [("lr_mean", ctypes.c_float), ("lr_rho", ctypes.c_float),
+                ("lr_scale", ctypes.c_float), ("lr_quat", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("min_log_scale", ctypes.c_float), ("max_log_scale", ctypes.c_float),
+                ("pad", ctypes.c_float * 3)]
+
+
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
+assert ctypes.sizeof(GsAdamOpts) == 48
 assert ctypes.sizeof(GsStatus) == 256
 
 _lib = None
@@ -54,6 +63,7 @@ SIGNATURES = {
     "gs_build_arch": (_I, []),
     "gs_read_status": (_I, [_P, _P, ctypes.POINTER(GsStatus)]),
     "gs_last_error": (ctypes.c_char_p, []),
+    "gs_memset": (_I, [_P, _I, _SZ, _P]),
     "gs_project_workspace_size": (_SZ, [_I, _I, _I, _I, _OPTS, _I64]),
     "gs_project_count_pairs": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _SZ, _P,
                                     ctypes.POINTER(ctypes.c_int64)]),
@@ -69,6 +79,16 @@ SIGNATURES = {
                                   _I, _P, _SZ, _P]),
     "gs_voxelize_count_evals": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P]),
     "gs_read_pairs": (_I, [_P, _SZ, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "gs_l1_loss": (_I, [_P, _P, _I64, ctypes.c_float, _P, _P, _I, _P]),
+    "gs_tv3d_loss": (_I, [_P, _I, _I, _I, ctypes.c_float, _P, _P, _I, _P]),
+    "gs_ssim_workspace_size": (_SZ, [_I64]),
+    "gs_ssim2d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
+                            _SZ, _P]),
+    "gs_ssim3d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
+                            _SZ, _P]),
+    "gs_adam_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P,
+                          ctypes.c_void_p, _P]),
+    "gs_activate": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
     "gs_timing_enable": (None, [_I]),
     "gs_timing_reset": (None, []),
     "gs_timing_read": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),

@@ -89,6 +89,13 @@ int gs_build_arch(void) {
 
 const char* gs_last_error(void) { return gs::t_err; }
 
+int gs_memset(void* d_ptr, int value, size_t bytes, void* stream) {
+  if (!d_ptr && bytes) return GS_ERR_ARG;
+  if (!bytes) return GS_OK;
+  GS_CUDA(cudaMemsetAsync(d_ptr, value, bytes, (cudaStream_t)stream));
+  return GS_OK;
+}
+
 int gs_read_status(const void* d_ws, void* stream, gs_status* h_out) {
   if (!d_ws || !h_out) return GS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

@@ -1,0 +1,126 @@
+"""One optimisation step of Gaussian-splatting CT reconstruction (Eq. 5, Fig. 2 loop) through
+libgsct calls only: project -> L1 + D-SSIM (fused fwd/bwd) -> per-Gaussian backward ->
+voxelize -> TV (fused) -> voxelizer backward (accumulated) -> Adam with activations.
+
+PyTorch only allocates the device buffers and provides the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .projector import Projector
+from .voxelizer import Voxelizer
+
+
+@dataclass
+class ReconConfig:
+    alpha_ssim: float = 0.25   # Eq. 5 weights; the paper gives no values
+    alpha_tv: float = 0.05
+    lr_mean: float = 2e-4
+    lr_rho: float = 1e-2
+    lr_scale: float = 5e-3
+    lr_quat: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    min_log_scale: float = math.log(1e-4)
+    max_log_scale: float = math.log(0.5)
+    tile: int = 16
+    cut: float = 3.0
+    tv_roi: tuple | None = None  # (lo, dim) of the TV region; None = whole grid
+
+
+def inverse_softplus(x: np.ndarray) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x > 20, x, np.log(np.expm1(np.maximum(x, 1e-12))))
+
+
+class Reconstruction:
+    """Holds the device state of one reconstruction: raw and activated parameters, Adam
+    moments, the target projections, the workspaces and the loss accumulator."""
+
+    def __init__(self, views, W, H, target: torch.Tensor, grid, mean_rho, scale, quat,
+                 cfg: ReconConfig = ReconConfig(), device="cuda", data_range: float | None = None):
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.n = int(mean_rho.shape[0])
+        dev = self.device
+        mr = np.asarray(mean_rho, dtype=np.float64)
+        sc = np.asarray(scale, dtype=np.float64)
+        raw_mr = np.concatenate([mr[:, :3], inverse_softplus(mr[:, 3])[:, None]], 1)
+        raw_sc = np.concatenate([np.log(np.maximum(sc[:, :3], 1e-12)), np.zeros((self.n, 1))], 1)
+        self.raw = [torch.from_numpy(a.astype(np.float32)).to(dev)
+                    for a in (raw_mr, raw_sc, np.asarray(quat, dtype=np.float32))]
+        self.act = [torch.empty_like(t) for t in self.raw]
+        self.grads = [torch.zeros_like(t) for t in self.raw]
+        self.m = torch.zeros((3 * self.n, 4), dtype=torch.float32, device=dev)
+        self.v = torch.zeros_like(self.m)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.target = target.contiguous()
+        self.W, self.H = int(W), int(H)
+        self.projector = Projector(views, W, H, cut=cfg.cut, tile=cfg.tile, device=dev)
+        if cfg.tv_roi is None:
+            self.voxelizer = Voxelizer(grid, cut=cfg.cut, device=dev)
+        else:
+            self.voxelizer = Voxelizer(grid, cfg.tv_roi[0], cfg.tv_roi[1], cut=cfg.cut, device=dev)
+        self.img = torch.empty_like(self.target)
+        self.dimg = torch.empty_like(self.target)
+        self.vol = torch.empty(self.voxelizer.shape, dtype=torch.float32, device=dev)
+        self.dvol = torch.empty_like(self.vol)
+        self.ssim_ws = torch.empty(B.lib().gs_ssim_workspace_size(self.target.numel()),
+                                   dtype=torch.uint8, device=dev)
+        self.data_range = float(data_range if data_range is not None else float(self.target.max()))
+        o = B.GsAdamOpts()
+        o.lr_mean, o.lr_rho, o.lr_scale, o.lr_quat = cfg.lr_mean, cfg.lr_rho, cfg.lr_scale, cfg.lr_quat
+        o.beta1, o.beta2, o.eps = cfg.beta1, cfg.beta2, cfg.eps
+        o.min_log_scale, o.max_log_scale = cfg.min_log_scale, cfg.max_log_scale
+        self.adam_opts = o
+        self.activate()
+        self.plan()
+
+    def activate(self):
+        L = B.lib()
+        B.check(L.gs_activate(*[B.ptr(t) for t in self.raw], *[B.ptr(t) for t in self.act],
+                              self.n, B.stream_handle()), "gs_activate")
+
+    def plan(self):
+        """Size both workspaces for the current parameters (synchronous)."""
+        self.projector.ensure_capacity(*self.act)
+        self.voxelizer.ensure_capacity(*self.act)
+
+    def step(self):
+        """One full iteration; the loss lands in self.loss (device), no host synchronisation."""
+        L = B.lib()
+        s = B.stream_handle()
+        cfg = self.cfg
+        B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
+        self.projector.forward(*self.act, out=self.img)
+        n_img = self.img.numel()
+        B.check(L.gs_l1_loss(B.ptr(self.img), B.ptr(self.target), n_img, 1.0, B.ptr(self.loss),
+                             B.ptr(self.dimg), 0, s), "gs_l1_loss")
+        if cfg.alpha_ssim > 0:
+            B.check(L.gs_ssim2d_loss(B.ptr(self.img), B.ptr(self.target), self.img.shape[0],
+                                     self.H, self.W, self.data_range, cfg.alpha_ssim,
+                                     B.ptr(self.loss), B.ptr(self.dimg), 1, B.ptr(self.ssim_ws),
+                                     self.ssim_ws.numel(), s), "gs_ssim2d_loss")
+        self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=False,
+                                reuse=True)
+        if cfg.alpha_tv > 0:
+            self.voxelizer.forward(*self.act, out=self.vol)
+            dz, dy, dx = self.vol.shape
+            B.check(L.gs_tv3d_loss(B.ptr(self.vol), dx, dy, dz, cfg.alpha_tv, B.ptr(self.loss),
+                                   B.ptr(self.dvol), 0, s), "gs_tv3d_loss")
+            self.voxelizer.backward(*self.act, self.dvol, grads=self.grads, accumulate=True,
+                                    reuse=True)
+        B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
+                               *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
+                               self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
+                "gs_adam_step")
+        return self.loss

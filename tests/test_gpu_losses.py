@@ -1,0 +1,158 @@
+"""Parity of the fused loss kernels (Eq. 5, Eq. 6) and the Adam step with the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import losses as OL
+from oracle import optim as OO
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01844_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _s():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _run_loss(B, name, x, y, *extra, ws=None, weight=1.0, accumulate_into=None):
+    L = B.lib()
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    yd = torch.from_numpy(y.astype(np.float32)).cuda() if y is not None else None
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros_like(xd) if accumulate_into is None else \
+        torch.from_numpy(accumulate_into.astype(np.float32)).cuda()
+    acc = 0 if accumulate_into is None else 1
+    if name == "l1":
+        rc = L.gs_l1_loss(B.ptr(xd), B.ptr(yd), xd.numel(), weight, B.ptr(loss), B.ptr(grad), acc, _s())
+    elif name == "tv":
+        dz, dy, dx = x.shape
+        rc = L.gs_tv3d_loss(B.ptr(xd), dx, dy, dz, weight, B.ptr(loss), B.ptr(grad), acc, _s())
+    elif name == "ssim2d":
+        wsb = torch.empty(L.gs_ssim_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
+        n, H, W = x.shape
+        rc = L.gs_ssim2d_loss(B.ptr(xd), B.ptr(yd), n, H, W, extra[0], weight, B.ptr(loss),
+                              B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
+    else:
+        wsb = torch.empty(L.gs_ssim_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
+        dz, dy, dx = x.shape
+        rc = L.gs_ssim3d_loss(B.ptr(xd), B.ptr(yd), dx, dy, dz, extra[0], weight, B.ptr(loss),
+                              B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
+    B.check(rc, name)
+    torch.cuda.synchronize()
+    return float(loss.item()), grad.cpu().numpy().astype(np.float64)
+
+
+def _x32(a):
+    return a.astype(np.float32).astype(np.float64)
+
+
+def test_l1(B):
+    rng = np.random.default_rng(0)
+    x, y = _x32(rng.standard_normal(100003)), _x32(rng.standard_normal(100003))
+    val, g = _run_loss(B, "l1", x, y, weight=0.7)
+    want, gw = OL.value_and_grad(lambda a, b: 0.7 * OL.l1(a, b), x, y)
+    assert abs(val - want) <= 1e-5 * abs(want)
+    np.testing.assert_allclose(g, gw, rtol=1e-6, atol=1e-12)
+    val2, g2 = _run_loss(B, "l1", x, y, weight=0.7, accumulate_into=np.ones_like(x))
+    np.testing.assert_allclose(g2, gw + 1.0, rtol=1e-6, atol=1e-7)
+
+
+def test_tv3d(B):
+    rng = np.random.default_rng(1)
+    v = _x32(rng.random((13, 17, 20)))
+    val, g = _run_loss(B, "tv", v, None, weight=0.3)
+    want, gw = OL.value_and_grad(lambda a: 0.3 * OL.tv3d(a), v)
+    assert abs(val - want) <= 1e-5 * abs(want)
+    np.testing.assert_allclose(g, gw, rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("shape", [(3, 37, 53), (2, 64, 64), (1, 5, 7)])
+def test_ssim2d(B, shape):
+    rng = np.random.default_rng(2)
+    y = _x32(rng.random(shape))
+    x = _x32(np.clip(y + 0.1 * rng.standard_normal(shape), 0, None))
+    L = float(y.max())
+    val, g = _run_loss(B, "ssim2d", x, y, L, weight=0.25)
+    want, gw = OL.value_and_grad(lambda a, b: 0.25 * (1 - OL.ssim2d(a, b, L)), x, y)
+    assert abs(val - want) <= 2e-5 * max(1.0, abs(want)), (val, want)
+    scale = np.abs(gw).max()
+    assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
+
+
+@pytest.mark.parametrize("shape", [(21, 19, 35), (12, 16, 16)])
+def test_ssim3d(B, shape):
+    rng = np.random.default_rng(3)
+    y = _x32(rng.random(shape))
+    x = _x32(np.clip(y + 0.1 * rng.standard_normal(shape), 0, None))
+    L = float(y.max())
+    val, g = _run_loss(B, "ssim3d", x, y, L, weight=0.5)
+    want, gw = OL.value_and_grad(lambda a, b: 0.5 * (1 - OL.ssim3d(a, b, L)), x, y)
+    assert abs(val - want) <= 2e-5 * max(1.0, abs(want)), (val, want)
+    scale = np.abs(gw).max()
+    assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
+
+
+def test_adam_matches_oracle(B):
+    rng = np.random.default_rng(4)
+    n = 1000
+    raw = [_x32(rng.standard_normal((n, 4))) for _ in range(3)]
+    raw[1][:, 3] = 0
+    raw[1][:, :3] = np.log(0.02) + 0.3 * raw[1][:, :3]
+    o = B.GsAdamOpts()
+    o.lr_mean, o.lr_rho, o.lr_scale, o.lr_quat = 1e-3, 1e-2, 5e-3, 2e-3
+    o.beta1, o.beta2, o.eps = 0.9, 0.999, 1e-15
+    o.min_log_scale, o.max_log_scale = np.log(1e-4), np.log(0.5)
+    d_raw = [torch.from_numpy(a.astype(np.float32)).cuda() for a in raw]
+    d_act = [torch.empty_like(t) for t in d_raw]
+    m = torch.zeros((3 * n, 4), device="cuda")
+    v = torch.zeros_like(m)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    om = [np.zeros((n, 4)) for _ in range(3)]
+    ov = [np.zeros((n, 4)) for _ in range(3)]
+    cur = [a.copy() for a in raw]
+    for t in range(1, 4):
+        gr = [_x32(rng.standard_normal((n, 4))) for _ in range(3)]
+        gr[1][:, 3] = 0
+        d_g = [torch.from_numpy(a.astype(np.float32)).cuda() for a in gr]
+        B.check(B.lib().gs_adam_step(*[B.ptr(x) for x in d_raw], B.ptr(m), B.ptr(v),
+                                     *[B.ptr(x) for x in d_g], *[B.ptr(x) for x in d_act], n,
+                                     B.ptr(step), ctypes.byref(o), _s()), "adam")
+        cur = OO.adam_step(cur, om, ov, gr, t, (1e-3, 1e-2, 5e-3, 2e-3), 0.9, 0.999, 1e-15,
+                           np.log(1e-4), np.log(0.5))
+    torch.cuda.synchronize()
+    assert int(step.item()) == 3
+    for a, b in zip(d_raw, cur):
+        np.testing.assert_allclose(a.cpu().numpy(), b, rtol=2e-5, atol=2e-6)
+    act = OO.activate(*cur)
+    for a, b in zip(d_act, act):
+        np.testing.assert_allclose(a.cpu().numpy(), b, rtol=2e-5, atol=2e-6)
+
+
+def test_recon_step_decreases_loss(B):
+    """A small reconstruction (projections of a second Gaussian set as the target): the loss
+    falls over the first iterations and the step's gradient equals the sum of its parts."""
+    import synth
+    import paper_2604_01844_gb300 as g
+    from paper_2604_01844_gb300.recon import ReconConfig, Reconstruction
+
+    views = synth.cone_views(8, 64, 64)
+    model = synth.gaussians(30, 1500, scale_median=0.03)
+    tgt = synth.gaussians(31, 1500, scale_median=0.03)
+    target = g.Projector(views, 64, 64).forward(*[torch.from_numpy(a).cuda() for a in tgt])
+    rec = Reconstruction(views, 64, 64, target.clone(), synth.cube_grid(48), *model,
+                         cfg=ReconConfig(lr_mean=1e-3, lr_rho=2e-2))
+    losses = []
+    for _ in range(30):
+        losses.append(float(rec.step().item()))
+    assert losses[-1] < 0.8 * losses[0], losses[::5]

@@ -559,3 +559,22 @@ def test_tv_ramp_and_psnr():
     gt = torch.zeros(10, dtype=torch.float64); gt[0] = 2.0
     est = gt.clone(); est[1] = 0.1
     assert abs(losses.psnr(est, gt) - 10 * math.log10(4 / (0.01 / 10))) < 1e-12
+
+
+def test_adam_reference_special_cases():
+    """With beta1 = beta2 = 0 and no bias correction left, Adam moves every raw parameter by
+    lr * g / (|g| + eps); the activations are softplus/exp as stated."""
+    from oracle import optim as OO
+    rng = np.random.default_rng(0)
+    raw = [rng.standard_normal((5, 4)) for _ in range(3)]
+    raw[1][:, 3] = 0
+    g = [rng.standard_normal((5, 4)) for _ in range(3)]
+    m = [np.zeros((5, 4)) for _ in range(3)]
+    v = [np.zeros((5, 4)) for _ in range(3)]
+    out = OO.adam_step(raw, m, v, g, 1, (0.1, 0.2, 0.3, 0.4), 0.0, 0.0, 0.0, -50, 50)
+    graw_q = g[2]
+    np.testing.assert_allclose(out[2], raw[2] - 0.4 * np.sign(graw_q), atol=1e-12)
+    np.testing.assert_allclose(out[0][:, :3], raw[0][:, :3] - 0.1 * np.sign(g[0][:, :3]), atol=1e-12)
+    mr, sc, q = OO.activate(*raw)
+    np.testing.assert_allclose(mr[:, 3], np.log1p(np.exp(raw[0][:, 3])), rtol=1e-12)
+    np.testing.assert_allclose(sc[:, :3], np.exp(raw[1][:, :3]), rtol=1e-12)
