@@ -31,6 +31,9 @@ WORKLOAD = {
     "views": 75, "W": 512, "H": 512, "gaussians": 50000, "tv_volume": 256, "tile": 16,
     "model_seed": 21, "target_seed": 22, "scale_median": 0.012, "scale_sigma_log": 0.4,
 }
+# a reduced case of the same kernels for profiler captures (16 views, 128^3 TV volume)
+SMALL = dict(WORKLOAD, workload="recon step, 16 cone views x 512^2, 50k Gaussians, TV on 128^3",
+             views=16, tv_volume=128)
 METRIC = "Gaussian-pixel evals/s (fwd+bwd step) at 75x512^2"
 UNIT = "evals/s"
 
@@ -388,7 +391,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["recon512", "small"], default="recon512",
+                    help="small: 16-view case of the same kernels, for profiler captures")
     args = ap.parse_args()
+    if args.workload == "small":
+        WORKLOAD.clear()
+        WORKLOAD.update(SMALL)
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
