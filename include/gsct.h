@@ -226,6 +226,28 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of gs_ssim2d_loss.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory themselves -- for instance a host
+ * framework that owns the whole device memory budget and hands none to plug-ins, or a
+ * latency-critical loop where an allocation's implicit device synchronisation is not
+ * acceptable.  Such a caller passes only its inputs and outputs: the scratch (three per-pixel
+ * maps) lives in a fixed device array inside the library, GS_SSIM2D_NOALLOC_MAX_PIXELS floats
+ * x 3 (24 MiB), which every device that loads the library keeps until the process exits.
+ *   - n_img * H * W above GS_SSIM2D_NOALLOC_MAX_PIXELS returns GS_ERR_CAPACITY (message in
+ *     gs_last_error) before any launch.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and caches it; make that first call before any stream
+ *     capture.  The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ *     routine).
+ *   - All calls share the one array, which keeps the last call's contents; every entry a call
+ *     reads it writes first, so nothing needs clearing.  Calls whose kernels overlap on the
+ *     GPU (e.g. on two streams at once) race on the array: serialise them.
+ * Results equal gs_ssim2d_loss's. */
+#define GS_SSIM2D_NOALLOC_MAX_PIXELS (1 << 21)
+int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H, int W,
+                           float data_range, float weight, float* d_loss, float* d_grad,
+                           int accumulate, void* stream);
+
 /* 3D SSIM term of Eq. 6 over a volume [z][y][x] with an 11 x 11 x 11 window; each thread
  * walks one z-row with a ring buffer of filtered planes (Sec. 3.5). */
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,

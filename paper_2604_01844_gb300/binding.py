@@ -86,6 +86,8 @@ SIGNATURES = {
                             _SZ, _P]),
     "gs_ssim3d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
                             _SZ, _P]),
+    "gs_ssim2d_loss_noalloc": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P,
+                                    _I, _P]),
     "gs_adam_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P,
                           ctypes.c_void_p, _P]),
     "gs_activate": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),

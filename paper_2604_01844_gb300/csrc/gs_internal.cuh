@@ -13,6 +13,7 @@ namespace gs {
 // ------------------------------------------------------------------------------------------
 void note_launch(const char* name, cudaStream_t s, bool begin);
 void set_last_error(const char* where, cudaError_t e);
+void set_last_error_msg(const char* msg);
 int num_sms();
 
 // Launch a kernel, counting it and (when timing is on) bracketing it with CUDA events on its

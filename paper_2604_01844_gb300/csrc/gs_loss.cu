@@ -14,6 +14,7 @@
 //            activations applied in the same pass.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -513,6 +514,70 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
   const float gscale = -weight / (float)plane;
   dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, n_img), block(kTile, kTile);
   float* maps = (float*)d_ws;
+  GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
+                d_loss, maps, plane));
+  return launch("ssim2d_bwd", k_ssim2d_bwd, grid, block, 0, s, d_x, d_y, H, W,
+                (const float*)maps, plane, d_grad, accumulate);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// SSIM 2D with a fixed scratch buffer, for callers that cannot allocate device memory.
+// The three per-pixel derivative maps live in this file-scope device array instead of a
+// caller workspace.  Every device that loads the library holds it (24 MiB) until the process
+// exits.
+// ------------------------------------------------------------------------------------------
+static __device__ __align__(256) float g_ssim2d_scratch[3 * (size_t)GS_SSIM2D_NOALLOC_MAX_PIXELS];
+
+namespace {
+std::mutex g_scratch_mu;
+float* g_scratch_addr[64] = {nullptr};
+
+// Device address of g_ssim2d_scratch on the current device.  The symbol's host-side name is
+// only a stand-in, so the address is looked up once per device (with that device current)
+// and cached.
+int ssim2d_scratch(float** out) {
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_ssim2d_scratch);
+    if (e != cudaSuccess || !p) {
+      gs::set_last_error("cudaGetSymbolAddress(g_ssim2d_scratch)", e);
+      return GS_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = (float*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return GS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H, int W,
+                           float data_range, float weight, float* d_loss, float* d_grad,
+                           int accumulate, void* stream) {
+  if (!d_x || !d_y || !d_grad || n_img < 1 || H < 1 || W < 1 || !(data_range > 0.f))
+    return GS_ERR_ARG;
+  if (n_img > 65535) return GS_ERR_ARG;
+  const int64_t plane = (int64_t)n_img * H * W;
+  if (plane > (int64_t)GS_SSIM2D_NOALLOC_MAX_PIXELS) {
+    gs::set_last_error_msg("gs_ssim2d_loss_noalloc: n_img * H * W exceeds "
+                           "GS_SSIM2D_NOALLOC_MAX_PIXELS (2097152)");
+    return GS_ERR_CAPACITY;
+  }
+  float* maps = nullptr;
+  GS_TRY(ssim2d_scratch(&maps));
+  cudaStream_t s = (cudaStream_t)stream;
+  const float C1 = (0.01f * data_range) * (0.01f * data_range);
+  const float C2 = (0.03f * data_range) * (0.03f * data_range);
+  const float gscale = -weight / (float)plane;
+  dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, n_img), block(kTile, kTile);
+  // kernel 1 writes every map entry kernel 2 reads, so the array needs no clearing between calls
   GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
                 d_loss, maps, plane));
   return launch("ssim2d_bwd", k_ssim2d_bwd, grid, block, 0, s, d_x, d_y, H, W,

@@ -60,6 +60,8 @@ void set_last_error(const char* where, cudaError_t e) {
   snprintf(t_err, sizeof(t_err), "%s: %s", where, cudaGetErrorString(e));
 }
 
+void set_last_error_msg(const char* msg) { snprintf(t_err, sizeof(t_err), "%s", msg); }
+
 int num_sms() {
   static int cached[64] = {0};
   int dev = 0;
