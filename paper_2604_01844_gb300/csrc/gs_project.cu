@@ -356,13 +356,15 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
                  const short4* __restrict__ rect, int n, int W, int H, int TW, int TH,
                  float* __restrict__ img, gs_status* st) {
   using S = RasterShape<T>;
+  constexpr int BH = T / 4;  // 8x4 warp blocks per tile column
   __shared__ float4 s_geo[S::NT];
   __shared__ float4 s_con[S::NT];
-  __shared__ short4 s_rect[S::NT];
+  __shared__ uint32_t s_mask[S::NT];  // bit b: the record's box touches warp block b
   __shared__ unsigned long long s_cnt;
   if (st->code != GS_OK) return;
   const int tile = blockIdx.x, v = blockIdx.y;
   const int tx = tile % TW, ty = tile / TW;
+  const int tx0 = tx * T, ty0 = ty * T;
   const uint2 r = ranges[(size_t)v * TH * TW + tile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int wx0[S::PIX], wy0[S::PIX];
@@ -385,24 +387,39 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
       const size_t rec = (size_t)v * n + vals[base + threadIdx.x];
       s_geo[threadIdx.x] = geo[rec];
       s_con[threadIdx.x] = conic[rec];
-      s_rect[threadIdx.x] = rect[rec];
+      // which 8x4 warp blocks of this tile the record's box touches
+      const short4 b = rect[rec];
+      const int bx0 = max(0, (b.x - tx0) >> 3), bx1 = min(S::BW - 1, (b.z - tx0) >> 3);
+      const int by0 = max(0, (b.y - ty0) >> 2), by1 = min(BH - 1, (b.w - ty0) >> 2);
+      uint32_t mask = 0u;
+      if (bx0 <= bx1) {
+        const uint32_t row = (2u << bx1) - (1u << bx0);
+        for (int by = by0; by <= by1; ++by) mask |= row << (by * S::BW);
+      }
+      s_mask[threadIdx.x] = mask;
     }
     __syncthreads();
-    for (int j = 0; j < m; ++j) {
-      const short4 b = s_rect[j];
-      const float4 g = s_geo[j];
-      const float4 c = s_con[j];
 #pragma unroll
-      for (int k = 0; k < S::PIX; ++k) {
-        // warp-uniform: skip records whose box misses this warp's 8x4 pixel block
-        if (b.z < wx0[k] || b.x > wx0[k] + 7 || b.w < wy0[k] || b.y > wy0[k] + 3) continue;
-        const float dx = fx[k] - g.x, dy = fy[k] - g.y;
-        const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, c.z * dy) * dy);
-        if (COUNT) {
-          cnt += (e > g.w && fx[k] < (float)W && fy[k] < (float)H) ? 1u : 0u;
-        } else {
-          const float val = ex2(e);
-          acc[k] = e > g.w ? fmaf(g.z, val, acc[k]) : acc[k];
+    for (int k = 0; k < S::PIX; ++k) {
+      const int wb = w + k * S::NW;
+      // each warp visits only the records that touch its block: a ballot over 32 records
+      // at a time, then one iteration per set bit
+      for (int j0 = 0; j0 < m; j0 += 32) {
+        const int jl = j0 + lane;
+        unsigned bits = __ballot_sync(0xffffffffu, jl < m && ((s_mask[jl] >> wb) & 1u));
+        while (bits) {
+          const int j = j0 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const float4 g = s_geo[j];
+          const float4 c = s_con[j];
+          const float dx = fx[k] - g.x, dy = fy[k] - g.y;
+          const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, c.z * dy) * dy);
+          if (COUNT) {
+            cnt += (e > g.w && fx[k] < (float)W && fy[k] < (float)H) ? 1u : 0u;
+          } else {
+            const float val = ex2(e);
+            acc[k] = e > g.w ? fmaf(g.z, val, acc[k]) : acc[k];
+          }
         }
       }
     }
@@ -423,7 +440,12 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
 }
 
 // ------------------------------------------------------------------------------------------
-// raster backward, per Gaussian: one warp per (Gaussian, tile) pair
+// raster backward, per Gaussian (Sec. 3.5): one thread per (Gaussian, tile) pair.  The thread
+// walks the rows of the pair's box inside the tile; on each row it solves the quadratic
+// exponent for the ellipse's chord, widened by one pixel on each side, and evaluates only
+// those pixels (with the forward's exact test e > e_cut, so both passes use the same mask).
+// The six moments are accumulated per row with dy factored out, then one pair of float4
+// atomics per pair: no warp reduction, no pixels outside the ellipse's chords.
 // ------------------------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(kThreads)
@@ -432,11 +454,7 @@ __global__ void __launch_bounds__(kThreads)
                  const short4* __restrict__ rect, int n, int W, int H, int TW, int TH,
                  const float* __restrict__ dimg, float4* __restrict__ fpgrad,
                  const gs_status* st) {
-  __shared__ float s_g[T * T];
-  __shared__ float4 s_geo[kThreads];
-  __shared__ float4 s_con[kThreads];
-  __shared__ short4 s_rect[kThreads];
-  __shared__ uint32_t s_idx[kThreads];
+  __shared__ float s_g[T][T + 1];
   if (st->code != GS_OK) return;
   const int tile = blockIdx.x, v = blockIdx.y;
   const uint2 r = ranges[(size_t)v * TH * TW + tile];
@@ -444,61 +462,50 @@ __global__ void __launch_bounds__(kThreads)
   const int tx0 = (tile % TW) * T, ty0 = (tile / TW) * T;
   for (int p = threadIdx.x; p < T * T; p += kThreads) {
     const int x = tx0 + p % T, y = ty0 + p / T;
-    s_g[p] = (x < W && y < H) ? dimg[((size_t)v * H + y) * W + x] : 0.f;
+    s_g[p / T][p % T] = (x < W && y < H) ? dimg[((size_t)v * H + y) * W + x] : 0.f;
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int lx = lane & 7, ly = lane >> 3;
-  for (uint32_t base = r.x; base < r.y; base += kThreads) {
-    const int m = (int)min((uint32_t)kThreads, r.y - base);
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-      const uint32_t i = vals[base + threadIdx.x];
-      const size_t rec = (size_t)v * n + i;
-      s_geo[threadIdx.x] = geo[rec];
-      s_con[threadIdx.x] = conic[rec];
-      s_rect[threadIdx.x] = rect[rec];
-      s_idx[threadIdx.x] = i;
-    }
-    __syncthreads();
-    for (int j = w; j < m; j += kThreads / 32) {
-      const short4 b = s_rect[j];
-      const int x0 = max((int)b.x, tx0), x1 = min((int)b.z, tx0 + T - 1);
-      const int y0 = max((int)b.y, ty0), y1 = min((int)b.w, ty0 + T - 1);
-      if (x0 > x1 || y0 > y1) continue;
-      const float4 g = s_geo[j];
-      const float4 c = s_con[j];
-      float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-      for (int yb = y0; yb <= y1; yb += 4) {
-        const int y = yb + ly;
-        for (int xb = x0; xb <= x1; xb += 8) {
-          const int x = xb + lx;
-          if (x <= x1 && y <= y1) {
-            const float dx = (float)x - g.x, dy = (float)y - g.y;
-            const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, c.z * dy) * dy);
-            if (e > g.w) {
-              const float G = s_g[(y - ty0) * T + (x - tx0)] * ex2(e);
-              const float Gx = G * dx, Gy = G * dy;
-              s0 += G;
-              sx += Gx;
-              sy += Gy;
-              sxx = fmaf(Gx, dx, sxx);
-              sxy = fmaf(Gx, dy, sxy);
-              syy = fmaf(Gy, dy, syy);
-            }
-          }
+  __syncthreads();
+  for (uint32_t p = r.x + threadIdx.x; p < r.y; p += kThreads) {
+    const size_t rec = (size_t)v * n + vals[p];
+    const short4 b = rect[rec];
+    const int x0 = max((int)b.x, tx0), x1 = min((int)b.z, tx0 + T - 1);
+    const int y0 = max((int)b.y, ty0), y1 = min((int)b.w, ty0 + T - 1);
+    if (x0 > x1 || y0 > y1) continue;
+    const float4 g = geo[rec];
+    const float4 c = conic[rec];  // exponent e = c.x dx^2 + c.y dx dy + c.z dy^2, c.x < 0
+    const float inv2a = 0.5f / c.x;
+    float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+    for (int y = y0; y <= y1; ++y) {
+      const float dy = (float)y - g.y;
+      const float B = c.y * dy, czdy = c.z * dy;
+      // chord of e(dx) = c.x dx^2 + B dx + czdy dy > e_cut
+      const float disc = B * B - 4.f * c.x * (czdy * dy - g.w);
+      if (!(disc > 0.f)) continue;
+      const float ctr = -B * inv2a, half = -sqrtf(disc) * inv2a;
+      const int xa = max(x0, (int)ceilf(g.x + ctr - half) - 1);
+      const int xb = min(x1, (int)floorf(g.x + ctr + half) + 1);
+      float r0 = 0.f, rx = 0.f, rxx = 0.f;
+      for (int x = xa; x <= xb; ++x) {
+        const float dx = (float)x - g.x;
+        const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, czdy) * dy);
+        if (e > g.w) {
+          const float G = s_g[y - ty0][x - tx0] * ex2(e);
+          const float Gx = G * dx;
+          r0 += G;
+          rx += Gx;
+          rxx = fmaf(Gx, dx, rxx);
         }
       }
-      s0 = gsd::warp_sum(s0);
-      sx = gsd::warp_sum(sx);
-      sy = gsd::warp_sum(sy);
-      sxx = gsd::warp_sum(sxx);
-      sxy = gsd::warp_sum(sxy);
-      syy = gsd::warp_sum(syy);
-      if (lane == 0) {
-        const size_t rec = (size_t)v * n + s_idx[j];
-        atomicAdd(&fpgrad[2 * rec], make_float4(s0, sx, sy, sxx));
-        atomicAdd(&fpgrad[2 * rec + 1], make_float4(sxy, syy, 0.f, 0.f));
-      }
+      s0 += r0;
+      sx += rx;
+      sxx += rxx;
+      sy = fmaf(dy, r0, sy);
+      sxy = fmaf(dy, rx, sxy);
+      syy = fmaf(dy * dy, r0, syy);
+    }
+    if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
+      atomicAdd(&fpgrad[2 * rec], make_float4(s0, sx, sy, sxx));
+      atomicAdd(&fpgrad[2 * rec + 1], make_float4(sxy, syy, 0.f, 0.f));
     }
   }
 }
