@@ -8,12 +8,14 @@
 //   emit         (key = view * tiles + tile, value = Gaussian) pairs in (view, Gaussian) order
 //   radix sort   stable, over the key bits in use
 //   ranges       [start, end) per (view, tile)
-//   raster_fwd   one CTA per (view, tile): footprint records staged through shared memory,
-//                each thread owns pixels and adds A * 2^(e) for e above the cut (additive, no
-//                depth order); warps skip records whose box misses their 8x4 pixel block
-//   raster_bwd   one CTA per (view, tile), one warp per (Gaussian, tile) pair: six moment
-//                sums of g * exp(-q/2) over the pair's pixels, warp-shuffle reduced, then one
-//                pair of float4 atomics (per-Gaussian backward, Sec. 3.5)
+//   raster_fwd   one CTA per (view, tile): footprint records staged through shared memory
+//                with a bitmask of the 8x4 warp blocks each record's box touches; each warp
+//                visits only its records (ballot + find-first-set), each thread owns pixels
+//                and adds A * 2^(e) for e above the cut (additive, no depth order)
+//   raster_bwd   one CTA per (view, tile), one thread per (Gaussian, tile) pair over the
+//                exact chords of its ellipse, pairs sorted by work per batch; six moment sums
+//                of g * exp(-q/2), then one pair of float4 atomics (per-Gaussian backward,
+//                Sec. 3.5)
 //   chain        one warp per Gaussian, lanes over views: moments -> footprint gradients ->
 //                d(mean, rho, scale, quaternion), reduced over views with shuffles
 #include <algorithm>
@@ -440,12 +442,17 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
 }
 
 // ------------------------------------------------------------------------------------------
-// raster backward, per Gaussian (Sec. 3.5): one thread per (Gaussian, tile) pair.  The thread
-// walks the rows of the pair's box inside the tile; on each row it solves the quadratic
-// exponent for the ellipse's chord, widened by one pixel on each side, and evaluates only
-// those pixels (with the forward's exact test e > e_cut, so both passes use the same mask).
-// The six moments are accumulated per row with dy factored out, then one pair of float4
-// atomics per pair: no warp reduction, no pixels outside the ellipse's chords.
+// raster backward, per Gaussian (Sec. 3.5): one thread per (Gaussian, tile) pair, in three
+// phases per batch of kThreads pairs of a tile:
+//   1. chords: for every row of the pair's box inside the tile, the pixel interval where the
+//      quadratic exponent exceeds the cut (solved in closed form, widened by 1/100 pixel so
+//      that it contains every pixel the forward's test accepts), stored in shared memory,
+//      and the pair's total work W (pixels on its chords);
+//   2. a counting sort of the batch by W (32 buckets, largest first), so that the 32 pairs of
+//      a warp carry nearly equal work;
+//   3. each thread walks its pair's chords row by row, re-testing e > e_cut exactly like the
+//      forward, and accumulates the six moments of g exp(-q/2) with dy factored out per row;
+//      one pair of float4 atomics per pair.  No warp reductions, no pixels off the chords.
 // ------------------------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(kThreads)
@@ -454,42 +461,108 @@ __global__ void __launch_bounds__(kThreads)
                  const short4* __restrict__ rect, int n, int W, int H, int TW, int TH,
                  const float* __restrict__ dimg, float4* __restrict__ fpgrad,
                  const gs_status* st) {
+  constexpr int kBuckets = 32;
+  constexpr uint16_t kEmpty = 0x0001;  // chord with start 1 > end 0
   __shared__ float s_g[T][T + 1];
+  __shared__ float4 s_geo[kThreads];
+  __shared__ float4 s_con[kThreads];
+  __shared__ uint16_t s_ch[T][kThreads];  // per row: start | end << 8, relative to the tile
+  __shared__ uint32_t s_rec[kThreads];
+  __shared__ uint16_t s_work[kThreads];
+  __shared__ uint8_t s_y0[kThreads];
+  __shared__ uint8_t s_y1[kThreads];
+  __shared__ uint16_t s_perm[kThreads];
+  __shared__ uint32_t s_hist[kBuckets];
   if (st->code != GS_OK) return;
   const int tile = blockIdx.x, v = blockIdx.y;
   const uint2 r = ranges[(size_t)v * TH * TW + tile];
   if (r.x == r.y) return;
   const int tx0 = (tile % TW) * T, ty0 = (tile / TW) * T;
-  for (int p = threadIdx.x; p < T * T; p += kThreads) {
+  const int t = threadIdx.x;
+  for (int p = t; p < T * T; p += kThreads) {
     const int x = tx0 + p % T, y = ty0 + p / T;
     s_g[p / T][p % T] = (x < W && y < H) ? dimg[((size_t)v * H + y) * W + x] : 0.f;
   }
-  __syncthreads();
-  for (uint32_t p = r.x + threadIdx.x; p < r.y; p += kThreads) {
-    const size_t rec = (size_t)v * n + vals[p];
-    const short4 b = rect[rec];
-    const int x0 = max((int)b.x, tx0), x1 = min((int)b.z, tx0 + T - 1);
-    const int y0 = max((int)b.y, ty0), y1 = min((int)b.w, ty0 + T - 1);
-    if (x0 > x1 || y0 > y1) continue;
-    const float4 g = geo[rec];
-    const float4 c = conic[rec];  // exponent e = c.x dx^2 + c.y dx dy + c.z dy^2, c.x < 0
-    const float inv2a = 0.5f / c.x;
+  for (uint32_t base = r.x; base < r.y; base += kThreads) {
+    const int m = (int)min((uint32_t)kThreads, r.y - base);
+    __syncthreads();
+    if (t < kBuckets) s_hist[t] = 0;
+    __syncthreads();
+    // phase 1: chords and work of pair t
+    if (t < m) {
+      const uint32_t rec = (uint32_t)v * (uint32_t)n + vals[base + t];
+      const short4 b = rect[rec];
+      const float4 g = geo[rec];
+      const float4 c = conic[rec];  // e = c.x dx^2 + c.y dx dy + c.z dy^2 with c.x < 0
+      s_rec[t] = rec;
+      s_geo[t] = g;
+      s_con[t] = c;
+      const int x0 = max((int)b.x, tx0) - tx0, x1 = min((int)b.z, tx0 + T - 1) - tx0;
+      const int y0 = max((int)b.y, ty0) - ty0, y1 = min((int)b.w, ty0 + T - 1) - ty0;
+      const float inv2a = 0.5f / c.x;
+      int work = 0, first = T, last = -1;
+      for (int yy = y0; yy <= y1; ++yy) {
+        uint16_t ch = kEmpty;
+        if (x0 <= x1) {
+          const float dy = (float)(ty0 + yy) - g.y;
+          const float B = c.y * dy;
+          const float disc = B * B - 4.f * c.x * (c.z * dy * dy - g.w);
+          if (disc > 0.f) {
+            const float ctr = g.x - (float)tx0 - B * inv2a, half = -sqrtf(disc) * inv2a;
+            const int xa = max(x0, (int)ceilf(ctr - half - 0.01f));
+            const int xb = min(x1, (int)floorf(ctr + half + 0.01f));
+            if (xa <= xb) {
+              ch = (uint16_t)(xa | (xb << 8));
+              work += xb - xa + 1;
+              first = min(first, yy);
+              last = yy;
+            }
+          }
+        }
+        s_ch[yy][t] = ch;
+      }
+      s_work[t] = (uint16_t)work;
+      s_y0[t] = (uint8_t)(first < T ? first : 0);
+      s_y1[t] = (uint8_t)(last >= 0 ? last : 0);
+      const int bucket = kBuckets - 1 - min(kBuckets - 1, (work * kBuckets) / (T * T + 1));
+      atomicAdd(&s_hist[bucket], 1u);
+    }
+    __syncthreads();
+    // phase 2: counting sort by work (descending)
+    if (t == 0) {
+      uint32_t a = 0;
+      for (int k = 0; k < kBuckets; ++k) {
+        const uint32_t cnt = s_hist[k];
+        s_hist[k] = a;
+        a += cnt;
+      }
+    }
+    __syncthreads();
+    if (t < m) {
+      const int work = s_work[t];
+      const int bucket = kBuckets - 1 - min(kBuckets - 1, (work * kBuckets) / (T * T + 1));
+      s_perm[atomicAdd(&s_hist[bucket], 1u)] = (uint16_t)t;
+    }
+    __syncthreads();
+    if (t >= m) continue;
+    // phase 3: walk pair j's chords row by row
+    const int j = s_perm[t];
+    const int work = s_work[j];
+    if (work == 0) continue;
+    const float4 g = s_geo[j];
+    const float4 c = s_con[j];
+    const int ya = s_y0[j], yb = s_y1[j];
     float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-    for (int y = y0; y <= y1; ++y) {
-      const float dy = (float)y - g.y;
-      const float B = c.y * dy, czdy = c.z * dy;
-      // chord of e(dx) = c.x dx^2 + B dx + czdy dy > e_cut
-      const float disc = B * B - 4.f * c.x * (czdy * dy - g.w);
-      if (!(disc > 0.f)) continue;
-      const float ctr = -B * inv2a, half = -sqrtf(disc) * inv2a;
-      const int xa = max(x0, (int)ceilf(g.x + ctr - half) - 1);
-      const int xb = min(x1, (int)floorf(g.x + ctr + half) + 1);
+    for (int yy = ya; yy <= yb; ++yy) {
+      const uint32_t ch = s_ch[yy][j];
+      const int xa = ch & 0xFF, xb = ch >> 8;
+      const float dy = (float)(ty0 + yy) - g.y, czdy = c.z * dy;
+      float dx = (float)(tx0 + xa) - g.x;
       float r0 = 0.f, rx = 0.f, rxx = 0.f;
-      for (int x = xa; x <= xb; ++x) {
-        const float dx = (float)x - g.x;
+      for (int x = xa; x <= xb; ++x, dx += 1.f) {
         const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, czdy) * dy);
         if (e > g.w) {
-          const float G = s_g[y - ty0][x - tx0] * ex2(e);
+          const float G = s_g[yy][x] * ex2(e);
           const float Gx = G * dx;
           r0 += G;
           rx += Gx;
@@ -504,8 +577,9 @@ __global__ void __launch_bounds__(kThreads)
       syy = fmaf(dy * dy, r0, syy);
     }
     if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
-      atomicAdd(&fpgrad[2 * rec], make_float4(s0, sx, sy, sxx));
-      atomicAdd(&fpgrad[2 * rec + 1], make_float4(sxy, syy, 0.f, 0.f));
+      const uint32_t rec = s_rec[j];
+      atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(s0, sx, sy, sxx));
+      atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(sxy, syy, 0.f, 0.f));
     }
   }
 }
