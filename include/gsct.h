@@ -280,6 +280,91 @@ int gs_activate(const float* d_raw_mean_rho, const float* d_raw_scale, const flo
                 float* d_mean_rho, float* d_scale, float* d_quat, int n, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Synthetic data: random-ellipsoid phantom (stands in for the paper's CT datasets).
+ * d_ell: device float[ne * 11], rows centre[3], semi-axes[3], quaternion (w, x, y, z),
+ * attenuation; ellipsoids add up where they overlap.
+ * ------------------------------------------------------------------------------------- */
+
+/* Exact line integrals (attenuation x chord length) through every pixel centre of every view
+ * (same pixel convention as gs_project).  d_img: n_views*H*W floats, overwritten. */
+int gs_phantom_project(const float* d_ell, int ne, const gs_view* d_views, int n_views, int W,
+                       int H, float* d_img, void* stream);
+
+/* The phantom sampled at voxel centres over the whole grid ([z][y][x], overwritten). */
+int gs_phantom_voxelize(const float* d_ell, int ne, const gs_grid* grid, float* d_vol,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Initialisation (Sec. 3.1): FDK reconstruction and gradient-magnitude sampling.
+ * ------------------------------------------------------------------------------------- */
+
+size_t gs_fdk_workspace_size(int n_views, int W, int H);
+
+/* Feldkamp-Davis-Kress reconstruction of n_views cone-beam projections (d_proj, [view][row]
+ * [col]) taken on a full circle (views evenly spaced over 360 degrees, flat detectors
+ * perpendicular to the central ray, which passes through the rotation axis).  Each view is
+ * cosine-weighted, ramp-filtered along detector rows (Ram-Lak kernel, direct convolution) and
+ * back-projected with the D_so^2 / U^2 weight and bilinear detector interpolation; the result
+ * over `grid` ([z][y][x]) is scaled by pi / n_views.  W <= 12288. */
+int gs_fdk(const float* d_proj, const gs_view* d_views, int n_views, int W, int H,
+           const gs_grid* grid, float* d_vol, void* d_ws, size_t ws_bytes, void* stream);
+
+size_t gs_grad_init_workspace_size(const gs_grid* grid, int n);
+
+/* Gradient-based initialisation of n Gaussians from the volume d_vol on `grid` (Sec. 3.1;
+ * Sec. 3.6 applies it to a ground-truth volume):
+ *   - weight w = |grad V| by central differences (one-sided at the border) where
+ *     V > threshold_frac * max(V), else 0;
+ *   - voxel j chosen by inverse CDF with the uniform d_uniforms[4j] (FP64 CDF), position
+ *     jittered inside the voxel by d_uniforms[4j+1..4j+3] (all in [0, 1));
+ *   - density density_k * V(p) (trilinear), identity rotation;
+ *   - isotropic scale = distance to the nearest other sampled mean (at least min_scale).
+ * Writes d_mean_rho, d_scale, d_quat (float4[n]) and, if d_voxel is not NULL, the chosen
+ * voxel indices (int32[n]). */
+int gs_grad_init(const float* d_vol, const gs_grid* grid, int n, float threshold_frac,
+                 float density_k, float min_scale, const float* d_uniforms, float* d_mean_rho,
+                 float* d_scale, float* d_quat, int32_t* d_voxel, void* d_ws, size_t ws_bytes,
+                 void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Volume fit (Sec. 3.6, Eq. 6): Gaussians fitted to a given volume, e.g. a prior for a warm
+ * start or a compressed representation.
+ * ------------------------------------------------------------------------------------- */
+typedef struct gs_fit_opts {
+  float alpha_ssim;                       /* weight of the 3D SSIM term of Eq. 6 */
+  float lr_mean, lr_rho, lr_scale, lr_quat;
+  float beta1, beta2, eps;                /* Adam */
+  float min_log_scale, max_log_scale;
+  float threshold_frac;                   /* background threshold of the initialisation */
+  float density_k;                        /* k of the initialisation (0.15 in Sec. 3.1) */
+  float data_range;                       /* SSIM data range L; <= 0: max |V_gt| (one sync) */
+  float cut;                              /* truncation radius, 0 = 3 */
+  int32_t init;                           /* 1: initialise from V_gt; 0: use the given params */
+  int32_t pad;
+} gs_fit_opts;
+
+/* Workspace of gs_fit_volume for n Gaussians on `grid` with room for max_pairs (brick,
+ * Gaussian) pairs of the voxelizer. */
+size_t gs_fit_volume_workspace_size(int n, const gs_grid* grid, int64_t max_pairs);
+
+/* Fits n Gaussians to d_vol_gt ([z][y][x] on `grid`) in `iters` iterations of voxelize ->
+ * L1 + alpha_ssim * (1 - SSIM3D) -> voxelizer backward -> Adam.  With opts->init = 1 the
+ * Gaussians are first sampled from the volume by gs_grad_init (uniforms d_uniforms, 4n
+ * floats); otherwise d_mean_rho / d_scale / d_quat hold the starting parameters.  The fitted
+ * (activated) parameters are written back to those arrays; d_loss (iters floats, may be NULL)
+ * receives the loss of every iteration.  Asynchronous except for one read-back of max |V_gt|
+ * when opts->data_range <= 0 and alpha_ssim > 0.  A voxelizer capacity overflow is reported by
+ * gs_fit_volume_status. */
+int gs_fit_volume(const float* d_vol_gt, const gs_grid* grid, int n, int iters,
+                  const gs_fit_opts* opts, const float* d_uniforms, float* d_mean_rho,
+                  float* d_scale, float* d_quat, float* d_loss, void* d_ws, size_t ws_bytes,
+                  void* stream);
+
+/* Status block of the voxelizer inside a gs_fit_volume workspace (synchronises `stream`). */
+int gs_fit_volume_status(const void* d_ws, size_t ws_bytes, int n, const gs_grid* grid,
+                         void* stream, gs_status* h_out);
+
+/* ---------------------------------------------------------------------------------------
  * Binning internals exposed for testing: the sorted (key, Gaussian) lists of the last
  * binning in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).
  * ------------------------------------------------------------------------------------- */

@@ -47,6 +47,16 @@ class GsAdamOpts(ctypes.Structure):
                 ("pad", ctypes.c_float * 3)]
 
 
+class GsFitOpts(ctypes.Structure):
+    _fields_ = [("alpha_ssim", ctypes.c_float), ("lr_mean", ctypes.c_float),
+                ("lr_rho", ctypes.c_float), ("lr_scale", ctypes.c_float),
+                ("lr_quat", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("min_log_scale", ctypes.c_float),
+                ("max_log_scale", ctypes.c_float), ("threshold_frac", ctypes.c_float),
+                ("density_k", ctypes.c_float), ("data_range", ctypes.c_float),
+                ("cut", ctypes.c_float), ("init", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
 assert ctypes.sizeof(GsAdamOpts) == 48
 assert ctypes.sizeof(GsStatus) == 256
@@ -91,6 +101,16 @@ SIGNATURES = {
     "gs_adam_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P,
                           ctypes.c_void_p, _P]),
     "gs_activate": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
+    "gs_phantom_project": (_I, [_P, _I, _P, _I, _I, _I, _P, _P]),
+    "gs_phantom_voxelize": (_I, [_P, _I, _GRID, _P, _P]),
+    "gs_fdk_workspace_size": (_SZ, [_I, _I, _I]),
+    "gs_fdk": (_I, [_P, _P, _I, _I, _I, _GRID, _P, _P, _SZ, _P]),
+    "gs_fit_volume_workspace_size": (_SZ, [_I, _GRID, _I64]),
+    "gs_fit_volume": (_I, [_P, _GRID, _I, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "gs_fit_volume_status": (_I, [_P, _SZ, _I, _GRID, _P, ctypes.POINTER(GsStatus)]),
+    "gs_grad_init_workspace_size": (_SZ, [_GRID, _I]),
+    "gs_grad_init": (_I, [_P, _GRID, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P,
+                          _P, _P, _P, _P, _SZ, _P]),
     "gs_timing_enable": (None, [_I]),
     "gs_timing_reset": (None, []),
     "gs_timing_read": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),

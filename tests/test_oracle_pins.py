@@ -578,3 +578,71 @@ def test_adam_reference_special_cases():
     mr, sc, q = OO.activate(*raw)
     np.testing.assert_allclose(mr[:, 3], np.log1p(np.exp(raw[0][:, 3])), rtol=1e-12)
     np.testing.assert_allclose(sc[:, :3], np.exp(raw[1][:, :3]), rtol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# Initialisation (Sec. 3.1): FDK and gradient sampling
+# ------------------------------------------------------------------------------------------
+def test_ramlak_kernel_has_no_dc():
+    """The Ram-Lak kernel's taps sum to zero as the kernel length grows (|w| vanishes at 0)."""
+    from oracle.init import ramlak
+    tau = 0.01
+    h = ramlak(4001, tau)
+    centre = 4000  # k = 0
+    assert abs(h.sum()) < 1e-3 * h[centre]
+    assert abs(h[centre] - 1 / (4 * tau * tau)) < 1e-9 / tau ** 2
+    assert h[centre + 2] == 0 and h[centre + 1] < 0
+
+
+def test_fdk_recovers_a_ball(orc):
+    """Textbook behaviour: FDK of exact cone-beam projections of a centred ball (many views)
+    recovers its attenuation in the interior within a few percent and ~0 outside.  Catches a
+    wrong ramp scale, a wrong back-projection weight or a missing pi / V."""
+    from oracle.init import fdk
+    W = H = 96
+    views = synth.cone_views(120, W, H, det_len=2.4)
+    V = orc.views64(views)
+    ell = np.array([[0, 0, 0, 0.45, 0.45, 0.45, 1, 0, 0, 0, 0.8]])
+    proj = orc.phantom_project(ell, V, W, H)
+    grid = synth.cube_grid(32, half=0.75)
+    vol = fdk(proj, V, grid)
+    c = -0.75 + (np.arange(32) + 0.5) * (1.5 / 32)
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(xx ** 2 + yy ** 2 + zz ** 2)
+    inner = vol[r < 0.3]
+    outer = vol[r > 0.6]
+    assert abs(inner.mean() - 0.8) < 0.04 * 0.8, inner.mean()
+    assert np.abs(outer).mean() < 0.05 * 0.8
+
+
+def test_grad_sampling_follows_the_weights():
+    """Inverse-CDF sampling: voxel frequencies match w / sum(w) (chi-square, 100k draws), and
+    voxels under the threshold are never drawn."""
+    from oracle.init import grad_init, grad_weights_f32
+    rng = np.random.default_rng(0)
+    grid = synth.cube_grid(6)
+    V = rng.random((6, 6, 6)).astype(np.float32)
+    n = 100000
+    u = rng.random((n, 4)).astype(np.float32)
+    _, _, _, idx, _ = grad_init(V, grid, n, 0.3, 0.15, 1e-6, u)
+    w = grad_weights_f32(V, grid, 0.3).ravel()
+    p = w / w.sum()
+    cnt = np.bincount(idx, minlength=w.size)
+    assert np.all(cnt[p == 0] == 0)
+    nz_ = p > 0
+    chi2 = (((cnt[nz_] - n * p[nz_]) ** 2) / (n * p[nz_])).sum()
+    dof = nz_.sum() - 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof)
+
+
+def test_grad_init_nn_scale_is_brute_force_nearest_distance():
+    from oracle.init import grad_init
+    rng = np.random.default_rng(1)
+    grid = synth.cube_grid(16)
+    V = rng.random((16, 16, 16)).astype(np.float32)
+    u = rng.random((300, 4)).astype(np.float32)
+    mr, sc, q, idx, _ = grad_init(V, grid, 300, 0.2, 0.15, 1e-6, u)
+    P = mr[:, :3]
+    D = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)) + np.eye(300) * 1e9
+    np.testing.assert_allclose(sc[:, 0], D.min(1), rtol=1e-12)
+    assert np.all(q[:, 0] == 1)
