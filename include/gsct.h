@@ -211,6 +211,10 @@ int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const
 int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, float* d_loss,
                float* d_grad, int accumulate, void* stream);
 
+/* Sum of squared differences sum (a - b)^2 over n elements, accumulated in FP64 into *d_out
+ * (INCREMENTED; the caller zeroes it); PSNR = 10 log10(peak^2 n / sse). */
+int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* stream);
+
 /* 3D total variation of Eq. 5: weight * (sum of |forward differences| along x, y and z where
  * the neighbour exists) / (nx ny nz), volume [z][y][x]; sub-gradient with sign(0) = 0. */
 int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,

@@ -454,6 +454,19 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void k_step_incr(int* step) { *step += 1; }
 
+// sum of squared differences in FP64 (for PSNR)
+__global__ void __launch_bounds__(kThreads)
+    k_sse(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+          double* __restrict__ out) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const double d = (double)a[i] - (double)b[i];
+    s += d * d;
+  }
+  block_add(s, out);
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_activate(const float4* __restrict__ raw_mr, const float4* __restrict__ raw_sc,
                const float4* __restrict__ raw_q, float4* __restrict__ mr,
@@ -487,6 +500,13 @@ int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, floa
   if (n == 0) return GS_OK;
   return launch("l1_loss", k_l1, dim3(grid_for(n / 4 + 1)), dim3(kThreads), 0,
                 (cudaStream_t)stream, d_a, d_b, n, weight / (float)n, d_loss, d_grad, accumulate);
+}
+
+int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* stream) {
+  if (n < 0 || (n > 0 && (!d_a || !d_b)) || !d_out) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  return launch("sse", k_sse, dim3(grid_for(n)), dim3(kThreads), 0, (cudaStream_t)stream, d_a,
+                d_b, n, d_out);
 }
 
 int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,

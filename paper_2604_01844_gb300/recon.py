@@ -124,3 +124,94 @@ class Reconstruction:
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
                 "gs_adam_step")
         return self.loss
+
+
+# ------------------------------------------------------------------------------------------
+# End-to-end reconstruction of a synthetic phantom: projections -> FDK -> gradient-based
+# initialisation (Sec. 3.1) -> optimisation (Eq. 5) until a target PSNR of the voxelized
+# Gaussians against the ground-truth volume.
+# ------------------------------------------------------------------------------------------
+class PhantomProblem:
+    """Ground truth of a random-ellipsoid phantom: cone-beam projections (exact line
+    integrals) and the volume sampled at voxel centres, made on the device."""
+
+    def __init__(self, ell: np.ndarray, views, W: int, H: int, grid, device="cuda"):
+        from .projector import views_to_device
+
+        self.device = torch.device(device)
+        self.views = views
+        self.W, self.H = int(W), int(H)
+        self.grid = grid
+        self.d_views = views_to_device(views, self.device)
+        self.d_ell = torch.from_numpy(np.ascontiguousarray(ell, dtype=np.float32)).to(self.device)
+        L = B.lib()
+        s = B.stream_handle()
+        nv = int(self.d_views.shape[0])
+        self.proj = torch.empty((nv, H, W), dtype=torch.float32, device=self.device)
+        B.check(L.gs_phantom_project(B.ptr(self.d_ell), ell.shape[0], B.ptr(self.d_views), nv,
+                                     W, H, B.ptr(self.proj), s), "gs_phantom_project")
+        dims = [int(x) for x in np.asarray(grid["dims"]).ravel()]
+        self.gt = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device=self.device)
+        B.check(L.gs_phantom_voxelize(B.ptr(self.d_ell), ell.shape[0],
+                                      ctypes.byref(B.grid_struct(grid)), B.ptr(self.gt), s),
+                "gs_phantom_voxelize")
+        self.peak = float(self.gt.max())
+
+
+def fdk_volume(problem: PhantomProblem, grid) -> torch.Tensor:
+    L = B.lib()
+    nv = int(problem.d_views.shape[0])
+    ws = torch.empty(L.gs_fdk_workspace_size(nv, problem.W, problem.H), dtype=torch.uint8,
+                     device=problem.device)
+    dims = [int(x) for x in np.asarray(grid["dims"]).ravel()]
+    vol = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device=problem.device)
+    B.check(L.gs_fdk(B.ptr(problem.proj), B.ptr(problem.d_views), nv, problem.W, problem.H,
+                     ctypes.byref(B.grid_struct(grid)), B.ptr(vol), B.ptr(ws), ws.numel(),
+                     B.stream_handle()), "gs_fdk")
+    return vol
+
+
+def gradient_init(vol: torch.Tensor, grid, n: int, uniforms: np.ndarray, threshold_frac=0.05,
+                  density_k=0.15, min_scale=None):
+    """n Gaussians sampled from `vol` (Sec. 3.1); returns three (n, 4) device tensors."""
+    L = B.lib()
+    g = B.grid_struct(grid)
+    if min_scale is None:
+        min_scale = 0.5 * float(np.asarray(grid["voxel"]).min())
+    out = [torch.empty((n, 4), dtype=torch.float32, device=vol.device) for _ in range(3)]
+    du = torch.from_numpy(np.ascontiguousarray(uniforms, dtype=np.float32)).to(vol.device)
+    ws = torch.empty(L.gs_grad_init_workspace_size(ctypes.byref(g), n), dtype=torch.uint8,
+                     device=vol.device)
+    B.check(L.gs_grad_init(B.ptr(vol), ctypes.byref(g), n, threshold_frac, density_k, min_scale,
+                           B.ptr(du), *[B.ptr(t) for t in out], None, B.ptr(ws), ws.numel(),
+                           B.stream_handle()), "gs_grad_init")
+    return out
+
+
+def psnr_of(vol: torch.Tensor, gt: torch.Tensor, peak: float, sse: torch.Tensor) -> float:
+    """PSNR of vol against gt (peak = max of gt) from the library's FP64 SSE (synchronises)."""
+    L = B.lib()
+    B.check(L.gs_memset(B.ptr(sse), 0, 8, B.stream_handle()), "gs_memset")
+    B.check(L.gs_sse(B.ptr(vol), B.ptr(gt), vol.numel(), B.ptr(sse), B.stream_handle()), "gs_sse")
+    mse = float(sse.item()) / vol.numel()
+    return 10.0 * math.log10(peak * peak / mse) if mse > 0 else float("inf")
+
+
+def reconstruct_to_psnr(rec: "Reconstruction", gt: torch.Tensor, peak: float, max_iters: int,
+                        target_psnr: float, eval_every: int = 25):
+    """Runs rec.step() until the PSNR of its voxelized volume (the TV volume, which covers the
+    ground-truth grid) reaches target_psnr.  Returns (history [(iter, gpu ms, psnr)], reached)."""
+    sse = torch.zeros(1, dtype=torch.float64, device=gt.device)
+    start = torch.cuda.Event(enable_timing=True)
+    start.record()
+    hist = []
+    for it in range(1, max_iters + 1):
+        rec.step()
+        if it % eval_every == 0 or it == max_iters:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            p = psnr_of(rec.vol, gt, peak, sse)
+            hist.append((it, start.elapsed_time(ev), p))
+            if p >= target_psnr:
+                return hist, True
+    return hist, False
