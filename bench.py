@@ -286,6 +286,9 @@ def run_ours(args, ws, rank, local):
         "clocks": clk,
         "loss": loss,
     }
+    if not args.no_extras:
+        out["time_to_psnr"] = time_to_psnr(device)
+        out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -294,6 +297,91 @@ def run_ours(args, ws, rank, local):
 
         dist.barrier()
         dist.destroy_process_group()
+
+
+def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
+    """Plain single-instance reconstruction of the 40-ellipsoid phantom from 75 cone views of
+    512^2 with 50k Gaussians (FDK-gradient init, L1 + D-SSIM + TV on the 256^3 volume): GPU
+    time from the projections to the first evaluation at or above target_db."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300.recon import (PhantomProblem, ReconConfig, Reconstruction,
+                                               fdk_volume, gradient_init, psnr_of,
+                                               reconstruct_to_psnr)
+
+    views = synth.cone_views(75, 512, 512)
+    grid = synth.cube_grid(256)
+    prob = PhantomProblem(synth.ellipsoid_phantom(1, 40), views, 512, 512, grid, device=device)
+    u = np.random.default_rng(7).random((50000, 4)).astype(np.float32)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fdk = fdk_volume(prob, grid)
+    mr, sc, q = gradient_init(fdk, grid, 50000, u)
+    e1.record()
+    torch.cuda.synchronize()
+    init_ms = e0.elapsed_time(e1)
+    sse = torch.zeros(1, dtype=torch.float64, device=device)
+    fdk_db = psnr_of(fdk, prob.gt, prob.peak, sse)
+    cfg = ReconConfig(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)
+    rec = Reconstruction(views, 512, 512, prob.proj.clone(), grid, mr.cpu().numpy(),
+                         sc.cpu().numpy(), q.cpu().numpy(), cfg=cfg, device=device)
+    init_db = psnr_of(rec.voxelizer.forward(*rec.act), prob.gt, prob.peak, sse)
+    hist, ok = reconstruct_to_psnr(rec, prob.gt, prob.peak, max_iters, target_db, eval_every)
+    it, ms, db = hist[-1]
+    return {"target_db": target_db, "reached": ok, "iters": it, "ms_optimise": round(ms, 2),
+            "ms_fdk_and_init": round(init_ms, 2), "ms_total": round(ms + init_ms, 2),
+            "psnr_fdk_db": round(fdk_db, 2), "psnr_init_db": round(init_db, 2),
+            "psnr_final_db": round(db, 2), "eval_every": eval_every,
+            "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3",
+            "note": "plain single-instance form; PSNR = 10 log10(max(V_gt)^2 / MSE) on 256^3"}
+
+
+def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
+    """gs_fit_volume of n Gaussians to a side^3 ground truth (120-ellipsoid phantom):
+    Gaussian-voxel evaluations per second of the fit iterations (forward voxelization's
+    in-cut evaluations per iteration / ms per iteration)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2604_01844_gb300 as g
+    from paper_2604_01844_gb300 import binding as B
+    from paper_2604_01844_gb300.fit import VolumeFit, fit_opts
+
+    grid = synth.cube_grid(side)
+    ell = torch.from_numpy(synth.ellipsoid_phantom(3, 120).astype(np.float32)).to(device)
+    gt = torch.empty((side, side, side), dtype=torch.float32, device=device)
+    import ctypes
+
+    B.check(B.lib().gs_phantom_voxelize(B.ptr(ell), 120, ctypes.byref(B.grid_struct(grid)),
+                                        B.ptr(gt), B.stream_handle()), "gs_phantom_voxelize")
+    u = torch.from_numpy(np.random.default_rng(11).random((n, 4)).astype(np.float32)).to(device)
+    f = VolumeFit(grid, n, max_pairs=16 * n, device=device)
+    opts = fit_opts(data_range=float(gt.abs().max()))
+    f.run(gt, warmup, opts, u)  # init + warm-up iterations
+    torch.cuda.synchronize()
+    opts.init = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    loss = torch.zeros(iters, device=device)
+    e0.record()
+    f.run(gt, iters, opts, None, loss)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    st = f.status()
+    vox = g.Voxelizer(grid, device=device)
+    evals = vox.count_evals(*f.params)
+    del vox, f, gt
+    torch.cuda.empty_cache()
+    return {"workload": f"gs_fit_volume, {n} Gaussians, {side}^3 ground truth, bricks 16^3",
+            "ms_per_iter": round(ms, 3), "voxel_evals_per_iter": evals,
+            "value": evals / (ms * 1e-3), "unit": "Gaussian-voxel evals/s",
+            "status": int(st.code), "loss_last": float(loss[-1].item())}
 
 
 def read_traffic(kernel: str):
@@ -386,11 +474,15 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-PSNR and volume-fit measurements")
+    ap.add_argument("--fit-side", type=int, default=1024)
+    ap.add_argument("--fit-gaussians", type=int, default=500000)
     ap.add_argument("--workload", choices=["recon512", "small"], default="recon512",
                     help="small: 16-view case of the same kernels, for profiler captures")
     args = ap.parse_args()
