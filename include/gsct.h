@@ -369,6 +369,30 @@ int gs_fit_volume_status(const void* d_ws, size_t ws_bytes, int n, const gs_grid
                          void* stream, gs_status* h_out);
 
 /* ---------------------------------------------------------------------------------------
+ * BF16 tensor-core GEMM (tcgen05, tensor memory, TMA) and helpers of the per-brick MLP
+ * initializer.  The paper has no learned initializer; the MLP is this build's addition.
+ * ------------------------------------------------------------------------------------- */
+
+#define GS_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up (recorded in *d_err) */
+
+/* C[M, N] = A[M, K] . B[N, K]^T (+ bias[N]) (then ReLU if relu != 0), A and B bf16 row-major
+ * with K contiguous, FP32 accumulation in tensor memory.  Writes FP32 C (d_c32, leading
+ * dimension ldc) and/or BF16 C (d_c16, same leading dimension); either may be NULL.
+ * M % 128 == 0, N % 128 == 0, K % 64 == 0 (pad with zeros); A, B 16-byte aligned.
+ * d_err: device int, set to GS_ERR_TIMEOUT if a pipeline wait gave up (the caller zeroes it). */
+int gs_gemm_bf16(const void* d_a, const void* d_b, int M, int N, int K, const float* d_bias,
+                 int relu, float* d_c32, void* d_c16, int ldc, int* d_err, void* stream);
+
+/* y = bf16(x), n elements. */
+int gs_f32_to_bf16(const float* d_x, void* d_y, int64_t n, void* stream);
+/* out[cols][rows] = in[rows][cols] (bf16). */
+int gs_transpose_bf16(const void* d_in, int rows, int cols, void* d_out, void* stream);
+/* out = bf16(g * [act > 0]) elementwise (ReLU backward). */
+int gs_relu_mask_bf16(const float* d_g, const void* d_act, int64_t n, void* d_out, void* stream);
+/* out[c] = sum over rows of g[r][c] (bias gradient). */
+int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Binning internals exposed for testing: the sorted (key, Gaussian) lists of the last
  * binning in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).
  * ------------------------------------------------------------------------------------- */

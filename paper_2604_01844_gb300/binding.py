@@ -112,6 +112,11 @@ SIGNATURES = {
     "gs_grad_init_workspace_size": (_SZ, [_GRID, _I]),
     "gs_grad_init": (_I, [_P, _GRID, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P,
                           _P, _P, _P, _P, _SZ, _P]),
+    "gs_gemm_bf16": (_I, [_P, _P, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "gs_f32_to_bf16": (_I, [_P, _P, _I64, _P]),
+    "gs_transpose_bf16": (_I, [_P, _I, _I, _P, _P]),
+    "gs_relu_mask_bf16": (_I, [_P, _P, _I64, _P, _P]),
+    "gs_colsum": (_I, [_P, _I, _I, _P, _P]),
     "gs_timing_enable": (None, [_I]),
     "gs_timing_reset": (None, []),
     "gs_timing_read": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),

@@ -215,3 +215,25 @@ def reconstruct_to_psnr(rec: "Reconstruction", gt: torch.Tensor, peak: float, ma
             if p >= target_psnr:
                 return hist, True
     return hist, False
+
+
+class GraphStep:
+    """The optimisation step captured once into a CUDA graph and replayed (one graph launch per
+    step).  Valid while the workspaces keep their capacity; call Reconstruction.plan() and
+    capture again after re-planning."""
+
+    def __init__(self, rec: "Reconstruction", warmup: int = 2):
+        self.rec = rec
+        side = torch.cuda.Stream(device=rec.device)
+        side.wait_stream(torch.cuda.current_stream(rec.device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):  # settle allocations outside the capture
+                rec.step()
+        torch.cuda.current_stream(rec.device).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            rec.step()
+
+    def __call__(self):
+        self.graph.replay()
+        return self.rec.loss

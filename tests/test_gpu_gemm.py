@@ -1,0 +1,55 @@
+"""The tcgen05 BF16 GEMM against a float64 matmul of the same bf16-rounded operands."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01844_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _bf16(a):
+    return torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 128, 256), (384, 256, 4096),
+                                   (1024, 384, 256)])
+@pytest.mark.parametrize("relu", [0, 1])
+def test_gemm_matches_float64(B, M, N, K, relu):
+    rng = np.random.default_rng(M + N + K)
+    a = _bf16(rng.standard_normal((M, K)))
+    b = _bf16(rng.standard_normal((N, K)))
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32))
+    want = a.double() @ b.double().T + bias.double()
+    if relu:
+        want = want.clamp_min(0)
+    da, db, dbias = a.cuda(), b.cuda(), bias.cuda()
+    c32 = torch.empty((M, N), device="cuda")
+    c16 = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.check(B.lib().gs_gemm_bf16(B.ptr(da), B.ptr(db), M, N, K, B.ptr(dbias), relu, B.ptr(c32),
+                                 B.ptr(c16), N, B.ptr(err),
+                                 torch.cuda.current_stream().cuda_stream), "gemm")
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = c32.cpu().double()
+    # FP32 accumulation of K products of bf16 values: error ~ K * 2^-24 * sum|a b|
+    bound = 2e-6 * K ** 0.5 * (a.double().abs() @ b.double().abs().T) + 1e-6
+    assert bool(((got - want).abs() <= bound).all()), float((got - want).abs().max())
+    assert torch.allclose(c16.cpu().double(), got, rtol=1e-2, atol=1e-2)
+
+
+def test_gemm_rejects_bad_shapes(B):
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    x = torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda")
+    rc = B.lib().gs_gemm_bf16(B.ptr(x), B.ptr(x), 100, 128, 64, None, 0, B.ptr(x), None, 128,
+                              B.ptr(err), torch.cuda.current_stream().cuda_stream)
+    assert rc == B.GS_ERR_ARG
