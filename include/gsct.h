@@ -279,6 +279,9 @@ int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, f
                  const float* d_g_quat, float* d_mean_rho, float* d_scale, float* d_quat, int n,
                  int* d_step, const gs_adam_opts* opts, void* stream);
 
+/* *d_step += 1 on the device (step counter of gs_adam_flat users). */
+int gs_step_incr(int* d_step, void* stream);
+
 /* Activated parameters from raw ones (same activations as gs_adam_step). */
 int gs_activate(const float* d_raw_mean_rho, const float* d_raw_scale, const float* d_raw_quat,
                 float* d_mean_rho, float* d_scale, float* d_quat, int n, void* stream);
@@ -387,8 +390,33 @@ int gs_gemm_bf16(const void* d_a, const void* d_b, int M, int N, int K, const fl
 int gs_f32_to_bf16(const float* d_x, void* d_y, int64_t n, void* stream);
 /* out[cols][rows] = in[rows][cols] (bf16). */
 int gs_transpose_bf16(const void* d_in, int rows, int cols, void* d_out, void* stream);
-/* out = bf16(g * [act > 0]) elementwise (ReLU backward). */
-int gs_relu_mask_bf16(const float* d_g, const void* d_act, int64_t n, void* d_out, void* stream);
+/* ReLU backward: g *= [act > 0] in place, and out = bf16(g). */
+int gs_relu_mask_bf16(float* d_g, const void* d_act, int64_t n, void* d_out, void* stream);
+
+/* Per-brick MLP initializer (bricks of 16^3 voxels, 32 Gaussians x 11 raw outputs each, in
+ * brick-local voxel units): raw r -> centre 16 (1/2 + 1/2 tanh(r0..2)), scale
+ * exp(clamp(r3..5, -3, 2)), quaternion (1 + r6, r7, r8, r9), density softplus(r10). */
+
+/* For n_bricks rows of raw outputs d_y (leading dimension ldy >= 352): decode, render each
+ * brick's 32 Gaussians (3-sigma cut) at its voxel centres, add mean |render - target| over all
+ * bricks' voxels to *d_loss, and write d loss / d raw to d_dy (ldd >= 352; NULL: no
+ * backward).  d_target: n_bricks x 4096 floats; d_render (NULL or n_bricks x 4096) gets the
+ * rendering. */
+int gs_brick_loss(const float* d_y, int ldy, const float* d_target, int n_bricks, float* d_loss,
+                  float* d_dy, int ldd, float* d_render, void* stream);
+/* Raw outputs -> world-space Gaussians (32 per brick): d_geo float4 per brick = (origin x, y,
+ * z, voxel size); densities multiplied by amp. */
+int gs_brick_decode(const float* d_y, int ldy, const float* d_geo, int n_bricks, float amp,
+                    float* d_mean_rho, float* d_scale, float* d_quat, void* stream);
+/* Bricks (int4 bx, by, bz, unused) of a [z][y][x] volume -> rows of 4096 values times scale,
+ * as bf16 (d_out16) and/or f32 (d_out32); voxels outside the volume read 0. */
+int gs_extract_bricks(const float* d_vol, int nx, int ny, int nz, const int32_t* d_bricks,
+                      int n_bricks, float scale, void* d_out16, float* d_out32, void* stream);
+/* Adam on a flat FP32 array with the device step count (not incremented here), optional bf16
+ * copy of the updated parameters. */
+int gs_adam_flat(float* d_p, float* d_m, float* d_v, const float* d_g, int64_t n,
+                 const int* d_step, float lr, float beta1, float beta2, float eps, void* d_p16,
+                 void* stream);
 /* out[c] = sum over rows of g[r][c] (bias gradient). */
 int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream);
 

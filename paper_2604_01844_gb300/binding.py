@@ -117,6 +117,12 @@ SIGNATURES = {
     "gs_transpose_bf16": (_I, [_P, _I, _I, _P, _P]),
     "gs_relu_mask_bf16": (_I, [_P, _P, _I64, _P, _P]),
     "gs_colsum": (_I, [_P, _I, _I, _P, _P]),
+    "gs_brick_loss": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "gs_brick_decode": (_I, [_P, _I, _P, _I, ctypes.c_float, _P, _P, _P, _P]),
+    "gs_extract_bricks": (_I, [_P, _I, _I, _I, _P, _I, ctypes.c_float, _P, _P, _P]),
+    "gs_adam_flat": (_I, [_P, _P, _P, _P, _I64, _P, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, ctypes.c_float, _P, _P]),
+    "gs_step_incr": (_I, [_P, _P]),
     "gs_timing_enable": (None, [_I]),
     "gs_timing_reset": (None, []),
     "gs_timing_read": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),

@@ -502,6 +502,11 @@ int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, floa
                 (cudaStream_t)stream, d_a, d_b, n, weight / (float)n, d_loss, d_grad, accumulate);
 }
 
+int gs_step_incr(int* d_step, void* stream) {
+  if (!d_step) return GS_ERR_ARG;
+  return launch("step_incr", k_step_incr, dim3(1), dim3(1), 0, (cudaStream_t)stream, d_step);
+}
+
 int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* stream) {
   if (n < 0 || (n > 0 && (!d_a || !d_b)) || !d_out) return GS_ERR_ARG;
   if (n == 0) return GS_OK;

@@ -276,12 +276,15 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows,
   }
 }
 
-// g (rows x cols, f32) times the ReLU mask of act (bf16, > 0), written as bf16
-__global__ void k_relu_mask_bf16(const float* __restrict__ g, const __nv_bfloat16* __restrict__ act,
+// g (rows x cols, f32) times the ReLU mask of act (bf16, > 0): masked in place and as bf16
+__global__ void k_relu_mask_bf16(float* __restrict__ g, const __nv_bfloat16* __restrict__ act,
                                  int64_t n, __nv_bfloat16* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? g[i] : 0.f);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = __bfloat162float(act[i]) > 0.f ? g[i] : 0.f;
+    g[i] = v;
+    out[i] = __float2bfloat16_rn(v);
+  }
 }
 
 // column sums of g (rows x cols, f32): bias gradient
@@ -336,7 +339,7 @@ int gs_transpose_bf16(const void* d_in, int rows, int cols, void* d_out, void* s
                 (const __nv_bfloat16*)d_in, rows, cols, (__nv_bfloat16*)d_out);
 }
 
-int gs_relu_mask_bf16(const float* d_g, const void* d_act, int64_t n, void* d_out, void* stream) {
+int gs_relu_mask_bf16(float* d_g, const void* d_act, int64_t n, void* d_out, void* stream) {
   if (!d_g || !d_act || !d_out || n < 0) return GS_ERR_ARG;
   if (n == 0) return GS_OK;
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * num_sms());
@@ -348,6 +351,258 @@ int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream) 
   if (!d_g || !d_out || rows < 0 || cols < 1) return GS_ERR_ARG;
   return launch("colsum", k_colsum, dim3((cols + 127) / 128), dim3(128), 0,
                 (cudaStream_t)stream, d_g, rows, cols, d_out);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Per-brick MLP initializer: bricks of 16^3 voxels, 32 Gaussians x 11 raw outputs per brick.
+// Training works in brick-local voxel units (voxel centres at i + 1/2, i = 0..15).
+// Raw output r of Gaussian g: centre = 16 (1/2 + 1/2 tanh(r0..2)); scale = exp(clamp(r3..5,
+// -3, 2)) voxels; quaternion (1 + r6, r7, r8, r9); density softplus(r10).
+// ------------------------------------------------------------------------------------------
+namespace gs {
+namespace {
+
+constexpr int kBrick = 16;
+constexpr int kBrickVox = kBrick * kBrick * kBrick;
+constexpr int kGPB = 32;        // Gaussians per brick
+constexpr int kRaw = 11;        // raw outputs per Gaussian
+constexpr int kOut = kGPB * kRaw;  // 352
+
+struct DecG {
+  float c[3], s[3], qn[4], inv_norm, rho;
+  float R[3][3], Si[3][3];
+  float th[3];      // tanh of r0..2
+  float sp_grad;    // d softplus / d r10
+  int clamp_mask;   // bit k: scale k clamped
+};
+
+__device__ __forceinline__ void decode_one(const float* r, DecG& d) {
+  for (int k = 0; k < 3; ++k) {
+    d.th[k] = tanhf(r[k]);
+    d.c[k] = 0.5f * kBrick * (1.f + d.th[k]);
+  }
+  d.clamp_mask = 0;
+  for (int k = 0; k < 3; ++k) {
+    float x = r[3 + k];
+    if (x < -3.f || x > 2.f) d.clamp_mask |= 1 << k;
+    x = fminf(fmaxf(x, -3.f), 2.f);
+    d.s[k] = expf(x);
+  }
+  const float q0 = 1.f + r[6], q1 = r[7], q2 = r[8], q3 = r[9];
+  d.inv_norm = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3 + 1e-20f);
+  d.qn[0] = q0 * d.inv_norm; d.qn[1] = q1 * d.inv_norm; d.qn[2] = q2 * d.inv_norm;
+  d.qn[3] = q3 * d.inv_norm;
+  gsd::quat_to_rot(d.qn[0], d.qn[1], d.qn[2], d.qn[3], d.R);
+  const float x = r[10];
+  d.rho = x > 20.f ? x : log1pf(expf(x));
+  d.sp_grad = 1.f / (1.f + expf(-x));
+  const float i0 = 1.f / (d.s[0] * d.s[0]), i1 = 1.f / (d.s[1] * d.s[1]), i2 = 1.f / (d.s[2] * d.s[2]);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      d.Si[a][b] = d.R[a][0] * i0 * d.R[b][0] + d.R[a][1] * i1 * d.R[b][1] + d.R[a][2] * i2 * d.R[b][2];
+}
+
+// one CTA per brick: decode, render, L1 against the target, backward to the raw outputs
+__global__ void __launch_bounds__(256)
+    k_brick_loss(const float* __restrict__ Y, int ldy, const float* __restrict__ T, int nb,
+                 float inv_count, float* __restrict__ loss, float* __restrict__ dY, int ldd,
+                 float* __restrict__ render_out) {
+  __shared__ DecG g[kGPB];
+  __shared__ float sg[kBrickVox];       // dL/dV per voxel
+  __shared__ float mom[kGPB][10];
+  __shared__ float part[8][10];
+  __shared__ float lpart[8];
+  const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t < kGPB) {
+    float r[kRaw];
+    for (int k = 0; k < kRaw; ++k) r[k] = Y[(size_t)b * ldy + t * kRaw + k];
+    decode_one(r, g[t]);
+  }
+  __syncthreads();
+  // thread t owns the z-column (x, y) = (t % 16, t / 16)
+  const float x = (float)(t % kBrick) + 0.5f, y = (float)(t / kBrick) + 0.5f;
+  float acc[kBrick];
+  for (int z = 0; z < kBrick; ++z) acc[z] = 0.f;
+  for (int j = 0; j < kGPB; ++j) {
+    const DecG& G = g[j];
+    const float dx = x - G.c[0], dy = y - G.c[1];
+    for (int z = 0; z < kBrick; ++z) {
+      const float dz = (float)z + 0.5f - G.c[2];
+      const float q = dx * (G.Si[0][0] * dx + 2.f * (G.Si[0][1] * dy + G.Si[0][2] * dz)) +
+                      dy * (G.Si[1][1] * dy + 2.f * G.Si[1][2] * dz) + dz * G.Si[2][2] * dz;
+      if (q < 9.f) acc[z] += G.rho * expf(-0.5f * q);
+    }
+  }
+  float l = 0.f;
+  for (int z = 0; z < kBrick; ++z) {
+    const int v = (z * kBrick + t / kBrick) * kBrick + t % kBrick;
+    const float d = acc[z] - T[(size_t)b * kBrickVox + v];
+    l += fabsf(d);
+    sg[v] = inv_count * ((d > 0.f) - (d < 0.f));
+    if (render_out) render_out[(size_t)b * kBrickVox + v] = acc[z];
+  }
+  l = gsd::warp_sum(l);
+  if (lane == 0) lpart[w] = l;
+  __syncthreads();
+  if (t == 0 && loss) {
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) s += lpart[k];
+    atomicAdd(loss, s * inv_count);
+  }
+  if (!dY) return;
+  // moments of g exp(-q/2) per Gaussian: {1, d, d d^T}
+  for (int j = 0; j < kGPB; ++j) {
+    const DecG& G = g[j];
+    const float dx = x - G.c[0], dy = y - G.c[1];
+    float m[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int z = 0; z < kBrick; ++z) {
+      const float dz = (float)z + 0.5f - G.c[2];
+      const float q = dx * (G.Si[0][0] * dx + 2.f * (G.Si[0][1] * dy + G.Si[0][2] * dz)) +
+                      dy * (G.Si[1][1] * dy + 2.f * G.Si[1][2] * dz) + dz * G.Si[2][2] * dz;
+      if (q < 9.f) {
+        const int v = (z * kBrick + t / kBrick) * kBrick + t % kBrick;
+        const float e = sg[v] * expf(-0.5f * q);
+        m[0] += e; m[1] += e * dx; m[2] += e * dy; m[3] += e * dz;
+        m[4] += e * dx * dx; m[5] += e * dx * dy; m[6] += e * dx * dz;
+        m[7] += e * dy * dy; m[8] += e * dy * dz; m[9] += e * dz * dz;
+      }
+    }
+    for (int k = 0; k < 10; ++k) m[k] = gsd::warp_sum(m[k]);
+    if (lane == 0)
+      for (int k = 0; k < 10; ++k) part[w][k] = m[k];
+    __syncthreads();
+    if (t < 10) {
+      float s = 0.f;
+      for (int k = 0; k < 8; ++k) s += part[k][t];
+      mom[j][t] = s;
+    }
+    __syncthreads();
+  }
+  if (t < kGPB) {
+    const DecG& G = g[t];
+    const float* M = mom[t];
+    const float Sd[3] = {M[1], M[2], M[3]};
+    const float Sdd[3][3] = {{M[4], M[5], M[6]}, {M[5], M[7], M[8]}, {M[6], M[8], M[9]}};
+    float gc[3], gs[3], GR[3][3];
+    for (int k = 0; k < 3; ++k)
+      gc[k] = G.rho * (G.Si[k][0] * Sd[0] + G.Si[k][1] * Sd[1] + G.Si[k][2] * Sd[2]);
+    for (int k = 0; k < 3; ++k) {
+      float Gr[3];
+      for (int a = 0; a < 3; ++a)
+        Gr[a] = -0.5f * G.rho * (Sdd[a][0] * G.R[0][k] + Sdd[a][1] * G.R[1][k] + Sdd[a][2] * G.R[2][k]);
+      const float rGr = G.R[0][k] * Gr[0] + G.R[1][k] * Gr[1] + G.R[2][k] * Gr[2];
+      const float is2 = 1.f / (G.s[k] * G.s[k]);
+      gs[k] = -2.f * is2 / G.s[k] * rGr;
+      for (int a = 0; a < 3; ++a) GR[a][k] = 2.f * is2 * Gr[a];
+    }
+    float gq[4];
+    gsd::rot_to_quat_grad(G.qn[0], G.qn[1], G.qn[2], G.qn[3], GR, gq);
+    gsd::quat_normalize_grad(G.qn, G.inv_norm, gq);
+    float* out = dY + (size_t)b * ldd + t * kRaw;
+    for (int k = 0; k < 3; ++k) out[k] = gc[k] * 0.5f * kBrick * (1.f - G.th[k] * G.th[k]);
+    for (int k = 0; k < 3; ++k) out[3 + k] = ((G.clamp_mask >> k) & 1) ? 0.f : gs[k] * G.s[k];
+    for (int k = 0; k < 4; ++k) out[6 + k] = gq[k];
+    out[10] = M[0] * G.sp_grad;
+  }
+}
+
+// raw outputs -> world-space Gaussians: brick origin (x, y, z) and voxel size in `geo`,
+// densities multiplied by `amp`
+__global__ void k_brick_decode(const float* __restrict__ Y, int ldy, const float4* __restrict__ geo,
+                               int nb, float amp, float4* __restrict__ mean_rho,
+                               float4* __restrict__ scale, float4* __restrict__ quat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * kGPB) return;
+  const int b = i / kGPB, j = i % kGPB;
+  float r[kRaw];
+  for (int k = 0; k < kRaw; ++k) r[k] = Y[(size_t)b * ldy + j * kRaw + k];
+  DecG d;
+  decode_one(r, d);
+  const float4 o = geo[b];
+  mean_rho[i] = make_float4(o.x + d.c[0] * o.w, o.y + d.c[1] * o.w, o.z + d.c[2] * o.w, d.rho * amp);
+  scale[i] = make_float4(d.s[0] * o.w, d.s[1] * o.w, d.s[2] * o.w, 0.f);
+  quat[i] = make_float4(d.qn[0], d.qn[1], d.qn[2], d.qn[3]);
+}
+
+// bricks (bx, by, bz) of a [z][y][x] volume -> rows of 4096 values scaled by `scale`
+// (bf16 and/or f32); voxels outside the volume read as 0
+__global__ void k_extract_bricks(const float* __restrict__ vol, int nx, int ny, int nz,
+                                 const int4* __restrict__ bricks, float scale,
+                                 __nv_bfloat16* __restrict__ out16, float* __restrict__ out32) {
+  const int b = blockIdx.x;
+  const int4 id = bricks[b];
+  for (int v = threadIdx.x; v < kBrickVox; v += blockDim.x) {
+    const int x = id.x * kBrick + v % kBrick, y = id.y * kBrick + (v / kBrick) % kBrick,
+              z = id.z * kBrick + v / (kBrick * kBrick);
+    const float val = (x < nx && y < ny && z < nz) ? vol[((size_t)z * ny + y) * nx + x] * scale : 0.f;
+    if (out16) out16[(size_t)b * kBrickVox + v] = __float2bfloat16_rn(val);
+    if (out32) out32[(size_t)b * kBrickVox + v] = val;
+  }
+}
+
+// Adam on a flat FP32 array (bias-corrected with the device step count), bf16 copy written
+__global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int64_t n, const int* __restrict__ step,
+                            float lr, float b1, float b2, float eps,
+                            __nv_bfloat16* __restrict__ p16) {
+  const int t = *step + 1;
+  const float c1 = 1.f / (1.f - powf(b1, (float)t)), c2 = 1.f / (1.f - powf(b2, (float)t));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    if (p16) p16[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" {
+
+int gs_brick_loss(const float* d_y, int ldy, const float* d_target, int n_bricks, float* d_loss,
+                  float* d_dy, int ldd, float* d_render, void* stream) {
+  if (!d_y || !d_target || n_bricks < 1 || ldy < gs::kOut || (d_dy && ldd < gs::kOut))
+    return GS_ERR_ARG;
+  const float inv = 1.f / ((float)n_bricks * gs::kBrickVox);
+  return gs::launch("brick_loss", gs::k_brick_loss, dim3(n_bricks), dim3(256), 0,
+                    (cudaStream_t)stream, d_y, ldy, d_target, n_bricks, inv, d_loss, d_dy, ldd,
+                    d_render);
+}
+
+int gs_brick_decode(const float* d_y, int ldy, const float* d_geo, int n_bricks, float amp,
+                    float* d_mean_rho, float* d_scale, float* d_quat, void* stream) {
+  if (!d_y || !d_geo || n_bricks < 1 || ldy < gs::kOut || !d_mean_rho || !d_scale || !d_quat)
+    return GS_ERR_ARG;
+  const int n = n_bricks * gs::kGPB;
+  return gs::launch("brick_decode", gs::k_brick_decode, dim3((n + 255) / 256), dim3(256), 0,
+                    (cudaStream_t)stream, d_y, ldy, (const float4*)d_geo, n_bricks, amp,
+                    (float4*)d_mean_rho, (float4*)d_scale, (float4*)d_quat);
+}
+
+int gs_extract_bricks(const float* d_vol, int nx, int ny, int nz, const int32_t* d_bricks,
+                      int n_bricks, float scale, void* d_out16, float* d_out32, void* stream) {
+  if (!d_vol || !d_bricks || n_bricks < 1 || (!d_out16 && !d_out32)) return GS_ERR_ARG;
+  return gs::launch("extract_bricks", gs::k_extract_bricks, dim3(n_bricks), dim3(256), 0,
+                    (cudaStream_t)stream, d_vol, nx, ny, nz, (const int4*)d_bricks, scale,
+                    (__nv_bfloat16*)d_out16, d_out32);
+}
+
+int gs_adam_flat(float* d_p, float* d_m, float* d_v, const float* d_g, int64_t n,
+                 const int* d_step, float lr, float beta1, float beta2, float eps, void* d_p16,
+                 void* stream) {
+  if (!d_p || !d_m || !d_v || !d_g || !d_step || n < 0) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * gs::num_sms());
+  return gs::launch("adam_flat", gs::k_adam_flat, dim3(grid), dim3(256), 0,
+                    (cudaStream_t)stream, d_p, d_m, d_v, d_g, n, d_step, lr, beta1, beta2, eps,
+                    (__nv_bfloat16*)d_p16);
 }
 
 }  // extern "C"
