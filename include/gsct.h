@@ -394,14 +394,18 @@ int gs_transpose_bf16(const void* d_in, int rows, int cols, void* d_out, void* s
 int gs_relu_mask_bf16(float* d_g, const void* d_act, int64_t n, void* d_out, void* stream);
 
 /* Per-brick MLP initializer (bricks of 16^3 voxels, 32 Gaussians x 11 raw outputs each, in
- * brick-local voxel units): raw r -> centre 16 (1/2 + 1/2 tanh(r0..2)), scale
- * exp(clamp(r3..5, -3, 2)), quaternion (1 + r6, r7, r8, r9), density softplus(r10). */
+ * brick-local voxel units).  Gaussian g lives in cell (g % 4, g / 4 % 4, g / 16) of a
+ * 4 x 4 x 2 lattice of 4 x 4 x 8-voxel cells: centre = cell centre + (2, 2, 4) tanh(r0..2),
+ * scale = (1.2, 1.2, 2.4) exp(clamp(r3..5, -3, 2)), quaternion (1 + r6, r7, r8, r9),
+ * density softplus(r10). */
 
 /* For n_bricks rows of raw outputs d_y (leading dimension ldy >= 352): decode, render each
- * brick's 32 Gaussians (3-sigma cut) at its voxel centres, add mean |render - target| over all
- * bricks' voxels to *d_loss, and write d loss / d raw to d_dy (ldd >= 352; NULL: no
- * backward).  d_target: n_bricks x 4096 floats; d_render (NULL or n_bricks x 4096) gets the
- * rendering. */
+ * brick's 32 Gaussians (3-sigma cut) at the voxel centres of the brick extended by a margin of
+ * 4 voxels on every side (24^3), compare with the target (the brick's d_target values inside,
+ * 0 in the margin, so that the bricks' renderings add up when assembled), add the mean
+ * absolute difference over all bricks' regions to *d_loss, and write d loss / d raw to d_dy
+ * (ldd >= 352; NULL: no backward).  d_target: n_bricks x 4096 floats; d_render (NULL or
+ * n_bricks x 4096) gets the rendering inside the brick. */
 int gs_brick_loss(const float* d_y, int ldy, const float* d_target, int n_bricks, float* d_loss,
                   float* d_dy, int ldd, float* d_render, void* stream);
 /* Raw outputs -> world-space Gaussians (32 per brick): d_geo float4 per brick = (origin x, y,

@@ -378,17 +378,30 @@ struct DecG {
   int clamp_mask;   // bit k: scale k clamped
 };
 
-__device__ __forceinline__ void decode_one(const float* r, DecG& d) {
+// Gaussian g of a brick lives in cell (g % 4, g / 4 % 4, g / 16) of a 4 x 4 x 2 lattice of
+// 4 x 4 x 8-voxel cells: centre = cell centre + half-cell * tanh(r0..2), base scale = 0.3 x
+// cell size, so that r = 0 already covers the brick evenly.
+__device__ __forceinline__ void lattice(int g, float base[3], float half[3], float sbase[3]) {
+  base[0] = ((g % 4) + 0.5f) * 4.f;
+  base[1] = (((g / 4) % 4) + 0.5f) * 4.f;
+  base[2] = ((g / 16) + 0.5f) * 8.f;
+  half[0] = 2.f; half[1] = 2.f; half[2] = 4.f;
+  sbase[0] = 1.2f; sbase[1] = 1.2f; sbase[2] = 2.4f;
+}
+
+__device__ __forceinline__ void decode_one(const float* r, int gi, DecG& d) {
+  float base[3], half[3], sbase[3];
+  lattice(gi, base, half, sbase);
   for (int k = 0; k < 3; ++k) {
     d.th[k] = tanhf(r[k]);
-    d.c[k] = 0.5f * kBrick * (1.f + d.th[k]);
+    d.c[k] = base[k] + half[k] * d.th[k];
   }
   d.clamp_mask = 0;
   for (int k = 0; k < 3; ++k) {
     float x = r[3 + k];
     if (x < -3.f || x > 2.f) d.clamp_mask |= 1 << k;
     x = fminf(fmaxf(x, -3.f), 2.f);
-    d.s[k] = expf(x);
+    d.s[k] = sbase[k] * expf(x);
   }
   const float q0 = 1.f + r[6], q1 = r[7], q2 = r[8], q3 = r[9];
   d.inv_norm = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3 + 1e-20f);
@@ -404,13 +417,24 @@ __device__ __forceinline__ void decode_one(const float* r, DecG& d) {
       d.Si[a][b] = d.R[a][0] * i0 * d.R[b][0] + d.R[a][1] * i1 * d.R[b][1] + d.R[a][2] * i2 * d.R[b][2];
 }
 
-// one CTA per brick: decode, render, L1 against the target, backward to the raw outputs
+// one CTA per brick: decode, render over the brick plus a margin of kMargin voxels on every
+// side (target: the brick's values inside, 0 in the margin, so that the bricks' renderings
+// add up when assembled into a volume), L1, backward to the raw outputs
+constexpr int kMargin = 4;
+constexpr int kSide = kBrick + 2 * kMargin;        // 24
+constexpr int kRegion = kSide * kSide * kSide;     // 13824
+
+__device__ __forceinline__ float quad_at(const DecG& G, float dx, float dy, float dz) {
+  return dx * (G.Si[0][0] * dx + 2.f * (G.Si[0][1] * dy + G.Si[0][2] * dz)) +
+         dy * (G.Si[1][1] * dy + 2.f * G.Si[1][2] * dz) + dz * G.Si[2][2] * dz;
+}
+
 __global__ void __launch_bounds__(256)
     k_brick_loss(const float* __restrict__ Y, int ldy, const float* __restrict__ T, int nb,
                  float inv_count, float* __restrict__ loss, float* __restrict__ dY, int ldd,
                  float* __restrict__ render_out) {
+  extern __shared__ float sg[];  // dL/dV over the region
   __shared__ DecG g[kGPB];
-  __shared__ float sg[kBrickVox];       // dL/dV per voxel
   __shared__ float mom[kGPB][10];
   __shared__ float part[8][10];
   __shared__ float lpart[8];
@@ -418,30 +442,27 @@ __global__ void __launch_bounds__(256)
   if (t < kGPB) {
     float r[kRaw];
     for (int k = 0; k < kRaw; ++k) r[k] = Y[(size_t)b * ldy + t * kRaw + k];
-    decode_one(r, g[t]);
+    decode_one(r, t, g[t]);
   }
   __syncthreads();
-  // thread t owns the z-column (x, y) = (t % 16, t / 16)
-  const float x = (float)(t % kBrick) + 0.5f, y = (float)(t / kBrick) + 0.5f;
-  float acc[kBrick];
-  for (int z = 0; z < kBrick; ++z) acc[z] = 0.f;
-  for (int j = 0; j < kGPB; ++j) {
-    const DecG& G = g[j];
-    const float dx = x - G.c[0], dy = y - G.c[1];
-    for (int z = 0; z < kBrick; ++z) {
-      const float dz = (float)z + 0.5f - G.c[2];
-      const float q = dx * (G.Si[0][0] * dx + 2.f * (G.Si[0][1] * dy + G.Si[0][2] * dz)) +
-                      dy * (G.Si[1][1] * dy + 2.f * G.Si[1][2] * dz) + dz * G.Si[2][2] * dz;
-      if (q < 9.f) acc[z] += G.rho * expf(-0.5f * q);
-    }
-  }
   float l = 0.f;
-  for (int z = 0; z < kBrick; ++z) {
-    const int v = (z * kBrick + t / kBrick) * kBrick + t % kBrick;
-    const float d = acc[z] - T[(size_t)b * kBrickVox + v];
+  for (int v = t; v < kRegion; v += 256) {
+    const int xi = v % kSide - kMargin, yi = (v / kSide) % kSide - kMargin,
+              zi = v / (kSide * kSide) - kMargin;
+    const float x = (float)xi + 0.5f, y = (float)yi + 0.5f, z = (float)zi + 0.5f;
+    float acc = 0.f;
+    for (int j = 0; j < kGPB; ++j) {
+      const DecG& G = g[j];
+      const float q = quad_at(G, x - G.c[0], y - G.c[1], z - G.c[2]);
+      if (q < 9.f) acc += G.rho * expf(-0.5f * q);
+    }
+    const bool inside = xi >= 0 && xi < kBrick && yi >= 0 && yi < kBrick && zi >= 0 && zi < kBrick;
+    const int bv = (zi * kBrick + yi) * kBrick + xi;
+    const float tgt = inside ? T[(size_t)b * kBrickVox + bv] : 0.f;
+    const float d = acc - tgt;
     l += fabsf(d);
     sg[v] = inv_count * ((d > 0.f) - (d < 0.f));
-    if (render_out) render_out[(size_t)b * kBrickVox + v] = acc[z];
+    if (render_out && inside) render_out[(size_t)b * kBrickVox + bv] = acc;
   }
   l = gsd::warp_sum(l);
   if (lane == 0) lpart[w] = l;
@@ -455,14 +476,13 @@ __global__ void __launch_bounds__(256)
   // moments of g exp(-q/2) per Gaussian: {1, d, d d^T}
   for (int j = 0; j < kGPB; ++j) {
     const DecG& G = g[j];
-    const float dx = x - G.c[0], dy = y - G.c[1];
     float m[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int z = 0; z < kBrick; ++z) {
-      const float dz = (float)z + 0.5f - G.c[2];
-      const float q = dx * (G.Si[0][0] * dx + 2.f * (G.Si[0][1] * dy + G.Si[0][2] * dz)) +
-                      dy * (G.Si[1][1] * dy + 2.f * G.Si[1][2] * dz) + dz * G.Si[2][2] * dz;
+    for (int v = t; v < kRegion; v += 256) {
+      const float dx = (float)(v % kSide - kMargin) + 0.5f - G.c[0];
+      const float dy = (float)((v / kSide) % kSide - kMargin) + 0.5f - G.c[1];
+      const float dz = (float)(v / (kSide * kSide) - kMargin) + 0.5f - G.c[2];
+      const float q = quad_at(G, dx, dy, dz);
       if (q < 9.f) {
-        const int v = (z * kBrick + t / kBrick) * kBrick + t % kBrick;
         const float e = sg[v] * expf(-0.5f * q);
         m[0] += e; m[1] += e * dx; m[2] += e * dy; m[3] += e * dz;
         m[4] += e * dx * dx; m[5] += e * dx * dy; m[6] += e * dx * dz;
@@ -501,7 +521,9 @@ __global__ void __launch_bounds__(256)
     gsd::rot_to_quat_grad(G.qn[0], G.qn[1], G.qn[2], G.qn[3], GR, gq);
     gsd::quat_normalize_grad(G.qn, G.inv_norm, gq);
     float* out = dY + (size_t)b * ldd + t * kRaw;
-    for (int k = 0; k < 3; ++k) out[k] = gc[k] * 0.5f * kBrick * (1.f - G.th[k] * G.th[k]);
+    float base[3], half[3], sbase[3];
+    lattice(t, base, half, sbase);
+    for (int k = 0; k < 3; ++k) out[k] = gc[k] * half[k] * (1.f - G.th[k] * G.th[k]);
     for (int k = 0; k < 3; ++k) out[3 + k] = ((G.clamp_mask >> k) & 1) ? 0.f : gs[k] * G.s[k];
     for (int k = 0; k < 4; ++k) out[6 + k] = gq[k];
     out[10] = M[0] * G.sp_grad;
@@ -519,7 +541,7 @@ __global__ void k_brick_decode(const float* __restrict__ Y, int ldy, const float
   float r[kRaw];
   for (int k = 0; k < kRaw; ++k) r[k] = Y[(size_t)b * ldy + j * kRaw + k];
   DecG d;
-  decode_one(r, d);
+  decode_one(r, j, d);
   const float4 o = geo[b];
   mean_rho[i] = make_float4(o.x + d.c[0] * o.w, o.y + d.c[1] * o.w, o.z + d.c[2] * o.w, d.rho * amp);
   scale[i] = make_float4(d.s[0] * o.w, d.s[1] * o.w, d.s[2] * o.w, 0.f);
@@ -570,8 +592,15 @@ int gs_brick_loss(const float* d_y, int ldy, const float* d_target, int n_bricks
                   float* d_dy, int ldd, float* d_render, void* stream) {
   if (!d_y || !d_target || n_bricks < 1 || ldy < gs::kOut || (d_dy && ldd < gs::kOut))
     return GS_ERR_ARG;
-  const float inv = 1.f / ((float)n_bricks * gs::kBrickVox);
-  return gs::launch("brick_loss", gs::k_brick_loss, dim3(n_bricks), dim3(256), 0,
+  const float inv = 1.f / ((float)n_bricks * gs::kRegion);
+  static bool attr = false;
+  if (!attr) {
+    GS_CUDA(cudaFuncSetAttribute(gs::k_brick_loss, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(gs::kRegion * sizeof(float))));
+    attr = true;
+  }
+  return gs::launch("brick_loss", gs::k_brick_loss, dim3(n_bricks), dim3(256),
+                    gs::kRegion * sizeof(float),
                     (cudaStream_t)stream, d_y, ldy, d_target, n_bricks, inv, d_loss, d_dy, ldd,
                     d_render);
 }

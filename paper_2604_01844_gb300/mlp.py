@@ -35,9 +35,9 @@ class BrickMLP:
             if li == 3:
                 w *= 0.1
                 w[N_OUT:] = 0.0
-                # start from small, moderately dense Gaussians: scale raw ~ 0.5, density raw ~ -1
-                b[:N_OUT].reshape(32, 11)[:, 3:6] = 0.5
-                b[:N_OUT].reshape(32, 11)[:, 10] = -1.0
+                # start from the lattice (offsets 0, base scales) with densities about the
+                # mean intensity of a normalised brick
+                b[:N_OUT].reshape(32, 11)[:, 10] = -0.5
             self.W.append(torch.from_numpy(w.astype(np.float32)).to(self.device))
             self.b.append(torch.from_numpy(b.astype(np.float32)).to(self.device))
         self.W16 = [torch.empty(w.shape, dtype=torch.bfloat16, device=self.device) for w in self.W]

@@ -649,21 +649,25 @@ def test_grad_init_nn_scale_is_brute_force_nearest_distance():
 
 
 def test_brick_render_reference_special_case():
-    """The MLP's brick renderer: raw outputs that decode to one axis-aligned Gaussian at the
-    brick centre (tanh 0, scale e^0.5, identity quaternion) reproduce the separable product of
-    1D Gaussians inside the 3-sigma ellipsoid; the other 31 have zero density."""
+    """The MLP's brick renderer: raw outputs that decode to one axis-aligned Gaussian at its
+    lattice cell centre (2, 2, 4) (tanh 0, scale base * e^0.5, identity quaternion) reproduce
+    the separable product of 1D Gaussians inside the 3-sigma ellipsoid; the other 31 have zero
+    density."""
     from oracle import mlp as OM
     raw = torch.zeros(1, 352, dtype=torch.float64)
     r = raw.view(1, 32, 11)
     r[:, :, 10] = -60.0        # softplus(-60) ~ 1e-26
     r[0, 0, 3:6] = 0.5
     r[0, 0, 10] = 3.0
-    img = OM.render(raw)[0].reshape(16, 16, 16)
-    s = math.exp(0.5)
+    img = OM.render(raw, margin=0)[0].reshape(16, 16, 16)
+    s = np.array([1.2, 1.2, 2.4]) * math.exp(0.5)
     rho = math.log1p(math.exp(3.0))
-    ax = np.arange(16) + 0.5 - 8.0
-    g1 = np.exp(-0.5 * (ax / s) ** 2)
-    want = rho * g1[:, None, None] * g1[None, :, None] * g1[None, None, :]
-    q = (ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2) / s ** 2
+    ax = np.arange(16) + 0.5
+    gx = np.exp(-0.5 * ((ax - 2.0) / s[0]) ** 2)
+    gy = np.exp(-0.5 * ((ax - 2.0) / s[1]) ** 2)
+    gz = np.exp(-0.5 * ((ax - 4.0) / s[2]) ** 2)
+    want = rho * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    q = (((ax[None, None, :] - 2.0) / s[0]) ** 2 + ((ax[None, :, None] - 2.0) / s[1]) ** 2 +
+         ((ax[:, None, None] - 4.0) / s[2]) ** 2)
     want = np.where(q < 9, want, 0.0)
     np.testing.assert_allclose(img.numpy(), want, atol=1e-12)
