@@ -372,7 +372,7 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
     sse = torch.zeros(1, dtype=torch.float64, device=device)
     # warm the inference path once (module load, tensor-map set-up) outside the timing
     I.learned_init(mlp, fdk_volume(prob, grid), grid, 50000, u)
-    out = {"train_bricks": int(hist and 0) or None, "train_ms": round(train_ms, 1),
+    out = {"train_ms": round(train_ms, 1),
            "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)],
            "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3"}
     lr_sets = {"plain": [dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)],
@@ -408,7 +408,6 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
                    default=runs[0])
         out[name] = {"init_ms": round(init_ms, 2), "gaussians_from_mlp": n_mlp, "runs": runs,
                      "best_ms_to_target": best["ms_total"] if best["reached"] else None}
-    out.pop("train_bricks")
     return out
 
 

@@ -147,8 +147,8 @@ int gs_project(const float* d_mean_rho, const float* d_scale, const float* d_qua
  * the gradient arrays instead of overwriting them.  reuse = 1: the workspace still holds the
  * lists of a gs_project call with the same parameters and geometry; reuse = 0 rebuilds them
  * (recompute, no stored lists needed).  The truncation mask is held constant (its boundary is
- * not differentiated).  Per-Gaussian backward (Sec. 3.5): one warp per (Gaussian, tile) pair,
- * reduced with warp shuffles before one set of atomics per pair. */
+ * not differentiated).  Per-Gaussian backward (Sec. 3.5): one thread per (Gaussian, tile)
+ * pair walks the exact chords of its ellipse and issues one set of atomics per pair. */
 int gs_project_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
                         int n, const gs_view* d_views, int n_views, int W, int H,
                         const gs_opts* opts, const float* d_dimg, float* d_g_mean_rho,
@@ -161,6 +161,50 @@ int gs_project_backward(const float* d_mean_rho, const float* d_scale, const flo
 int gs_project_count_evals(const float* d_mean_rho, const float* d_scale, const float* d_quat,
                            int n, const gs_view* d_views, int n_views, int W, int H,
                            const gs_opts* opts, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched rasterizer: up to GS_MAX_INSTANCES independent reconstructions (each with its own
+ * Gaussians, views and detector size) projected with one kernel launch per pass.  The
+ * single-instance calls above are this with one instance.  Not described in the paper (which
+ * runs one reconstruction at a time); the per-pair arithmetic is the same as gs_project's.
+ *
+ * Layout: instances are concatenated in order.  Gaussian arrays hold sum(n) float4 records
+ * (instance k's Gaussians start at the sum of the earlier instances' n); d_views holds
+ * sum(n_views) records; images and their gradients hold sum(n_views * H * W) floats, instance
+ * k's block at the sum of the earlier blocks, each [view][row][col].  The instance table is
+ * a host array, read during the call (passed to the kernels by value, so a call makes no
+ * host-to-device copy and can be captured in a CUDA graph).  n may be 0 for some instances;
+ * n_views, W, H must be >= 1 and W, H <= 32767; the totals must stay below 2^31 (pairs,
+ * (view, Gaussian) records and (view, tile) keys).  GS_ERR_ARG otherwise.
+ * ------------------------------------------------------------------------------------- */
+#define GS_MAX_INSTANCES 32
+
+typedef struct gs_instance {
+  int32_t n;        /* Gaussians */
+  int32_t n_views;  /* views */
+  int32_t W, H;     /* detector columns, rows */
+} gs_instance;
+
+size_t gs_project_batch_workspace_size(const gs_instance* h_inst, int n_inst,
+                                       const gs_opts* opts, int64_t max_pairs);
+int gs_project_batch_count_pairs(const float* d_mean_rho, const float* d_scale,
+                                 const float* d_quat, const gs_view* d_views,
+                                 const gs_instance* h_inst, int n_inst, const gs_opts* opts,
+                                 void* d_ws, size_t ws_bytes, void* stream, int64_t* h_pairs);
+int gs_project_batch(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                     const gs_view* d_views, const gs_instance* h_inst, int n_inst,
+                     const gs_opts* opts, float* d_img, void* d_ws, size_t ws_bytes,
+                     void* stream);
+int gs_project_batch_backward(const float* d_mean_rho, const float* d_scale,
+                              const float* d_quat, const gs_view* d_views,
+                              const gs_instance* h_inst, int n_inst, const gs_opts* opts,
+                              const float* d_dimg, float* d_g_mean_rho, float* d_g_scale,
+                              float* d_g_quat, int accumulate, int reuse, void* d_ws,
+                              size_t ws_bytes, void* stream);
+int gs_project_batch_count_evals(const float* d_mean_rho, const float* d_scale,
+                                 const float* d_quat, const gs_view* d_views,
+                                 const gs_instance* h_inst, int n_inst, const gs_opts* opts,
+                                 void* d_ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Voxelizer (Sec. 3.3, Eq. 2)
@@ -425,8 +469,10 @@ int gs_adam_flat(float* d_p, float* d_m, float* d_v, const float* d_g, int64_t n
 int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * Binning internals exposed for testing: the sorted (key, Gaussian) lists of the last
- * binning in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).
+ * Binning internals exposed for testing: the sorted (key, value) lists of the last binning
+ * in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).  Rasterizer:
+ * key = (first key of the instance) + view * tiles + tile, value = record index (first record
+ * of the instance + view * n + Gaussian).  Voxelizer: key = brick, value = Gaussian.
  * ------------------------------------------------------------------------------------- */
 int gs_read_pairs(const void* d_ws, size_t ws_bytes, void* stream, int64_t cap,
                   uint32_t* h_keys, uint32_t* h_vals, int64_t* h_pairs);

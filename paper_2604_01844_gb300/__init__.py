@@ -6,8 +6,8 @@ __graft_entry__.build()).
 """
 from . import binding
 from .binding import GsError
-from .projector import Projector, ProjectFunction, project, views_to_device
+from .projector import BatchProjector, Projector, ProjectFunction, project, views_to_device
 from .voxelizer import Voxelizer, VoxelizeFunction, voxelize
 
-__all__ = ["binding", "GsError", "Projector", "ProjectFunction", "project", "views_to_device",
+__all__ = ["binding", "GsError", "BatchProjector", "Projector", "ProjectFunction", "project", "views_to_device",
            "Voxelizer", "VoxelizeFunction", "voxelize"]

@@ -57,7 +57,15 @@ class GsFitOpts(ctypes.Structure):
                 ("cut", ctypes.c_float), ("init", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class GsInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_views", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("H", ctypes.c_int32)]
+
+
+MAX_INSTANCES = 32
+
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
+assert ctypes.sizeof(GsInstance) == 16
 assert ctypes.sizeof(GsAdamOpts) == 48
 assert ctypes.sizeof(GsStatus) == 256
 
@@ -68,6 +76,7 @@ _P, _I, _I64, _SZ, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_
 _OPTS = ctypes.POINTER(GsOpts)
 _GRID = ctypes.POINTER(GsGrid)
 _I3 = ctypes.POINTER(ctypes.c_int32)
+_INST = ctypes.POINTER(GsInstance)
 SIGNATURES = {
     "gs_version": (ctypes.c_char_p, []),
     "gs_build_arch": (_I, []),
@@ -81,6 +90,13 @@ SIGNATURES = {
     "gs_project_backward": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _P, _P, _P, _I, _I,
                                  _P, _SZ, _P]),
     "gs_project_count_evals": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _SZ, _P]),
+    "gs_project_batch_workspace_size": (_SZ, [_INST, _I, _OPTS, _I64]),
+    "gs_project_batch_count_pairs": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _SZ, _P,
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "gs_project_batch": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _P, _SZ, _P]),
+    "gs_project_batch_backward": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _P, _P, _P, _I,
+                                       _I, _P, _SZ, _P]),
+    "gs_project_batch_count_evals": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _SZ, _P]),
     "gs_voxelize_workspace_size": (_SZ, [_I, _GRID, _I3, _I3, _OPTS, _I64]),
     "gs_voxelize_count_pairs": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P,
                                      ctypes.POINTER(ctypes.c_int64)]),

@@ -127,7 +127,8 @@ class Projector:
         return int(self.status().evals)
 
     def read_pairs(self):
-        """Sorted (key, Gaussian) lists of the last binning (synchronises)."""
+        """Sorted (key, record) lists of the last binning (synchronises); key = view * tiles +
+        tile, record = view * n + Gaussian."""
         st = self.status()
         n = int(st.pairs)
         keys = np.zeros(max(n, 1), dtype=np.uint32)
@@ -142,6 +143,123 @@ class Projector:
     @staticmethod
     def _token(*ts):
         return tuple((t.data_ptr(), t._version) for t in ts)
+
+
+class BatchProjector:
+    """Projects up to 32 independent instances (each its own Gaussians, views and W x H
+    detector) with one kernel launch per pass.
+
+    `instances` is a list of (views, W, H).  Parameters are the instances' (n_k, 4) arrays
+    concatenated in order, with `counts` = [n_k]; the image is one flat float32 tensor holding
+    each instance's (V_k, H_k, W_k) block in order (`split` returns the blocks as views).
+    """
+
+    def __init__(self, instances, cut: float = 3.0, eps: float = 0.0, znear: float = 0.1,
+                 tile: int = 16, device="cuda", headroom: float = 1.5):
+        if not 1 <= len(instances) <= B.MAX_INSTANCES:
+            raise ValueError(f"1 .. {B.MAX_INSTANCES} instances")
+        self.device = torch.device(device)
+        vs = [v if isinstance(v, torch.Tensor) else views_to_device(v, self.device)
+              for v, _, _ in instances]
+        self.views = torch.cat(vs, 0).contiguous()
+        self.shapes = [(int(v.shape[0]), int(H), int(W)) for v, (_, W, H) in zip(vs, instances)]
+        self.img_numel = sum(a * b * c for a, b, c in self.shapes)
+        self.opts = B.opts(cut=cut, eps=eps, znear=znear, tile=tile)
+        self.headroom = float(headroom)
+        self.ws = None
+        self.ws_counts = None
+        self.capacity = 0
+        self._fwd_token = None
+
+    def table(self, counts):
+        if len(counts) != len(self.shapes):
+            raise ValueError("one Gaussian count per instance")
+        t = (B.GsInstance * len(counts))()
+        for k, (n, (nv, H, W)) in enumerate(zip(counts, self.shapes)):
+            t[k].n, t[k].n_views, t[k].W, t[k].H = int(n), nv, W, H
+        return t
+
+    def split(self, flat: torch.Tensor):
+        out, off = [], 0
+        for nv, H, W in self.shapes:
+            out.append(flat[off:off + nv * H * W].view(nv, H, W))
+            off += nv * H * W
+        return out
+
+    def _alloc(self, counts, pairs):
+        t = self.table(counts)
+        nbytes = int(B.lib().gs_project_batch_workspace_size(t, len(counts),
+                                                             ctypes.byref(self.opts), int(pairs)))
+        if nbytes == 0:
+            raise B.GsError("invalid batch sizes")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ws_counts = list(counts)
+        self.capacity = pairs
+
+    def count_pairs(self, mean_rho, scale, quat, counts) -> int:
+        if self.ws is None or self.ws_counts != list(counts):
+            self._alloc(counts, 0)
+        out = ctypes.c_int64(0)
+        t = self.table(counts)
+        B.check(B.lib().gs_project_batch_count_pairs(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), B.ptr(self.views), t, len(counts),
+            ctypes.byref(self.opts), B.ptr(self.ws), self.ws.numel(), B.stream_handle(),
+            ctypes.byref(out)), "gs_project_batch_count_pairs")
+        return int(out.value)
+
+    def ensure_capacity(self, mean_rho, scale, quat, counts) -> int:
+        pairs = self.count_pairs(mean_rho, scale, quat, counts)
+        if self.ws_counts != list(counts) or pairs > self.capacity:
+            self._alloc(counts, int(pairs * self.headroom) + 1024)
+        return pairs
+
+    def _ready(self, mean_rho, scale, quat, counts):
+        if sum(counts) != mean_rho.shape[0]:
+            raise ValueError("counts must add up to the number of Gaussians")
+        if self.ws is None or self.ws_counts != list(counts) or self.capacity == 0:
+            self.ensure_capacity(mean_rho, scale, quat, counts)
+
+    def forward(self, mean_rho, scale, quat, counts, out: torch.Tensor | None = None):
+        mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
+        self._ready(mean_rho, scale, quat, counts)
+        if out is None:
+            out = torch.empty(self.img_numel, dtype=torch.float32, device=self.device)
+        t = self.table(counts)
+        B.check(B.lib().gs_project_batch(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), B.ptr(self.views), t, len(counts),
+            ctypes.byref(self.opts), B.ptr(out), B.ptr(self.ws), self.ws.numel(),
+            B.stream_handle()), "gs_project_batch")
+        self._fwd_token = Projector._token(mean_rho, scale, quat) + (tuple(counts),)
+        return out
+
+    def backward(self, mean_rho, scale, quat, counts, dimg, grads=None, accumulate=False,
+                 reuse: bool | None = None):
+        mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
+        dimg = dimg.contiguous()
+        self._ready(mean_rho, scale, quat, counts)
+        if reuse is None:
+            reuse = self._fwd_token == Projector._token(mean_rho, scale, quat) + (tuple(counts),)
+        if grads is None:
+            grads = tuple(torch.empty_like(x) for x in (mean_rho, scale, quat))
+            accumulate = False
+        g_mr, g_sc, g_q = grads
+        t = self.table(counts)
+        B.check(B.lib().gs_project_batch_backward(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), B.ptr(self.views), t, len(counts),
+            ctypes.byref(self.opts), B.ptr(dimg), B.ptr(g_mr), B.ptr(g_sc), B.ptr(g_q),
+            1 if accumulate else 0, 1 if reuse else 0, B.ptr(self.ws), self.ws.numel(),
+            B.stream_handle()), "gs_project_batch_backward")
+        return g_mr, g_sc, g_q
+
+    def count_evals(self, mean_rho, scale, quat, counts) -> int:
+        self.ensure_capacity(mean_rho, scale, quat, counts)
+        t = self.table(counts)
+        B.check(B.lib().gs_project_batch_count_evals(
+            B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), B.ptr(self.views), t, len(counts),
+            ctypes.byref(self.opts), B.ptr(self.ws), self.ws.numel(), B.stream_handle()),
+            "gs_project_batch_count_evals")
+        self._fwd_token = None
+        return int(B.read_status(self.ws).evals)
 
 
 class ProjectFunction(torch.autograd.Function):

@@ -90,3 +90,29 @@ def test_argument_errors_are_host_side(built):
     # misaligned workspace pointer
     rc = L.gs_project(16, 16, 16, 10, 16, 1, 8, 8, ctypes.byref(o), 16, 17, 1 << 20, None)
     assert rc == binding.GS_ERR_ARG
+
+
+def test_batch_table_validation(built):
+    """The batched rasterizer rejects bad instance tables on the host; a batch of one sizes its
+    workspace like the single-instance call."""
+    from paper_2604_01844_gb300 import binding
+
+    L = binding.lib()
+    o = binding.opts()
+    t = (binding.GsInstance * 33)()
+    for i in range(33):
+        t[i].n, t[i].n_views, t[i].W, t[i].H = 100, 2, 40, 30
+    one = L.gs_project_workspace_size(100, 2, 40, 30, ctypes.byref(o), 5000)
+    assert L.gs_project_batch_workspace_size(t, 1, ctypes.byref(o), 5000) == one > 0
+    assert L.gs_project_batch_workspace_size(t, 32, ctypes.byref(o), 0) > one
+    assert L.gs_project_batch_workspace_size(t, 33, ctypes.byref(o), 0) == 0
+    assert L.gs_project_batch_workspace_size(t, 0, ctypes.byref(o), 0) == 0
+    t[3].n = 0  # an empty instance is allowed
+    assert L.gs_project_batch_workspace_size(t, 8, ctypes.byref(o), 0) > 0
+    t[5].n_views = 0
+    assert L.gs_project_batch_workspace_size(t, 8, ctypes.byref(o), 0) == 0
+    t[5].n_views, t[6].W = 2, 40000
+    assert L.gs_project_batch_workspace_size(t, 8, ctypes.byref(o), 0) == 0
+    t[6].W = 40
+    rc = L.gs_project_batch(None, None, None, None, t, 8, ctypes.byref(o), 16, 16, 1 << 20, None)
+    assert rc == binding.GS_ERR_ARG

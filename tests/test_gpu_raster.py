@@ -104,8 +104,12 @@ def test_keys_and_sort_order_bit_exact(orc, gsct, tile):
     amb = (flags & 5) != 0  # box-edge or near-plane ambiguity changes keys
     proj = gsct.Projector(views, W, H, tile=tile)
     proj.forward(*to_dev(mr, sc, qt))
-    keys_g, vals_g = proj.read_pairs()
+    keys_g, recs_g = proj.read_pairs()
     TWH = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    # the device's values are (view, Gaussian) record indices v * n + i
+    n = mr.shape[0]
+    assert np.array_equal(recs_g.astype(np.int64) // n, keys_g.astype(np.int64) // TWH)
+    vals_g = recs_g.astype(np.int64) % n
 
     def strip(k, v):
         keep = ~amb[k // TWH, v]
