@@ -170,8 +170,10 @@ int gs_project_count_evals(const float* d_mean_rho, const float* d_scale, const 
  *
  * Layout: instances are concatenated in order.  Gaussian arrays hold sum(n) float4 records
  * (instance k's Gaussians start at the sum of the earlier instances' n); d_views holds
- * sum(n_views) records; images and their gradients hold sum(n_views * H * W) floats, instance
- * k's block at the sum of the earlier blocks, each [view][row][col].  The instance table is
+ * sum(n_views) records; images and their gradients hold one block of n_views * H * W floats
+ * per instance, [view][row][col], in order, each block starting at a multiple of 64 floats
+ * (256 bytes): instance k's block starts at the sum over earlier instances of their block
+ * size rounded up to 64.  The instance table is
  * a host array, read during the call (passed to the kernels by value, so a call makes no
  * host-to-device copy and can be captured in a CUDA graph).  n may be 0 for some instances;
  * n_views, W, H must be >= 1 and W, H <= 32767; the totals must stay below 2^31 (pairs,
@@ -242,6 +244,45 @@ int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const
                             int n, const gs_grid* grid, const int32_t roi_lo[3],
                             const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
                             size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched voxelizer: up to GS_MAX_INSTANCES independent volumes (each with its own Gaussians,
+ * grid and region of interest) voxelized with one kernel launch per pass.  The single-volume
+ * calls above are this with one instance.  Not described in the paper (one volume at a time);
+ * the per-voxel arithmetic is the same as gs_voxelize's.
+ *
+ * Layout: Gaussian arrays hold sum(n) float4 records in instance order; volumes and their
+ * gradients hold one region [z][y][x] of roi_dim[0] * roi_dim[1] * roi_dim[2] floats per
+ * instance, in order, each starting at a multiple of 64 floats (256 bytes) as for images.  The table is a host array read during the
+ * call (passed to the kernels by value: no host-to-device copy, capturable in a CUDA graph).
+ * Every instance is validated like gs_voxelize's grid and region; n may be 0.
+ * ------------------------------------------------------------------------------------- */
+typedef struct gs_voxel_instance {
+  int32_t n;             /* Gaussians */
+  gs_grid grid;          /* full grid */
+  int32_t roi_lo[3];     /* region of interest: first voxel (x, y, z) */
+  int32_t roi_dim[3];    /* region of interest: extent */
+} gs_voxel_instance;
+
+size_t gs_voxelize_batch_workspace_size(const gs_voxel_instance* h_inst, int n_inst,
+                                        const gs_opts* opts, int64_t max_pairs);
+int gs_voxelize_batch_count_pairs(const float* d_mean_rho, const float* d_scale,
+                                  const float* d_quat, const gs_voxel_instance* h_inst,
+                                  int n_inst, const gs_opts* opts, void* d_ws, size_t ws_bytes,
+                                  void* stream, int64_t* h_pairs);
+int gs_voxelize_batch(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                      const gs_voxel_instance* h_inst, int n_inst, const gs_opts* opts,
+                      float* d_vol, void* d_ws, size_t ws_bytes, void* stream);
+int gs_voxelize_batch_backward(const float* d_mean_rho, const float* d_scale,
+                               const float* d_quat, const gs_voxel_instance* h_inst, int n_inst,
+                               const gs_opts* opts, const float* d_dvol, float* d_g_mean_rho,
+                               float* d_g_scale, float* d_g_quat, int accumulate, int reuse,
+                               void* d_ws, size_t ws_bytes, void* stream);
+int gs_voxelize_batch_count_evals(const float* d_mean_rho, const float* d_scale,
+                                  const float* d_quat, const gs_voxel_instance* h_inst,
+                                  int n_inst, const gs_opts* opts, void* d_ws, size_t ws_bytes,
+                                  void* stream);
+
 
 /* ---------------------------------------------------------------------------------------
  * Loss terms of the reconstruction objective (Eq. 5) and of the volume fit (Eq. 6), each a

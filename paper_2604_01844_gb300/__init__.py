@@ -7,7 +7,7 @@ __graft_entry__.build()).
 from . import binding
 from .binding import GsError
 from .projector import BatchProjector, Projector, ProjectFunction, project, views_to_device
-from .voxelizer import Voxelizer, VoxelizeFunction, voxelize
+from .voxelizer import BatchVoxelizer, Voxelizer, VoxelizeFunction, voxelize
 
 __all__ = ["binding", "GsError", "BatchProjector", "Projector", "ProjectFunction", "project", "views_to_device",
-           "Voxelizer", "VoxelizeFunction", "voxelize"]
+           "BatchVoxelizer", "Voxelizer", "VoxelizeFunction", "voxelize"]

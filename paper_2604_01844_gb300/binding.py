@@ -62,10 +62,15 @@ class GsInstance(ctypes.Structure):
                 ("H", ctypes.c_int32)]
 
 
+class GsVoxelInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("grid", GsGrid), ("roi_lo", ctypes.c_int32 * 3),
+                ("roi_dim", ctypes.c_int32 * 3)]
+
+
 MAX_INSTANCES = 32
 
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
-assert ctypes.sizeof(GsInstance) == 16
+assert ctypes.sizeof(GsInstance) == 16 and ctypes.sizeof(GsVoxelInstance) == 64
 assert ctypes.sizeof(GsAdamOpts) == 48
 assert ctypes.sizeof(GsStatus) == 256
 
@@ -77,6 +82,7 @@ _OPTS = ctypes.POINTER(GsOpts)
 _GRID = ctypes.POINTER(GsGrid)
 _I3 = ctypes.POINTER(ctypes.c_int32)
 _INST = ctypes.POINTER(GsInstance)
+_VINST = ctypes.POINTER(GsVoxelInstance)
 SIGNATURES = {
     "gs_version": (ctypes.c_char_p, []),
     "gs_build_arch": (_I, []),
@@ -104,6 +110,13 @@ SIGNATURES = {
     "gs_voxelize_backward": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _P, _P, _P, _I,
                                   _I, _P, _SZ, _P]),
     "gs_voxelize_count_evals": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P]),
+    "gs_voxelize_batch_workspace_size": (_SZ, [_VINST, _I, _OPTS, _I64]),
+    "gs_voxelize_batch_count_pairs": (_I, [_P, _P, _P, _VINST, _I, _OPTS, _P, _SZ, _P,
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "gs_voxelize_batch": (_I, [_P, _P, _P, _VINST, _I, _OPTS, _P, _P, _SZ, _P]),
+    "gs_voxelize_batch_backward": (_I, [_P, _P, _P, _VINST, _I, _OPTS, _P, _P, _P, _P, _I, _I,
+                                        _P, _SZ, _P]),
+    "gs_voxelize_batch_count_evals": (_I, [_P, _P, _P, _VINST, _I, _OPTS, _P, _SZ, _P]),
     "gs_read_pairs": (_I, [_P, _SZ, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "gs_l1_loss": (_I, [_P, _P, _I64, ctypes.c_float, _P, _P, _I, _P]),
     "gs_tv3d_loss": (_I, [_P, _I, _I, _I, ctypes.c_float, _P, _P, _I, _P]),

@@ -122,7 +122,7 @@ int make_plan(const gs_instance* inst, int n_inst, const gs_opts* o, int64_t cap
     d.img_off = img;
     items += (int64_t)s.n * s.n_views;
     keys += (int64_t)s.n_views * d.TW * d.TH;
-    img += (int64_t)s.n_views * s.W * s.H;
+    img += ((int64_t)s.n_views * s.W * s.H + 63) / 64 * 64;  // blocks start 256-byte aligned
     gsum += s.n;
     vsum += s.n_views;
   }

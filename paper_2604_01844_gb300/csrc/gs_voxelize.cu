@@ -1,4 +1,6 @@
-// Voxelizer of FaCT-GS (Sec. 3.3, Eq. 2), forward and backward, sm_103a.
+// Voxelizer of FaCT-GS (Sec. 3.3, Eq. 2), forward and backward, sm_103a, for a batch of up to
+// 32 independent instances (own Gaussians, grid and region of interest) in one launch per pass;
+// a single volume is a batch of one.  The instance table is a __grid_constant__ parameter.
 //
 //   vox_prep    one thread per Gaussian: inverse covariance (pre-scaled to a base-2 exponent),
 //               the 3-sigma ellipsoid's axis-aligned index box clipped to the region of
@@ -49,40 +51,79 @@ struct Layout {
   size_t bytes = 0;
 };
 
-struct Plan {
-  int n = 0;
+constexpr int kMaxInst = GS_MAX_INSTANCES;
+
+struct VInst {
   VGrid g;
+  int n, g_off;
+  long long key_off, vol_off;
+};
+
+struct VBatch {
+  int count;
+  float cut2;
+  VInst in[kMaxInst];
+};
+
+__device__ __forceinline__ int inst_of_gaussian(const VBatch& b, int i) {
+  int k = 0;
+  while (k + 1 < b.count && b.in[k + 1].g_off <= i) ++k;
+  return k;
+}
+__device__ __forceinline__ int inst_of_key(const VBatch& b, int64_t key) {
+  int k = 0;
+  while (k + 1 < b.count && b.in[k + 1].key_off <= key) ++k;
+  return k;
+}
+
+struct Plan {
+  VBatch b;
+  int n = 0;  // Gaussians over all instances
   int64_t n_keys = 0, cap = 0;
   int nblocks = 0, key_bits = 0;
   SortPlan sort;
-  float cut2 = 9.f;
 };
 
-int make_plan(int n, const gs_grid* grid, const int32_t* roi_lo, const int32_t* roi_dim,
-              const gs_opts* o, int64_t cap, Plan& p) {
-  if (!grid || !roi_lo || !roi_dim || !o || n < 0 || cap < 0) return GS_ERR_ARG;
+int make_plan(const gs_voxel_instance* inst, int n_inst, const gs_opts* o, int64_t cap,
+              Plan& p) {
+  if (!inst || n_inst < 1 || n_inst > kMaxInst || !o || cap < 0) return GS_ERR_ARG;
   if (!(o->cut > 0.f)) return GS_ERR_ARG;
   if (o->brick != 0 && o->brick != kB) return GS_ERR_ARG;
-  for (int k = 0; k < 3; ++k) {
-    if (grid->dims[k] < 1 || grid->dims[k] > 32767) return GS_ERR_ARG;
-    if (!(grid->voxel[k] > 0.f)) return GS_ERR_ARG;
-    if (roi_dim[k] < 1 || roi_lo[k] < 0 || roi_lo[k] + roi_dim[k] > grid->dims[k])
-      return GS_ERR_ARG;
-    p.g.dims[k] = grid->dims[k];
-    p.g.o[k] = grid->origin[k];
-    p.g.h[k] = grid->voxel[k];
-    p.g.lo[k] = roi_lo[k];
-    p.g.dim[k] = roi_dim[k];
-    p.g.nb[k] = (roi_dim[k] + kB - 1) / kB;
+  memset(&p.b, 0, sizeof(p.b));
+  p.b.count = n_inst;
+  p.b.cut2 = o->cut * o->cut;
+  int64_t n = 0, keys = 0, vox = 0;
+  for (int q = 0; q < n_inst; ++q) {
+    const gs_voxel_instance& s = inst[q];
+    VInst& d = p.b.in[q];
+    if (s.n < 0) return GS_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+      if (s.grid.dims[k] < 1 || s.grid.dims[k] > 32767) return GS_ERR_ARG;
+      if (!(s.grid.voxel[k] > 0.f)) return GS_ERR_ARG;
+      if (s.roi_dim[k] < 1 || s.roi_lo[k] < 0 || s.roi_lo[k] + s.roi_dim[k] > s.grid.dims[k])
+        return GS_ERR_ARG;
+      d.g.dims[k] = s.grid.dims[k];
+      d.g.o[k] = s.grid.origin[k];
+      d.g.h[k] = s.grid.voxel[k];
+      d.g.lo[k] = s.roi_lo[k];
+      d.g.dim[k] = s.roi_dim[k];
+      d.g.nb[k] = (s.roi_dim[k] + kB - 1) / kB;
+    }
+    d.n = s.n;
+    d.g_off = (int)n;
+    d.key_off = keys;
+    d.vol_off = vox;
+    n += s.n;
+    keys += (int64_t)d.g.nb[0] * d.g.nb[1] * d.g.nb[2];
+    vox += ((int64_t)s.roi_dim[0] * s.roi_dim[1] * s.roi_dim[2] + 63) / 64 * 64;  // aligned
   }
-  p.n = n;
-  p.n_keys = (int64_t)p.g.nb[0] * p.g.nb[1] * p.g.nb[2];
-  if (p.n_keys > ((int64_t)1 << 31)) return GS_ERR_ARG;
+  if (n > ((int64_t)1 << 31) - kThreads || keys > ((int64_t)1 << 31) - 1) return GS_ERR_ARG;
+  p.n = (int)n;
+  p.n_keys = keys;
   p.cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
-  p.nblocks = (n + kThreads - 1) / kThreads;
+  p.nblocks = (p.n + kThreads - 1) / kThreads;
   p.key_bits = bits_for(p.n_keys);
   p.sort = make_sort_plan(p.key_bits);
-  p.cut2 = o->cut * o->cut;
   return GS_OK;
 }
 
@@ -137,8 +178,9 @@ __device__ __forceinline__ bool vox_gauss(const float4 sc, const float4 qt, VFwd
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_vox_prep(const float4* __restrict__ mean_rho, const float4* __restrict__ scale,
-               const float4* __restrict__ quat, int n, VGrid g, float cut2, gs_status* st,
+    k_vox_prep(const __grid_constant__ VBatch bt, const float4* __restrict__ mean_rho,
+               const float4* __restrict__ scale, const float4* __restrict__ quat, int n,
+               gs_status* st,
                float4* __restrict__ geo, float4* __restrict__ cov0, float4* __restrict__ cov1,
                short4* __restrict__ lo_out, short4* __restrict__ hi_out,
                uint32_t* __restrict__ counts, uint32_t* __restrict__ block_sums) {
@@ -150,6 +192,8 @@ __global__ void __launch_bounds__(kThreads)
   const int i = blockIdx.x * kThreads + threadIdx.x;
   uint32_t cnt = 0;
   if (i < n) {
+    const VGrid& g = bt.in[inst_of_gaussian(bt, i)].g;
+    const float cut2 = bt.cut2;
     const float4 mr = mean_rho[i];
     VFwd o;
     int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
@@ -205,15 +249,16 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_vox_emit(const uint32_t* __restrict__ counts, const short4* __restrict__ lo_in,
-               const short4* __restrict__ hi_in, const uint32_t* __restrict__ block_offs, int n,
-               VGrid g, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, gs_status* st,
+    k_vox_emit(const __grid_constant__ VBatch bt, const uint32_t* __restrict__ counts,
+               const short4* __restrict__ lo_in, const short4* __restrict__ hi_in,
+               const uint32_t* __restrict__ block_offs, int n, int64_t n_keys,
+               uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, gs_status* st,
                int64_t sorted_keys_off, int64_t sorted_vals_off) {
   __shared__ uint32_t warp_pre[kThreads / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->reserved[0] = sorted_keys_off;
     st->reserved[1] = sorted_vals_off;
-    st->reserved[2] = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+    st->reserved[2] = n_keys;
   }
   if (st->code != GS_OK) return;
   const int i = blockIdx.x * kThreads + threadIdx.x;
@@ -234,11 +279,14 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   if (cnt == 0) return;
   uint32_t off = block_offs[blockIdx.x] + warp_pre[w] + incl - cnt;
+  const VInst& I = bt.in[inst_of_gaussian(bt, i)];
+  const VGrid& g = I.g;
+  const uint32_t kbase = (uint32_t)I.key_off;
   const short4 a = lo_in[i], b = hi_in[i];
   for (int bz = (a.z - g.lo[2]) / kB; bz <= (b.z - g.lo[2]) / kB; ++bz)
     for (int by = (a.y - g.lo[1]) / kB; by <= (b.y - g.lo[1]) / kB; ++by)
       for (int bx = (a.x - g.lo[0]) / kB; bx <= (b.x - g.lo[0]) / kB; ++bx) {
-        keys[off] = (uint32_t)((bz * g.nb[1] + by) * g.nb[0] + bx);
+        keys[off] = kbase + (uint32_t)((bz * g.nb[1] + by) * g.nb[0] + bx);
         vals[off] = (uint32_t)i;
         ++off;
       }
@@ -249,8 +297,8 @@ __global__ void __launch_bounds__(kThreads)
     k_vox_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
               const float4* __restrict__ geo, const float4* __restrict__ cov0,
               const float4* __restrict__ cov1, const short4* __restrict__ lo_in,
-              const short4* __restrict__ hi_in, VGrid g, float* __restrict__ vol,
-              gs_status* st) {
+              const short4* __restrict__ hi_in, const __grid_constant__ VBatch bt,
+              float* __restrict__ vol, gs_status* st) {
   __shared__ float4 s_geo[kThreads];
   __shared__ float4 s_c0[kThreads];
   __shared__ float4 s_c1[kThreads];
@@ -258,7 +306,9 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ short4 s_hi[kThreads];
   __shared__ unsigned long long s_cnt;
   if (st->code != GS_OK) return;
-  const int brick = blockIdx.x;
+  const VInst& I = bt.in[inst_of_key(bt, blockIdx.x)];
+  const VGrid& g = I.g;
+  const int brick = (int)(blockIdx.x - I.key_off);
   const int bx = brick % g.nb[0], by = (brick / g.nb[0]) % g.nb[1], bz = brick / (g.nb[0] * g.nb[1]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wx0 = g.lo[0] + bx * kB + (w & 1) * 8;
@@ -274,7 +324,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int k = 0; k < kB; ++k) acc[k] = 0.f;
   uint32_t cnt = 0;
   if (COUNT && threadIdx.x == 0) s_cnt = 0ull;
-  const uint2 r = ranges[brick];
+  const uint2 r = ranges[blockIdx.x];
   for (uint32_t base = r.x; base < r.y; base += kThreads) {
     const int m = (int)min((uint32_t)kThreads, r.y - base);
     __syncthreads();
@@ -322,10 +372,11 @@ __global__ void __launch_bounds__(kThreads)
   if (!in_xy) return;
   const size_t sx = (size_t)g.dim[0], sxy = (size_t)g.dim[0] * g.dim[1];
   const size_t col = (size_t)(y - g.lo[1]) * sx + (x - g.lo[0]);
+  float* vo = vol + I.vol_off;
 #pragma unroll
   for (int k = 0; k < kB; ++k) {
     const int z = z0 + k;
-    if (z < g.lo[2] + g.dim[2]) vol[(size_t)(z - g.lo[2]) * sxy + col] = acc[k];
+    if (z < g.lo[2] + g.dim[2]) vo[(size_t)(z - g.lo[2]) * sxy + col] = acc[k];
   }
 }
 
@@ -333,8 +384,9 @@ __global__ void __launch_bounds__(kThreads)
     k_vox_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
               const float4* __restrict__ geo, const float4* __restrict__ cov0,
               const float4* __restrict__ cov1, const short4* __restrict__ lo_in,
-              const short4* __restrict__ hi_in, VGrid g, const float* __restrict__ dvol,
-              float4* __restrict__ vgrad, const gs_status* st) {
+              const short4* __restrict__ hi_in, const __grid_constant__ VBatch bt,
+              const float* __restrict__ dvol_all, float4* __restrict__ vgrad,
+              const gs_status* st) {
   __shared__ float s_g[kB * kB * kB];
   __shared__ float4 s_geo[kThreads];
   __shared__ float4 s_c0[kThreads];
@@ -343,9 +395,12 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ short4 s_hi[kThreads];
   __shared__ uint32_t s_idx[kThreads];
   if (st->code != GS_OK) return;
-  const int brick = blockIdx.x;
-  const uint2 r = ranges[brick];
+  const uint2 r = ranges[blockIdx.x];
   if (r.x == r.y) return;
+  const VInst& I = bt.in[inst_of_key(bt, blockIdx.x)];
+  const VGrid& g = I.g;
+  const float* dvol = dvol_all + I.vol_off;
+  const int brick = (int)(blockIdx.x - I.key_off);
   const int bx = brick % g.nb[0], by = (brick / g.nb[0]) % g.nb[1], bz = brick / (g.nb[0] * g.nb[1]);
   const int x0b = g.lo[0] + bx * kB, y0b = g.lo[1] + by * kB, z0b = g.lo[2] + bz * kB;
   const size_t sx = (size_t)g.dim[0], sxy = (size_t)g.dim[0] * g.dim[1];
@@ -470,16 +525,23 @@ __global__ void __launch_bounds__(kThreads)
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int cap_from_ws(int n, const gs_grid* grid, const int32_t* lo, const int32_t* dim,
-                const gs_opts* o, size_t ws_bytes, int64_t& cap) {
+int check_ptrs(const Plan& p, const float* mr, const float* sc, const float* qt, void* ws) {
+  if (p.n > 0 && (!mr || !sc || !qt)) return GS_ERR_ARG;
+  if (!ws || !aligned16(ws) || !aligned16(mr) || !aligned16(sc) || !aligned16(qt))
+    return GS_ERR_ARG;
+  return GS_OK;
+}
+
+int cap_from_ws(const gs_voxel_instance* inst, int n_inst, const gs_opts* o, size_t ws_bytes,
+                int64_t& cap) {
   Plan p0;
-  GS_TRY(make_plan(n, grid, lo, dim, o, 0, p0));
+  GS_TRY(make_plan(inst, n_inst, o, 0, p0));
   const size_t base = carve(nullptr, p0).bytes;
   if (ws_bytes < base) return GS_ERR_CAPACITY;
   int64_t c = (int64_t)((ws_bytes - base) / 16);
   while (c > 0) {
     Plan p;
-    GS_TRY(make_plan(n, grid, lo, dim, o, c, p));
+    GS_TRY(make_plan(inst, n_inst, o, c, p));
     if (carve(nullptr, p).bytes <= ws_bytes) break;
     c -= 64;
   }
@@ -487,17 +549,28 @@ int cap_from_ws(int n, const gs_grid* grid, const int32_t* lo, const int32_t* di
   return GS_OK;
 }
 
-int prepare(const float* mr, const float* sc, const float* qt, int n, const gs_grid* grid,
-            const int32_t* lo, const int32_t* dim, const gs_opts* o, void* ws, size_t ws_bytes,
-            Plan& p, Layout& L) {
-  if (n > 0 && (!mr || !sc || !qt)) return GS_ERR_ARG;
-  if (!ws || !aligned16(ws) || !aligned16(mr) || !aligned16(sc) || !aligned16(qt))
-    return GS_ERR_ARG;
+// Validates the table and the pointers (host only, before any launch), then plans the
+// workspace's pair capacity from its size.
+int prepare(const float* mr, const float* sc, const float* qt, const gs_voxel_instance* inst,
+            int n_inst, const gs_opts* o, void* ws, size_t ws_bytes, Plan& p, Layout& L) {
+  {
+    Plan p0;
+    GS_TRY(make_plan(inst, n_inst, o, 0, p0));
+    GS_TRY(check_ptrs(p0, mr, sc, qt, ws));
+  }
   int64_t cap = 0;
-  GS_TRY(cap_from_ws(n, grid, lo, dim, o, ws_bytes, cap));
-  GS_TRY(make_plan(n, grid, lo, dim, o, cap, p));
+  GS_TRY(cap_from_ws(inst, n_inst, o, ws_bytes, cap));
+  GS_TRY(make_plan(inst, n_inst, o, cap, p));
   L = carve(ws, p);
   return GS_OK;
+}
+
+int prep_and_scan(const Plan& p, const Layout& L, const float* mr, const float* sc,
+                  const float* qt, cudaStream_t s) {
+  GS_TRY(launch("vox_prep", k_vox_prep, dim3(p.nblocks), dim3(kThreads), 0, s, p.b,
+                (const float4*)mr, (const float4*)sc, (const float4*)qt, p.n, L.st, L.geo,
+                L.cov0, L.cov1, L.lo, L.hi, L.counts, L.block_sums));
+  return scan_block_sums(L.block_sums, L.block_offs, p.nblocks, L.st, p.cap, s);
 }
 
 int bin_bricks(const Plan& p, const Layout& L, const float* mr, const float* sc, const float* qt,
@@ -510,16 +583,13 @@ int bin_bricks(const Plan& p, const Layout& L, const float* mr, const float* sc,
     *svals = L.vals;
     return GS_OK;
   }
-  GS_TRY(launch("vox_prep", k_vox_prep, dim3(p.nblocks), dim3(kThreads), 0, s,
-                (const float4*)mr, (const float4*)sc, (const float4*)qt, p.n, p.g, p.cut2, L.st,
-                L.geo, L.cov0, L.cov1, L.lo, L.hi, L.counts, L.block_sums));
-  GS_TRY(scan_block_sums(L.block_sums, L.block_offs, p.nblocks, L.st, p.cap, s));
+  GS_TRY(prep_and_scan(p, L, mr, sc, qt, s));
   const bool odd = (p.sort.passes & 1) != 0;
   uint32_t* fk = odd ? L.keys_alt : L.keys;
   uint32_t* fv = odd ? L.vals_alt : L.vals;
-  GS_TRY(launch("vox_emit", k_vox_emit, dim3(p.nblocks), dim3(kThreads), 0, s,
+  GS_TRY(launch("vox_emit", k_vox_emit, dim3(p.nblocks), dim3(kThreads), 0, s, p.b,
                 (const uint32_t*)L.counts, (const short4*)L.lo, (const short4*)L.hi,
-                (const uint32_t*)L.block_offs, p.n, p.g, L.keys, L.vals, L.st,
+                (const uint32_t*)L.block_offs, p.n, p.n_keys, L.keys, L.vals, L.st,
                 (int64_t)((char*)fk - (char*)ws), (int64_t)((char*)fv - (char*)ws)));
   uint32_t* k = L.keys;
   uint32_t* v = L.vals;
@@ -536,10 +606,22 @@ int vox_fwd(const Plan& p, const Layout& L, const uint32_t* vals, float* vol, bo
   if (count)
     return launch("vox_count", k_vox_fwd<true>, grid, block, 0, s, (const uint2*)L.ranges, vals,
                   (const float4*)L.geo, (const float4*)L.cov0, (const float4*)L.cov1,
-                  (const short4*)L.lo, (const short4*)L.hi, p.g, vol, L.st);
+                  (const short4*)L.lo, (const short4*)L.hi, p.b, vol, L.st);
   return launch("vox_fwd", k_vox_fwd<false>, grid, block, 0, s, (const uint2*)L.ranges, vals,
                 (const float4*)L.geo, (const float4*)L.cov0, (const float4*)L.cov1,
-                (const short4*)L.lo, (const short4*)L.hi, p.g, vol, L.st);
+                (const short4*)L.lo, (const short4*)L.hi, p.b, vol, L.st);
+}
+
+gs_voxel_instance one(int n, const gs_grid* grid, const int32_t* lo, const int32_t* dim) {
+  gs_voxel_instance v;
+  memset(&v, 0, sizeof(v));
+  v.n = n;
+  if (grid) v.grid = *grid;
+  for (int k = 0; k < 3; ++k) {
+    v.roi_lo[k] = lo ? lo[k] : -1;
+    v.roi_dim[k] = dim ? dim[k] : 0;
+  }
+  return v;
 }
 
 }  // namespace
@@ -549,60 +631,53 @@ using namespace gs;
 
 extern "C" {
 
-size_t gs_voxelize_workspace_size(int n, const gs_grid* grid, const int32_t roi_lo[3],
-                                  const int32_t roi_dim[3], const gs_opts* opts,
-                                  int64_t max_pairs) {
+size_t gs_voxelize_batch_workspace_size(const gs_voxel_instance* inst, int n_inst,
+                                        const gs_opts* opts, int64_t max_pairs) {
   Plan p;
-  if (make_plan(n, grid, roi_lo, roi_dim, opts, max_pairs, p) != GS_OK) return 0;
+  if (make_plan(inst, n_inst, opts, max_pairs, p) != GS_OK) return 0;
   return carve(nullptr, p).bytes;
 }
 
-int gs_voxelize_count_pairs(const float* d_mean_rho, const float* d_scale, const float* d_quat,
-                            int n, const gs_grid* grid, const int32_t roi_lo[3],
-                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
-                            size_t ws_bytes, void* stream, int64_t* h_pairs) {
+int gs_voxelize_batch_count_pairs(const float* d_mean_rho, const float* d_scale,
+                                  const float* d_quat, const gs_voxel_instance* inst, int n_inst,
+                                  const gs_opts* opts, void* d_ws, size_t ws_bytes, void* stream,
+                                  int64_t* h_pairs) {
   if (!h_pairs) return GS_ERR_ARG;
   Plan p;
   Layout L;
-  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, n, grid, roi_lo, roi_dim, opts, d_ws, ws_bytes, p,
-                 L));
+  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, inst, n_inst, opts, d_ws, ws_bytes, p, L));
   cudaStream_t s = (cudaStream_t)stream;
   if (p.n == 0) {
     *h_pairs = 0;
     return GS_OK;
   }
-  GS_TRY(launch("vox_prep", k_vox_prep, dim3(p.nblocks), dim3(kThreads), 0, s,
-                (const float4*)d_mean_rho, (const float4*)d_scale, (const float4*)d_quat, p.n,
-                p.g, p.cut2, L.st, L.geo, L.cov0, L.cov1, L.lo, L.hi, L.counts, L.block_sums));
-  GS_TRY(scan_block_sums(L.block_sums, L.block_offs, p.nblocks, L.st, p.cap, s));
+  GS_TRY(prep_and_scan(p, L, d_mean_rho, d_scale, d_quat, s));
   gs_status st;
   GS_TRY(gs_read_status(d_ws, stream, &st));
   *h_pairs = st.pairs;
   return GS_OK;
 }
 
-int gs_voxelize(const float* d_mean_rho, const float* d_scale, const float* d_quat, int n,
-                const gs_grid* grid, const int32_t roi_lo[3], const int32_t roi_dim[3],
-                const gs_opts* opts, float* d_vol, void* d_ws, size_t ws_bytes, void* stream) {
+int gs_voxelize_batch(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                      const gs_voxel_instance* inst, int n_inst, const gs_opts* opts,
+                      float* d_vol, void* d_ws, size_t ws_bytes, void* stream) {
   if (!d_vol) return GS_ERR_ARG;
   Plan p;
   Layout L;
-  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, n, grid, roi_lo, roi_dim, opts, d_ws, ws_bytes, p,
-                 L));
+  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, inst, n_inst, opts, d_ws, ws_bytes, p, L));
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t *k, *v;
   GS_TRY(bin_bricks(p, L, d_mean_rho, d_scale, d_quat, s, d_ws, &k, &v));
   return vox_fwd(p, L, v, d_vol, false, s);
 }
 
-int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const float* d_quat,
-                            int n, const gs_grid* grid, const int32_t roi_lo[3],
-                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
-                            size_t ws_bytes, void* stream) {
+int gs_voxelize_batch_count_evals(const float* d_mean_rho, const float* d_scale,
+                                  const float* d_quat, const gs_voxel_instance* inst, int n_inst,
+                                  const gs_opts* opts, void* d_ws, size_t ws_bytes,
+                                  void* stream) {
   Plan p;
   Layout L;
-  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, n, grid, roi_lo, roi_dim, opts, d_ws, ws_bytes, p,
-                 L));
+  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, inst, n_inst, opts, d_ws, ws_bytes, p, L));
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t *k, *v;
   GS_TRY(bin_bricks(p, L, d_mean_rho, d_scale, d_quat, s, d_ws, &k, &v));
@@ -610,18 +685,17 @@ int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const
   return vox_fwd(p, L, v, nullptr, true, s);
 }
 
-int gs_voxelize_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
-                         int n, const gs_grid* grid, const int32_t roi_lo[3],
-                         const int32_t roi_dim[3], const gs_opts* opts, const float* d_dvol,
-                         float* d_g_mean_rho, float* d_g_scale, float* d_g_quat, int accumulate,
-                         int reuse, void* d_ws, size_t ws_bytes, void* stream) {
-  if (!d_dvol || (n > 0 && (!d_g_mean_rho || !d_g_scale || !d_g_quat))) return GS_ERR_ARG;
-  if (!aligned16(d_g_mean_rho) || !aligned16(d_g_scale) || !aligned16(d_g_quat))
-    return GS_ERR_ARG;
+int gs_voxelize_batch_backward(const float* d_mean_rho, const float* d_scale,
+                               const float* d_quat, const gs_voxel_instance* inst, int n_inst,
+                               const gs_opts* opts, const float* d_dvol, float* d_g_mean_rho,
+                               float* d_g_scale, float* d_g_quat, int accumulate, int reuse,
+                               void* d_ws, size_t ws_bytes, void* stream) {
   Plan p;
   Layout L;
-  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, n, grid, roi_lo, roi_dim, opts, d_ws, ws_bytes, p,
-                 L));
+  GS_TRY(prepare(d_mean_rho, d_scale, d_quat, inst, n_inst, opts, d_ws, ws_bytes, p, L));
+  if (!d_dvol || (p.n > 0 && (!d_g_mean_rho || !d_g_scale || !d_g_quat))) return GS_ERR_ARG;
+  if (!aligned16(d_g_mean_rho) || !aligned16(d_g_scale) || !aligned16(d_g_quat))
+    return GS_ERR_ARG;
   if (p.n == 0) return GS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t* v;
@@ -635,11 +709,62 @@ int gs_voxelize_backward(const float* d_mean_rho, const float* d_scale, const fl
   GS_TRY(launch("vox_bwd", k_vox_bwd, dim3((unsigned)p.n_keys), dim3(kThreads), 0, s,
                 (const uint2*)L.ranges, (const uint32_t*)v, (const float4*)L.geo,
                 (const float4*)L.cov0, (const float4*)L.cov1, (const short4*)L.lo,
-                (const short4*)L.hi, p.g, d_dvol, L.vgrad, (const gs_status*)L.st));
+                (const short4*)L.hi, p.b, d_dvol, L.vgrad, (const gs_status*)L.st));
   return launch("vox_chain", k_vox_chain, dim3(p.nblocks), dim3(kThreads), 0, s,
                 (const float4*)d_mean_rho, (const float4*)d_scale, (const float4*)d_quat, p.n,
                 (const float4*)L.vgrad, (float4*)d_g_mean_rho, (float4*)d_g_scale,
                 (float4*)d_g_quat, accumulate);
+}
+
+// ---- single volume = batch of one ----------------------------------------------------------
+
+size_t gs_voxelize_workspace_size(int n, const gs_grid* grid, const int32_t roi_lo[3],
+                                  const int32_t roi_dim[3], const gs_opts* opts,
+                                  int64_t max_pairs) {
+  if (!grid || !roi_lo || !roi_dim) return 0;
+  const gs_voxel_instance v = one(n, grid, roi_lo, roi_dim);
+  return gs_voxelize_batch_workspace_size(&v, 1, opts, max_pairs);
+}
+
+int gs_voxelize_count_pairs(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                            int n, const gs_grid* grid, const int32_t roi_lo[3],
+                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
+                            size_t ws_bytes, void* stream, int64_t* h_pairs) {
+  if (!grid || !roi_lo || !roi_dim) return GS_ERR_ARG;
+  const gs_voxel_instance v = one(n, grid, roi_lo, roi_dim);
+  return gs_voxelize_batch_count_pairs(d_mean_rho, d_scale, d_quat, &v, 1, opts, d_ws, ws_bytes,
+                                       stream, h_pairs);
+}
+
+int gs_voxelize(const float* d_mean_rho, const float* d_scale, const float* d_quat, int n,
+                const gs_grid* grid, const int32_t roi_lo[3], const int32_t roi_dim[3],
+                const gs_opts* opts, float* d_vol, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!grid || !roi_lo || !roi_dim) return GS_ERR_ARG;
+  const gs_voxel_instance v = one(n, grid, roi_lo, roi_dim);
+  return gs_voxelize_batch(d_mean_rho, d_scale, d_quat, &v, 1, opts, d_vol, d_ws, ws_bytes,
+                           stream);
+}
+
+int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                            int n, const gs_grid* grid, const int32_t roi_lo[3],
+                            const int32_t roi_dim[3], const gs_opts* opts, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+  if (!grid || !roi_lo || !roi_dim) return GS_ERR_ARG;
+  const gs_voxel_instance v = one(n, grid, roi_lo, roi_dim);
+  return gs_voxelize_batch_count_evals(d_mean_rho, d_scale, d_quat, &v, 1, opts, d_ws, ws_bytes,
+                                       stream);
+}
+
+int gs_voxelize_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
+                         int n, const gs_grid* grid, const int32_t roi_lo[3],
+                         const int32_t roi_dim[3], const gs_opts* opts, const float* d_dvol,
+                         float* d_g_mean_rho, float* d_g_scale, float* d_g_quat, int accumulate,
+                         int reuse, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!grid || !roi_lo || !roi_dim) return GS_ERR_ARG;
+  const gs_voxel_instance v = one(n, grid, roi_lo, roi_dim);
+  return gs_voxelize_batch_backward(d_mean_rho, d_scale, d_quat, &v, 1, opts, d_dvol,
+                                    d_g_mean_rho, d_g_scale, d_g_quat, accumulate, reuse, d_ws,
+                                    ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -145,6 +145,16 @@ class Projector:
         return tuple((t.data_ptr(), t._version) for t in ts)
 
 
+def block_offsets(sizes):
+    """Start of each instance's block in a batched image or volume (blocks start at multiples
+    of 64 floats); the last entry is the total length."""
+    out, off = [], 0
+    for n in sizes:
+        out.append(off)
+        off += (int(n) + 63) // 64 * 64
+    return out + [off]
+
+
 class BatchProjector:
     """Projects up to 32 independent instances (each its own Gaussians, views and W x H
     detector) with one kernel launch per pass.
@@ -163,7 +173,8 @@ class BatchProjector:
               for v, _, _ in instances]
         self.views = torch.cat(vs, 0).contiguous()
         self.shapes = [(int(v.shape[0]), int(H), int(W)) for v, (_, W, H) in zip(vs, instances)]
-        self.img_numel = sum(a * b * c for a, b, c in self.shapes)
+        self.offsets = block_offsets([a * b * c for a, b, c in self.shapes])
+        self.img_numel = self.offsets[-1]
         self.opts = B.opts(cut=cut, eps=eps, znear=znear, tile=tile)
         self.headroom = float(headroom)
         self.ws = None
@@ -180,11 +191,8 @@ class BatchProjector:
         return t
 
     def split(self, flat: torch.Tensor):
-        out, off = [], 0
-        for nv, H, W in self.shapes:
-            out.append(flat[off:off + nv * H * W].view(nv, H, W))
-            off += nv * H * W
-        return out
+        return [flat[o:o + nv * H * W].view(nv, H, W)
+                for o, (nv, H, W) in zip(self.offsets, self.shapes)]
 
     def _alloc(self, counts, pairs):
         t = self.table(counts)

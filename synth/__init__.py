@@ -176,3 +176,20 @@ def tiny_config(seed: int = 0):
     random rotations, densities U(0.05, 1); 8 cone views of 64x64; 64^3 grid."""
     g = gaussians(seed, 2000)
     return g, cone_views(8, 64, 64), cube_grid(64)
+
+
+def batch_specs(seeds=range(100, 116), sides=(128, 192, 256, 320, 384),
+                detectors=(256, 320, 384, 448, 512), views=(25, 75), gaussians=(10000, 80000),
+                n_ellipsoids=40):
+    """Uneven reconstructions for the batched form: per seed, a volume side, a detector side
+    and a view count drawn uniformly from the given sets/ranges, a Gaussian budget uniform in
+    the given range, and a random-ellipsoid phantom of that seed."""
+    out = []
+    for s in seeds:
+        rng = _rng(s)
+        out.append(dict(seed=int(s), side=int(rng.choice(sides)),
+                        det=int(rng.choice(detectors)),
+                        n_views=int(rng.integers(views[0], views[1] + 1)),
+                        n=int(rng.integers(gaussians[0], gaussians[1] + 1)),
+                        n_ellipsoids=int(n_ellipsoids)))
+    return out

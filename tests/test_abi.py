@@ -116,3 +116,26 @@ def test_batch_table_validation(built):
     t[6].W = 40
     rc = L.gs_project_batch(None, None, None, None, t, 8, ctypes.byref(o), 16, 16, 1 << 20, None)
     assert rc == binding.GS_ERR_ARG
+
+
+def test_voxel_batch_table_validation(built):
+    from paper_2604_01844_gb300 import binding
+
+    L = binding.lib()
+    o = binding.opts()
+    g = binding.GsGrid()
+    for k in range(3):
+        g.dims[k], g.origin[k], g.voxel[k] = 64, -1.0, 2 / 64
+    t = (binding.GsVoxelInstance * 33)()
+    for i in range(33):
+        t[i].n, t[i].grid = 100, g
+        for k in range(3):
+            t[i].roi_lo[k], t[i].roi_dim[k] = 0, 64
+    one = L.gs_voxelize_workspace_size(100, ctypes.byref(g), binding.i3((0, 0, 0)),
+                                       binding.i3((64, 64, 64)), ctypes.byref(o), 777)
+    assert L.gs_voxelize_batch_workspace_size(t, 1, ctypes.byref(o), 777) == one > 0
+    assert L.gs_voxelize_batch_workspace_size(t, 33, ctypes.byref(o), 0) == 0
+    t[2].roi_lo[1] = 1  # region leaves the grid
+    assert L.gs_voxelize_batch_workspace_size(t, 4, ctypes.byref(o), 0) == 0
+    t[2].roi_lo[1], t[2].n = 0, 0
+    assert L.gs_voxelize_batch_workspace_size(t, 4, ctypes.byref(o), 0) > 0

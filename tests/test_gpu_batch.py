@@ -73,7 +73,9 @@ def test_batch_backward_matches_oracle(orc, gsct, reuse):
     d, counts = _concat(inst)
     rng = np.random.default_rng(7)
     ws = [rng.standard_normal((len(v), H, W)) for *_, v, W, H in inst]
-    dimg = torch.from_numpy(np.concatenate([w.ravel() for w in ws]).astype(np.float32)).cuda()
+    dimg = torch.zeros(bp.img_numel, device="cuda")
+    for o, w in zip(bp.offsets, ws):
+        dimg[o:o + w.size] = torch.from_numpy(w.ravel().astype(np.float32)).cuda()
     if reuse:
         bp.forward(*d, counts)
     got = grads11(*bp.backward(*d, counts, dimg, reuse=reuse))
@@ -129,7 +131,7 @@ def test_batch_of_one_equals_single(gsct):
     views = synth.cone_views(3, 48, 40)
     d = to_dev(mr, sc, qt)
     bp = gsct.BatchProjector([(views, 48, 40)])
-    a = bp.forward(*d, [700]).view(3, 40, 48)
+    a = bp.split(bp.forward(*d, [700]))[0]
     b = gsct.Projector(views, 48, 40).forward(*d)
     assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
 
@@ -139,3 +141,66 @@ def test_batch_rejects_mismatched_counts(gsct):
     bp = gsct.BatchProjector([(views, 16, 16)])
     with pytest.raises(ValueError):
         bp.forward(*to_dev(*synth.gaussians(1, 3)), [2])
+
+
+# ---- batched voxelizer -------------------------------------------------------------------
+IDX_BAND = 2e-4  # index-space guard band of the voxel box edges
+
+# uneven instances: grids, regions (ragged, off-origin) and Gaussian counts differ; one empty
+VSPECS = [(400, 48, (0, 0, 0), (48, 48, 48)), (0, 32, (0, 0, 0), (32, 32, 32)),
+          (900, 72, (5, 9, 13), (37, 50, 23)), (150, 40, (8, 8, 8), (16, 16, 16)),
+          (700, 64, (0, 0, 0), (64, 64, 64))]
+
+
+def _vinstances(specs, seed=500, median=0.04):
+    out = []
+    for k, (n, side, lo, dim) in enumerate(specs):
+        mr, sc, qt = synth.gaussians(seed + k, max(n, 1), scale_median=median)
+        out.append((mr[:n], sc[:n], qt[:n], synth.cube_grid(side), lo, dim))
+    return out
+
+
+def test_batch_voxelize_matches_oracle_and_single(orc, gsct):
+    inst = _vinstances(VSPECS)
+    bv = gsct.BatchVoxelizer([(g, lo, dim) for *_, g, lo, dim in inst])
+    d, counts = _concat(inst)
+    vols = bv.split(bv.forward(*d, counts))
+    for (mr, sc, qt, grid, lo, dim), vol in zip(inst, vols):
+        single = gsct.Voxelizer(grid, lo, dim).forward(*to_dev(mr, sc, qt))
+        assert np.array_equal(vol.cpu().numpy(), single.cpu().numpy())
+        if mr.shape[0] == 0:
+            assert float(vol.abs().max()) == 0.0
+            continue
+        P = orc.params64(mr, sc, qt)
+        want, _ = orc.voxelize(P, grid, lo, dim)
+        allow = orc.voxelize_ambiguity(P, grid, lo, dim, REL_BAND, IDX_BAND)
+        err = np.abs(vol.cpu().numpy().astype(np.float64) - want)
+        assert (err <= IMG_TOL * np.abs(want).max() + allow + 1e-30).all()
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_batch_voxelize_backward_matches_oracle(orc, gsct, reuse):
+    import torch
+
+    inst = _vinstances(VSPECS, seed=600)
+    bv = gsct.BatchVoxelizer([(g, lo, dim) for *_, g, lo, dim in inst])
+    d, counts = _concat(inst)
+    rng = np.random.default_rng(9)
+    ws = [rng.standard_normal((dim[2], dim[1], dim[0])) for *_, dim in inst]
+    dvol = torch.zeros(bv.numel, device="cuda")
+    for o, w in zip(bv.offsets, ws):
+        dvol[o:o + w.size] = torch.from_numpy(w.ravel().astype(np.float32)).cuda()
+    if reuse:
+        bv.forward(*d, counts)
+    got = grads11(*bv.backward(*d, counts, dvol, reuse=reuse))
+    off = 0
+    for (mr, sc, qt, grid, lo, dim), w in zip(inst, ws):
+        n = mr.shape[0]
+        if n:
+            P = orc.params64(mr, sc, qt)
+            want = orc.voxelize_grad(P, grid, w, lo, dim)
+            flags = orc.voxel_flags(P, grid, lo, dim, REL_BAND, IDX_BAND)
+            clean = flags == 0
+            assert clean.mean() > 0.85
+            assert_grads_close(got[off:off + n], want, clean)
+        off += n
