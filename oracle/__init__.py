@@ -55,10 +55,11 @@ def lib():
                 "orc_project_pixels": (None, [i, P, i, P, i, i, d, d, d, i, P, P, i]),
                 "orc_project_ambiguity": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i]),
                 "orc_project_exact": (None, [i, P, i, P, i, i, P, i]),
-                "orc_pair_flags": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i]),
+                "orc_pair_flags": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i, i]),
+                "orc_min_q_rect": (d, [d, d, d, d, d, d, d, d, d]),
                 "orc_voxel_flags": (None, [i, P, P, P, P, d, d, d, P]),
                 "orc_pixel_ray": (None, [P, i, i, i, i, P, P]),
-                "orc_keys": (ll, [i, P, i, P, i, i, d, d, d, i, ll, P, P, P]),
+                "orc_keys": (ll, [i, P, i, P, i, i, d, d, d, i, ll, P, P, P, i]),
                 "orc_project_grad": (None, [i, P, i, P, i, i, d, d, d, P, P, i]),
                 "orc_voxelize": (ll, [i, P, P, P, P, d, P, i]),
                 "orc_voxelize_points": (None, [i, P, P, d, i, P, P, i]),
@@ -154,12 +155,21 @@ def project_ambiguity(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0):
     return allow
 
 
-def pair_flags(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0):
-    """Guard-band flags per (view, Gaussian), (V, N) int32 (see gs_oracle.cpp)."""
+def pair_flags(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0, tile=0):
+    """Guard-band flags per (view, Gaussian), (V, N) int32 (see gs_oracle.cpp); tile > 0 adds
+    the tight tile rule's flag (16) for tiles of that side."""
     flags = np.zeros((V.shape[0], P.shape[0]), dtype=np.int32)
     lib().orc_pair_flags(P.shape[0], _p(P), V.shape[0], _p(V), W, H, opts.cut, opts.eps,
-                         opts.znear, rel_band, px_band, _p(flags), nthreads)
+                         opts.znear, rel_band, px_band, _p(flags), nthreads, int(tile))
     return flags
+
+
+def min_q_rect(ca, cb, cc, px, py, x0, x1, y0, y1):
+    """Minimum of the footprint's quadratic form over a pixel-coordinate rectangle."""
+    return lib().orc_min_q_rect(ca, cb, cc, px, py, x0, x1, y0, y1)
+
+
+TILE_MARGIN = 1e-3  # the tight tile rule lists a tile if min q over it < (1 + margin) Q
 
 
 def voxel_flags(P, grid, roi_lo, roi_dim, rel_band, idx_band, cut=3.0):
@@ -184,17 +194,19 @@ def pixel_ray(view13, W, H, col, row):
     return o, d
 
 
-def keys(P, V, W, H, T, opts=Opts()):
-    """Sorted (key, gaussian) pairs and per-(view, Gaussian) tile counts (V, N)."""
+def keys(P, V, W, H, T, opts=Opts(), tight=True):
+    """Sorted (key, gaussian) pairs and per-(view, Gaussian) tile counts (V, N); tight=False
+    lists every tile of the bounding box."""
     n, nv = P.shape[0], V.shape[0]
     counts = np.zeros((nv, n), dtype=np.int32)
     L = lib()
+    t = 1 if tight else 0
     total = L.orc_keys(n, _p(P), nv, _p(V), W, H, opts.cut, opts.eps, opts.znear, T, 0,
-                       None, None, _p(counts))
+                       None, None, _p(counts), t)
     k = np.zeros(max(total, 1), dtype=np.int32)
     v = np.zeros(max(total, 1), dtype=np.int32)
     L.orc_keys(n, _p(P), nv, _p(V), W, H, opts.cut, opts.eps, opts.znear, T, total, _p(k), _p(v),
-               _p(counts))
+               _p(counts), t)
     return k[:total], v[:total], counts
 
 

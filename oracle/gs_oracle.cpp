@@ -459,15 +459,44 @@ void orc_project_ambiguity(int n, const double* g, int nv, const double* views, 
   }
 }
 
+// Minimum of q = ca u^2 + 2 cb u v + cc v^2 (u = x - px, v = y - py; ca, cc > 0 and
+// ca cc > cb^2) over the rectangle [x0, x1] x [y0, y1]: 0 when the centre lies inside;
+// otherwise the minimum sits on the boundary, and on each edge q is a convex quadratic in one
+// variable whose minimum is at its vertex clamped to the edge.
+double orc_min_q_rect(double ca, double cb, double cc, double px, double py, double x0,
+                      double x1, double y0, double y1) {
+  const double u0 = x0 - px, u1 = x1 - px, v0 = y0 - py, v1 = y1 - py;
+  if (u0 <= 0.0 && u1 >= 0.0 && v0 <= 0.0 && v1 >= 0.0) return 0.0;
+  auto q = [&](double u, double v) { return ca * u * u + 2.0 * cb * u * v + cc * v * v; };
+  auto on_row = [&](double v) { return q(std::clamp(-cb * v / ca, u0, u1), v); };
+  auto on_col = [&](double u) { return q(u, std::clamp(-cb * u / cc, v0, v1)); };
+  return std::min(std::min(on_row(v0), on_row(v1)), std::min(on_col(u0), on_col(u1)));
+}
+
+// Tight tile rule (an extension of the bounding-box keys of Sec. 3.5, after the tight
+// ellipse-tile tests of the splatting rasterizers the paper builds on): a tile of the clipped
+// box is listed only if the cut ellipse, enlarged to q < (1 + kTileMargin) Q, meets the
+// rectangle of pixel centres the tile shares with the box.  The margin keeps every tile that
+// holds a pixel inside the cut even under the rounding of an FP32 implementation.
+constexpr double kTileMargin = 1e-3;
+
+double tile_min_q(const Footprint<double>& f, int T, int tx, int ty) {
+  const double x0 = std::max(tx * T, f.ix0), x1 = std::min(tx * T + T - 1, f.ix1);
+  const double y0 = std::max(ty * T, f.iy0), y1 = std::min(ty * T + T - 1, f.iy1);
+  return orc_min_q_rect(f.ca, f.cb, f.cc, f.px, f.py, x0, x1, y0, y1);
+}
+
 // Guard-band flags per (view, Gaussian) pair, view-major (nv*n ints), for comparing an FP32
 // implementation with this FP64 definition:
 //   1: a box edge lies within px_band of an integer (the clipped pixel range may differ)
 //   2: some pixel of the box has |q - Q| <= rel_band * Q (its in/out decision may differ)
 //   4: cone depth within 1e-5 (relative) of the near plane
 //   8: density cut active and |A| within rel_band of eps or Q within rel_band of cut^2
+//  16: (T > 0) some tile of the box has its minimum q within rel_band * Q of the tight tile
+//      rule's threshold (its listing may differ)
 void orc_pair_flags(int n, const double* g, int nv, const double* views, int W, int H,
                     double cut, double eps, double znear, double rel_band, double px_band,
-                    int* flags, int nthreads) {
+                    int* flags, int nthreads, int T) {
   Opts o{cut, eps, znear};
   set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic)
@@ -489,6 +518,13 @@ void orc_pair_flags(int n, const double* g, int nv, const double* views, int W, 
         double aa = std::fabs(val(f.A));
         if (std::fabs(aa - eps) <= rel_band * eps) fl |= 8;
         if (f.Q > 0.0 && std::fabs(f.Q - cut * cut) <= rel_band * cut * cut) fl |= 8;
+      }
+      if (!f.culled && T > 0) {
+        for (int ty = f.iy0 / T; ty <= f.iy1 / T; ++ty)
+          for (int tx = f.ix0 / T; tx <= f.ix1 / T; ++tx)
+            if (std::fabs(tile_min_q(f, T, tx, ty) - (1.0 + kTileMargin) * f.Q) <=
+                rel_band * f.Q)
+              fl |= 16;
       }
       if (!f.culled) {
         int x0 = std::max(0, f.ix0 - 1), x1 = std::min(W - 1, f.ix1 + 1);
@@ -608,12 +644,13 @@ void orc_pixel_ray(const double* view, int W, int H, int col, int row, double* o
 }
 
 // Keys of Sec. 3.5: for every non-culled (view k, Gaussian i) pair, the tiles of side T that
-// its clipped pixel box touches; key = (k * TH + ty) * TW + tx.  Emitted in ascending i, tiles
-// row-major, then sorted stably by key, so inside one key the Gaussian indices ascend.
-// counts: nv*n (view-major) tiles per pair.  Returns the total; fills keys/vals if total <= cap.
+// its clipped pixel box touches (tight = 1: only those passing the tight tile rule);
+// key = (k * TH + ty) * TW + tx.  Emitted in ascending i, tiles row-major, then sorted stably
+// by key, so inside one key the Gaussian indices ascend.  counts: nv*n (view-major) tiles per
+// pair.  Returns the total; fills keys/vals if total <= cap.
 long long orc_keys(int n, const double* g, int nv, const double* views, int W, int H, double cut,
                    double eps, double znear, int T, long long cap, int* keys, int* vals,
-                   int* counts) {
+                   int* counts, int tight) {
   Opts o{cut, eps, znear};
   int TW = (W + T - 1) / T, TH = (H + T - 1) / T;
   std::vector<std::pair<long long, int>> kv;
@@ -627,6 +664,7 @@ long long orc_keys(int n, const double* g, int nv, const double* views, int W, i
       if (!f.culled) {
         for (int ty = f.iy0 / T; ty <= f.iy1 / T; ++ty)
           for (int tx = f.ix0 / T; tx <= f.ix1 / T; ++tx) {
+            if (tight && !(tile_min_q(f, T, tx, ty) < (1.0 + kTileMargin) * f.Q)) continue;
             kv.push_back({((long long)k * TH + ty) * TW + tx, i});
             ++c;
           }

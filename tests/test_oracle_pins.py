@@ -301,7 +301,7 @@ def test_keys_brute_force(orc):
     W, H, T = 40, 36, 8
     V = orc.views64(synth.cone_views(3, W, H))
     P = _rand_P(16, 60, median=0.04)
-    keys, vals, counts = orc.keys(P, V, W, H, T)
+    keys, vals, counts = orc.keys(P, V, W, H, T, tight=False)
     fp = orc.footprints(P, V, W, H)
     TW, TH = (W + T - 1) // T, (H + T - 1) // T
     assert np.all(np.diff(keys) >= 0)
@@ -325,6 +325,82 @@ def test_keys_brute_force(orc):
                     assert (y // T) * TW + x // T in want
             assert listed.get((k, i), set()) == want
             assert counts[k, i] == len(want)
+
+
+def test_min_q_rect_against_dense_sampling(orc):
+    """The rectangle minimum of the quadratic form: exact for an axis-aligned conic (sum of the
+    squared distances to the intervals), never above a dense sample's minimum, and within the
+    sampling resolution of it, for rectangles holding the centre, beside it and diagonal to it."""
+    rng = np.random.default_rng(3)
+    # axis-aligned: closed form
+    for _ in range(50):
+        ca, cc = rng.uniform(0.05, 2.0, 2)
+        px, py = rng.uniform(-10, 10, 2)
+        x0, y0 = rng.uniform(-12, 12, 2)
+        x1, y1 = x0 + rng.uniform(0, 8), y0 + rng.uniform(0, 8)
+        ddx = max(x0 - px, 0.0, px - x1)
+        ddy = max(y0 - py, 0.0, py - y1)
+        assert abs(orc.min_q_rect(ca, 0.0, cc, px, py, x0, x1, y0, y1) -
+                   (ca * ddx * ddx + cc * ddy * ddy)) <= 1e-12 * (1 + ca + cc) * 400
+    # general conics: dense sampling
+    for _ in range(200):
+        a, c = rng.uniform(0.05, 2.0, 2)
+        b = rng.uniform(-0.95, 0.95) * np.sqrt(a * c)
+        px, py = rng.uniform(-10, 10, 2)
+        x0, y0 = rng.uniform(-14, 10, 2)
+        x1, y1 = x0 + rng.uniform(0, 10), y0 + rng.uniform(0, 10)
+        got = orc.min_q_rect(a, b, c, px, py, x0, x1, y0, y1)
+        xs, ys = np.linspace(x0, x1, 401), np.linspace(y0, y1, 401)
+        X, Y = np.meshgrid(xs - px, ys - py)
+        qs = a * X * X + 2 * b * X * Y + c * Y * Y
+        grid_min = qs.min()
+        assert got <= grid_min + 1e-9 * (1 + grid_min)
+        h = max(x1 - x0, y1 - y0) / 400
+        slope = 2 * (a + abs(b) + c) * (abs(px) + abs(py) + 30)
+        assert grid_min - got <= slope * h + 1e-9
+
+
+def test_tight_keys_brute_force(orc):
+    """Tight tile rule: the listed tiles are a subset of the bounding box's, every pixel with
+    q < Q lies in a listed tile, every listed tile's rectangle minimum is under the enlarged
+    cut and every unlisted one's is not, and the rule removes tiles on a typical case."""
+    W, H, T = 48, 40, 8
+    V = orc.views64(synth.cone_views(3, W, H))
+    P = _rand_P(17, 80, median=0.05)
+    kt, vt, ct = orc.keys(P, V, W, H, T, tight=True)
+    kb, vb, cb = orc.keys(P, V, W, H, T, tight=False)
+    fp = orc.footprints(P, V, W, H)
+    TW, TH = (W + T - 1) // T, (H + T - 1) // T
+    assert np.all(np.diff(kt) >= 0)
+    same = kt[1:] == kt[:-1]
+    assert np.all(vt[1:][same] > vt[:-1][same])
+    tight, box = {}, {}
+    for kk, vv in zip(kt.tolist(), vt.tolist()):
+        tight.setdefault((kk // (TH * TW), vv), set()).add(kk % (TH * TW))
+    for kk, vv in zip(kb.tolist(), vb.tolist()):
+        box.setdefault((kk // (TH * TW), vv), set()).add(kk % (TH * TW))
+    yy, xx = np.mgrid[0:H, 0:W]
+    for k in range(3):
+        for i in range(80):
+            t_set, b_set = tight.get((k, i), set()), box.get((k, i), set())
+            assert t_set <= b_set
+            assert ct[k, i] == len(t_set)
+            if fp["culled"][k, i]:
+                continue
+            ca, cbb, cc = fp["ca"][k, i], fp["cb"][k, i], fp["cc"][k, i]
+            px, py, Q = fp["px"][k, i], fp["py"][k, i], fp["Q"][k, i]
+            ix0, ix1, iy0, iy1 = (int(fp[f][k, i]) for f in ("ix0", "ix1", "iy0", "iy1"))
+            dx, dy = xx - px, yy - py
+            q = ca * dx * dx + 2 * cbb * dx * dy + cc * dy * dy
+            inbox = (xx >= ix0) & (xx <= ix1) & (yy >= iy0) & (yy <= iy1)
+            for y, x in zip(*np.nonzero((q < Q) & inbox)):
+                assert (y // T) * TW + x // T in t_set
+            for tile in b_set:
+                tx, ty = tile % TW, tile // TW
+                m = orc.min_q_rect(ca, cbb, cc, px, py, max(tx * T, ix0), min(tx * T + T - 1, ix1),
+                                   max(ty * T, iy0), min(ty * T + T - 1, iy1))
+                assert (tile in t_set) == (m < (1 + orc.TILE_MARGIN) * Q)
+    assert len(kt) < 0.95 * len(kb)
 
 
 def test_density_cut_reading(orc):
