@@ -5,7 +5,8 @@
 // Pipeline of one call (all on `stream`, no host read-back):
 //   view_setup   per-view camera frame
 //   preprocess   one thread per (instance, view, Gaussian): local-affine (EWA) projection,
-//                integration factor mu, conic, 3-sigma box, tile count; warp-shuffle block sums
+//                integration factor mu, conic, 3-sigma box, and the count of the box's tiles
+//                that the cut ellipse actually meets (tight tile rule); warp-shuffle block sums
 //   scan         block sums -> offsets, pair total, capacity check
 //   emit         (key = instance key offset + view * tiles + tile, value = record index)
 //   radix sort   stable, over the key bits in use
@@ -74,6 +75,7 @@ struct Layout {
   float4* geo = nullptr;    // (px, py, A, e_cut): e_cut = -1/2 log2(e) * Q
   float4* conic = nullptr;  // -1/2 log2(e) * (a, 2b, c, 0): exponent = a'dx^2 + b'dx dy + c'dy^2
   short4* rect = nullptr;   // clipped inclusive pixel box (x0, y0, x1, y1); x0 > x1 if culled
+  uint32_t* tmask = nullptr;  // tight tile rule answers for the box's first 32 tiles
   uint32_t* counts = nullptr;
   uint32_t* block_sums = nullptr;
   uint32_t* block_offs = nullptr;
@@ -148,6 +150,7 @@ Layout carve(void* ws, const Plan& p) {
   L.geo = c.take<float4>(p.items);
   L.conic = c.take<float4>(p.items);
   L.rect = c.take<short4>(p.items);
+  L.tmask = c.take<uint32_t>(p.items);
   L.counts = c.take<uint32_t>(p.items);
   L.block_sums = c.take<uint32_t>(p.nblocks + 1);
   L.block_offs = c.take<uint32_t>(p.nblocks + 1);
@@ -160,6 +163,48 @@ Layout carve(void* ws, const Plan& p) {
   L.vals_alt = c.take<uint32_t>(p.cap);
   L.bytes = align_up(c.off, 256);
   return L;
+}
+
+// Whether a record's cut ellipse can reach the rectangle [x0, x1] x [y0, y1] (pixel-centre
+// coordinates): the maximum of its concave exponent e over the rectangle, which lies at the
+// centre if the centre is inside and otherwise on an edge (a 1-D concave quadratic there,
+// maximised at its clamped vertex), against the cut with a relative margin of 1e-3.  The
+// margin makes the answer a superset of the per-pixel FP32 test, so that a tile or block
+// dropped on a false answer never held a contribution.  h = (1/(2 c.x), 1/(2 c.z)).
+struct Ell {
+  float4 g, c;
+  float hx, hz;
+};
+__device__ __forceinline__ Ell make_ell(const float4 g, const float4 c) {
+  return Ell{g, c, 0.5f / c.x, 0.5f / c.z};
+}
+__device__ __forceinline__ float edge_max(float ca, float cb, float cc, float h, float u0,
+                                          float u1, float w) {
+  // max over u in [u0, u1] of ca u^2 + cb w u + cc w^2 (ca < 0, h = 1 / (2 ca))
+  const float u = fminf(fmaxf(-cb * w * h, u0), u1);
+  return fmaf(fmaf(ca, u, cb * w), u, cc * w * w);
+}
+__device__ __forceinline__ bool ellipse_meets_rect(const Ell& E, float x0, float x1, float y0,
+                                                   float y1) {
+  const float4 g = E.g, c = E.c;
+  const float u0 = x0 - g.x, u1 = x1 - g.x, v0 = y0 - g.y, v1 = y1 - g.y;
+  if (u0 <= 0.f && u1 >= 0.f && v0 <= 0.f && v1 >= 0.f) return true;
+  float m = fmaxf(edge_max(c.x, c.y, c.z, E.hx, u0, u1, v0),
+                  edge_max(c.x, c.y, c.z, E.hx, u0, u1, v1));
+  m = fmaxf(m, fmaxf(edge_max(c.z, c.y, c.x, E.hz, v0, v1, u0),
+                     edge_max(c.z, c.y, c.x, E.hz, v0, v1, u1)));
+  return m > g.w * 1.001f;
+}
+
+// Tight tile rule: tile (tx, ty) of side T is listed for a record whose clipped pixel box is
+// (x0, y0)-(x1, y1) only if its cut ellipse meets the pixel-centre rectangle the tile shares
+// with the box.  Preprocess evaluates it (and keeps the answers for up to 32 tiles as a bit
+// mask in the box's tile order); emit reads the mask, or re-evaluates for larger boxes.
+constexpr int kMaskTiles = 32;
+__device__ __forceinline__ bool tile_listed(const Ell& E, int T, int tx, int ty, int x0, int y0,
+                                            int x1, int y1) {
+  return ellipse_meets_rect(E, (float)max(tx * T, x0), (float)min(tx * T + T - 1, x1),
+                            (float)max(ty * T, y0), (float)min(ty * T + T - 1, y1));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -184,7 +229,8 @@ __global__ void __launch_bounds__(kThreads)
                  const float4* __restrict__ scale, const float4* __restrict__ quat,
                  int64_t items, const ViewFrame* __restrict__ frames, float4* __restrict__ geo,
                  float4* __restrict__ conic, short4* __restrict__ rect,
-                 uint32_t* __restrict__ counts, uint32_t* __restrict__ block_sums) {
+                 uint32_t* __restrict__ tmask, uint32_t* __restrict__ counts,
+                 uint32_t* __restrict__ block_sums) {
   __shared__ uint32_t warp_sums[kThreads / 32];
   const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   uint32_t cnt = 0;
@@ -200,10 +246,21 @@ __global__ void __launch_bounds__(kThreads)
                                 b.znear, o, x0, y0, x1, y1);
     if (live) {
       const int T = b.T;
-      cnt = (uint32_t)((x1 / T - x0 / T + 1) * (y1 / T - y0 / T + 1));
       const float k = gsd::kNegHalfLog2e;
-      geo[idx] = make_float4(o.px, o.py, o.A, k * o.Q);
-      conic[idx] = make_float4(k * o.ca, 2.f * k * o.cb, k * o.cc, 0.f);
+      const float4 gg = make_float4(o.px, o.py, o.A, k * o.Q);
+      const float4 cc = make_float4(k * o.ca, 2.f * k * o.cb, k * o.cc, 0.f);
+      const Ell E = make_ell(gg, cc);
+      uint32_t tm = 0u;
+      int bit = 0;
+      for (int ty = y0 / T; ty <= y1 / T; ++ty)
+        for (int tx = x0 / T; tx <= x1 / T; ++tx, ++bit)
+          if (tile_listed(E, T, tx, ty, x0, y0, x1, y1)) {
+            ++cnt;
+            if (bit < kMaskTiles) tm |= 1u << bit;
+          }
+      tmask[idx] = tm;
+      geo[idx] = gg;
+      conic[idx] = cc;
       rect[idx] = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
     } else {
       geo[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -228,7 +285,9 @@ __global__ void __launch_bounds__(kThreads)
 // emit: same block decomposition as preprocess; in-block exclusive prefix by warp scans
 __global__ void __launch_bounds__(kThreads)
     k_emit(const __grid_constant__ Batch b, const uint32_t* __restrict__ counts,
-           const short4* __restrict__ rect, const uint32_t* __restrict__ block_offs,
+           const float4* __restrict__ geo, const float4* __restrict__ conic,
+           const short4* __restrict__ rect, const uint32_t* __restrict__ tmask,
+           const uint32_t* __restrict__ block_offs,
            int64_t items, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
            gs_status* st, int64_t sorted_keys_off, int64_t sorted_vals_off) {
   __shared__ uint32_t warp_pre[kThreads / 32];
@@ -262,23 +321,53 @@ __global__ void __launch_bounds__(kThreads)
   const short4 r = rect[idx];
   const int T = b.T;
   const uint32_t kbase = (uint32_t)(I.key_off + (int64_t)v * I.TW * I.TH);
-  for (int ty = r.y / T; ty <= r.w / T; ++ty)
-    for (int tx = r.x / T; tx <= r.z / T; ++tx) {
+  const int ntx = r.z / T - r.x / T + 1, nty = r.w / T - r.y / T + 1;
+  if (ntx * nty <= kMaskTiles) {
+    uint32_t tm = tmask[idx];
+    while (tm) {
+      const int bit = __ffs(tm) - 1;
+      tm &= tm - 1u;
+      const int ty = r.y / T + bit / ntx, tx = r.x / T + bit % ntx;
       keys[off] = kbase + (uint32_t)(ty * I.TW + tx);
       vals[off] = (uint32_t)idx;
       ++off;
     }
+  } else {
+    const Ell E = make_ell(geo[idx], conic[idx]);
+    for (int ty = r.y / T; ty <= r.w / T; ++ty)
+      for (int tx = r.x / T; tx <= r.z / T; ++tx) {
+        if (!tile_listed(E, T, tx, ty, r.x, r.y, r.z, r.w)) continue;
+        keys[off] = kbase + (uint32_t)(ty * I.TW + tx);
+        vals[off] = (uint32_t)idx;
+        ++off;
+      }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
 // raster forward (and the in-cut evaluation counter)
 // ------------------------------------------------------------------------------------------
+// Exponent of a footprint record at pixel offset (dx, dy), base 2 and pre-scaled by
+// -1/2 log2(e): e = a' dx^2 + b' dx dy + c' dy^2, evaluated as ((a' dx + b' dy) dx + c' dy^2)
+// with the row terms b' dy and c' dy^2 shared by every pixel of a row.  The forward, the
+// evaluation counter and the backward all decide the cut e > e_cut with this exact sequence.
+__device__ __forceinline__ float row_b(const float4 c, float dy) { return c.y * dy; }
+__device__ __forceinline__ float row_c(const float4 c, float dy) { return (c.z * dy) * dy; }
+__device__ __forceinline__ float expo(const float4 c, float dx, float bdy, float cdy2) {
+  return fmaf(fmaf(c.x, dx, bdy), dx, cdy2);
+}
+
+// Raster CTA shape: warps own blocks of 4 rows x (8 PX) columns; a lane owns PX pixels of one
+// row, 8 columns apart, so that one record's row terms serve PX pixels.
 template <int T>
 struct RasterShape {
-  static constexpr int NT = T * T >= 256 ? 256 : T * T;  // threads per CTA
-  static constexpr int PIX = T * T / NT;                 // pixels per thread
-  static constexpr int NW = NT / 32;                     // warps
-  static constexpr int BW = T / 8;                       // 8x4 warp blocks per tile row
+  static constexpr int PX = T >= 16 ? 2 : 1;     // pixels per lane
+  static constexpr int BW = 8 * PX;              // warp block width
+  static constexpr int LBW = PX == 2 ? 4 : 3;    // log2(BW)
+  static constexpr int NBX = T / BW, NBY = T / 4, NB = NBX * NBY;  // warp blocks per tile
+  static constexpr int NW = NB < 8 ? NB : 8;     // warps per CTA
+  static constexpr int NT = 32 * NW;             // threads per CTA
+  static constexpr int BPW = NB / NW;            // warp blocks per warp
 };
 
 template <int T, bool COUNT>
@@ -288,7 +377,6 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
                  float* __restrict__ img, gs_status* st) {
   using S = RasterShape<T>;
-  constexpr int BH = T / 4;  // 8x4 warp blocks per tile column
   __shared__ float4 s_geo[S::NT];
   __shared__ float4 s_con[S::NT];
   __shared__ uint32_t s_mask[S::NT];  // bit k: the record's box touches warp block k
@@ -299,21 +387,23 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
   const int64_t lk = key - I.key_off;
   const int v = (int)(lk / (I.TW * I.TH)), tile = (int)(lk - (int64_t)v * I.TW * I.TH);
   const int W = I.W, H = I.H;
-  const int tx = tile % I.TW, ty = tile / I.TW;
-  const int tx0 = tx * T, ty0 = ty * T;
+  const int tx0 = (tile % I.TW) * T, ty0 = (tile / I.TW) * T;
   const uint2 r = ranges[key];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int wx0[S::PIX], wy0[S::PIX];
-  float fx[S::PIX], fy[S::PIX], acc[S::PIX];
+  int px0[S::BPW], py[S::BPW];
+  float fx[S::BPW][S::PX], fy[S::BPW], acc[S::BPW][S::PX];
   uint32_t cnt = 0;
 #pragma unroll
-  for (int k = 0; k < S::PIX; ++k) {
+  for (int k = 0; k < S::BPW; ++k) {
     const int wb = w + k * S::NW;
-    wx0[k] = tx0 + (wb % S::BW) * 8;
-    wy0[k] = ty0 + (wb / S::BW) * 4;
-    fx[k] = (float)(wx0[k] + (lane & 7));
-    fy[k] = (float)(wy0[k] + (lane >> 3));
-    acc[k] = 0.f;
+    px0[k] = tx0 + (wb % S::NBX) * S::BW + (lane & 7);
+    py[k] = ty0 + (wb / S::NBX) * 4 + (lane >> 3);
+    fy[k] = (float)py[k];
+#pragma unroll
+    for (int q = 0; q < S::PX; ++q) {
+      fx[k][q] = (float)(px0[k] + 8 * q);
+      acc[k][q] = 0.f;
+    }
   }
   if (COUNT && threadIdx.x == 0) s_cnt = 0ull;
   for (uint32_t base = r.x; base < r.y; base += S::NT) {
@@ -324,18 +414,18 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
       s_geo[threadIdx.x] = geo[rec];
       s_con[threadIdx.x] = conic[rec];
       const short4 bx = rect[rec];
-      const int bx0 = max(0, (bx.x - tx0) >> 3), bx1 = min(S::BW - 1, (bx.z - tx0) >> 3);
-      const int by0 = max(0, (bx.y - ty0) >> 2), by1 = min(BH - 1, (bx.w - ty0) >> 2);
+      const int bx0 = max(0, (bx.x - tx0) >> S::LBW), bx1 = min(S::NBX - 1, (bx.z - tx0) >> S::LBW);
+      const int by0 = max(0, (bx.y - ty0) >> 2), by1 = min(S::NBY - 1, (bx.w - ty0) >> 2);
       uint32_t mask = 0u;
       if (bx0 <= bx1) {
         const uint32_t row = (2u << bx1) - (1u << bx0);
-        for (int by = by0; by <= by1; ++by) mask |= row << (by * S::BW);
+        for (int by = by0; by <= by1; ++by) mask |= row << (by * S::NBX);
       }
       s_mask[threadIdx.x] = mask;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < S::PIX; ++k) {
+    for (int k = 0; k < S::BPW; ++k) {
       const int wb = w + k * S::NW;
       // each warp visits only the records that touch its block: a ballot over 32 records
       // at a time, then one iteration per set bit
@@ -347,13 +437,17 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
           bits &= bits - 1u;
           const float4 g = s_geo[j];
           const float4 c = s_con[j];
-          const float dx = fx[k] - g.x, dy = fy[k] - g.y;
-          const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, c.z * dy) * dy);
-          if (COUNT) {
-            cnt += (e > g.w && fx[k] < (float)W && fy[k] < (float)H) ? 1u : 0u;
-          } else {
-            const float val = ex2(e);
-            acc[k] = e > g.w ? fmaf(g.z, val, acc[k]) : acc[k];
+          const float dy = fy[k] - g.y;
+          const float bdy = row_b(c, dy), cdy2 = row_c(c, dy);
+#pragma unroll
+          for (int q = 0; q < S::PX; ++q) {
+            const float e = expo(c, fx[k][q] - g.x, bdy, cdy2);
+            if (COUNT) {
+              cnt += (e > g.w && fx[k][q] < (float)W && fy[k] < (float)H) ? 1u : 0u;
+            } else {
+              const float val = ex2(e);
+              acc[k][q] = e > g.w ? fmaf(g.z, val, acc[k][q]) : acc[k][q];
+            }
           }
         }
       }
@@ -369,43 +463,89 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
   }
   float* im = img + I.img_off + (int64_t)v * H * W;
 #pragma unroll
-  for (int k = 0; k < S::PIX; ++k) {
-    const int x = wx0[k] + (lane & 7), y = wy0[k] + (lane >> 3);
-    if (x < W && y < H) im[(size_t)y * W + x] = acc[k];
+  for (int k = 0; k < S::BPW; ++k) {
+    if (py[k] >= H) continue;
+#pragma unroll
+    for (int q = 0; q < S::PX; ++q) {
+      const int x = px0[k] + 8 * q;
+      if (x < W) im[(size_t)py[k] * W + x] = acc[k][q];
+    }
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // raster backward, per Gaussian (Sec. 3.5): one thread per (Gaussian, tile) pair, in three
-// phases per batch of kThreads pairs of a tile:
-//   1. chords: for every row of the pair's box inside the tile, the pixel interval where the
-//      quadratic exponent exceeds the cut (solved in closed form, widened by 1/100 pixel so
-//      that it contains every pixel the forward's test accepts), stored in shared memory,
-//      and the pair's total work W (pixels on its chords);
-//   2. a counting sort of the batch by W (32 buckets, largest first), so that the 32 pairs of
-//      a warp carry nearly equal work;
-//   3. each thread walks its pair's chords row by row, re-testing e > e_cut exactly like the
-//      forward, and accumulates the six moments of g exp(-q/2) with dy factored out per row;
-//      one pair of float4 atomics per pair.  No warp reductions, no pixels off the chords.
+// phases per batch of up to 2 x kThreads pairs of a tile:
+//   1. staging: the pair's record and its box clipped to the tile; a work estimate (rows in
+//      the tile x the chord length at the middle row);
+//   2. a counting sort of the batch by (rows, chord length), largest first;
+//   3. thread t walks sorted pair t and, when the batch holds more than kThreads pairs, also
+//      pair (m - 1 - t) from the light end: the 32 pairs a warp walks together have nearly
+//      the same loop shape, and every warp carries about the same total work, so no warp
+//      holds the block at its barrier for long.  Per row, the pixel interval where the
+//      exponent exceeds the cut is solved in closed form (widened by 1/100 pixel so that it
+//      contains every pixel the forward's test accepts), each pixel is re-tested exactly like
+//      the forward (same offsets, same expression), and the six moments of g exp(-q/2) are
+//      accumulated with dy factored out per row; one pair of float4 atomics per pair.
 // ------------------------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void bwd_walk(const float4 g, const float4 c, uint32_t box, int tx0,
+                                         int ty0, const float (*s_g)[T + 1], uint32_t rec,
+                                         float4* __restrict__ fpgrad) {
+  const int x0 = box & 0xFF, y0 = (box >> 8) & 0xFF, x1 = (box >> 16) & 0xFF, y1 = box >> 24;
+  if (x0 > x1) return;
+  const float inv2a = 0.5f / c.x;
+  float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+  for (int yy = y0; yy <= y1; ++yy) {
+    const float dy = (float)(ty0 + yy) - g.y;
+    const float B = row_b(c, dy), cdy2 = row_c(c, dy);
+    const float disc = B * B - 4.f * c.x * (cdy2 - g.w);
+    if (!(disc > 0.f)) continue;
+    const float ctr = g.x - (float)tx0 - B * inv2a, half = -sqrtf(disc) * inv2a;
+    const int xa = max(x0, (int)ceilf(ctr - half - 0.01f));
+    const int xb = min(x1, (int)floorf(ctr + half + 0.01f));
+    float r0 = 0.f, rx = 0.f, rxx = 0.f;
+    float fx = (float)(tx0 + xa);
+    for (int x = xa; x <= xb; ++x, fx += 1.f) {
+      const float dx = fx - g.x;
+      const float e = expo(c, dx, B, cdy2);
+      if (e > g.w) {
+        const float G = s_g[yy][x] * ex2(e);
+        const float Gx = G * dx;
+        r0 += G;
+        rx += Gx;
+        rxx = fmaf(Gx, dx, rxx);
+      }
+    }
+    s0 += r0;
+    sx += rx;
+    sxx += rxx;
+    sy = fmaf(dy, r0, sy);
+    sxy = fmaf(dy, rx, sxy);
+    syy = fmaf(dy * dy, r0, syy);
+  }
+  if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
+    atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(s0, sx, sy, sxx));
+    atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(sxy, syy, 0.f, 0.f));
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kThreads, 6)
     k_raster_bwd(const __grid_constant__ Batch b, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ vals, const float4* __restrict__ geo,
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
                  const float* __restrict__ dimg, float4* __restrict__ fpgrad,
                  const gs_status* st) {
-  constexpr int kBuckets = 32;
-  constexpr uint16_t kEmpty = 0x0001;  // chord with start 1 > end 0
+  constexpr int kRowCls = 16, kLenCls = 4, kBuckets = kRowCls * kLenCls;
+  constexpr int kBatch = 2 * kThreads;
   __shared__ float s_g[T][T + 1];
-  __shared__ float4 s_geo[kThreads];
-  __shared__ float4 s_con[kThreads];
-  __shared__ uint16_t s_ch[T][kThreads];  // per row: start | end << 8, relative to the tile
-  __shared__ uint32_t s_rec[kThreads];
-  __shared__ uint16_t s_work[kThreads];
-  __shared__ uint8_t s_y0[kThreads];
-  __shared__ uint8_t s_y1[kThreads];
-  __shared__ uint16_t s_perm[kThreads];
+  __shared__ float4 s_geo[kBatch];
+  __shared__ float4 s_con[kBatch];
+  __shared__ uint32_t s_rec[kBatch];
+  __shared__ uint32_t s_box[kBatch];  // tile-local x0 | y0 << 8 | x1 << 16 | y1 << 24
+  __shared__ uint8_t s_key[kBatch];
+  __shared__ uint16_t s_perm[kBatch];
   __shared__ uint32_t s_hist[kBuckets];
   if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
@@ -422,103 +562,66 @@ __global__ void __launch_bounds__(kThreads)
     const int x = tx0 + p % T, y = ty0 + p / T;
     s_g[p / T][p % T] = (x < W && y < H) ? dv[(size_t)y * W + x] : 0.f;
   }
-  for (uint32_t base = r.x; base < r.y; base += kThreads) {
-    const int m = (int)min((uint32_t)kThreads, r.y - base);
+  for (uint32_t base = r.x; base < r.y; base += kBatch) {
+    const int m = (int)min((uint32_t)kBatch, r.y - base);
     __syncthreads();
     if (t < kBuckets) s_hist[t] = 0;
     __syncthreads();
-    // phase 1: chords and work of pair t
-    if (t < m) {
-      const uint32_t rec = vals[base + t];
+    // phase 1: staging and work estimate of pairs t and t + kThreads
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = t + h * kThreads;
+      if (i >= m) break;
+      const uint32_t rec = vals[base + i];
       const short4 bx = rect[rec];
       const float4 g = geo[rec];
       const float4 c = conic[rec];  // e = c.x dx^2 + c.y dx dy + c.z dy^2 with c.x < 0
-      s_rec[t] = rec;
-      s_geo[t] = g;
-      s_con[t] = c;
+      s_rec[i] = rec;
+      s_geo[i] = g;
+      s_con[i] = c;
       const int x0 = max((int)bx.x, tx0) - tx0, x1 = min((int)bx.z, tx0 + T - 1) - tx0;
       const int y0 = max((int)bx.y, ty0) - ty0, y1 = min((int)bx.w, ty0 + T - 1) - ty0;
-      const float inv2a = 0.5f / c.x;
-      int work = 0, first = T, last = -1;
-      for (int yy = y0; yy <= y1; ++yy) {
-        uint16_t ch = kEmpty;
-        if (x0 <= x1) {
-          const float dy = (float)(ty0 + yy) - g.y;
-          const float B = c.y * dy;
-          const float disc = B * B - 4.f * c.x * (c.z * dy * dy - g.w);
-          if (disc > 0.f) {
-            const float ctr = g.x - (float)tx0 - B * inv2a, half = -sqrtf(disc) * inv2a;
-            const int xa = max(x0, (int)ceilf(ctr - half - 0.01f));
-            const int xb = min(x1, (int)floorf(ctr + half + 0.01f));
-            if (xa <= xb) {
-              ch = (uint16_t)(xa | (xb << 8));
-              work += xb - xa + 1;
-              first = min(first, yy);
-              last = yy;
-            }
-          }
-        }
-        s_ch[yy][t] = ch;
+      int rows = 0, len = 0;
+      if (x0 <= x1 && y0 <= y1) {
+        rows = y1 - y0 + 1;
+        const float dy = (float)(ty0 + ((y0 + y1) >> 1)) - g.y;
+        const float B = row_b(c, dy);
+        const float disc = B * B - 4.f * c.x * (row_c(c, dy) - g.w);
+        len = disc > 0.f ? min(x1 - x0 + 1, (int)(-sqrtf(disc) / c.x) + 1) : 1;
       }
-      s_work[t] = (uint16_t)work;
-      s_y0[t] = (uint8_t)(first < T ? first : 0);
-      s_y1[t] = (uint8_t)(last >= 0 ? last : 0);
-      const int bucket = kBuckets - 1 - min(kBuckets - 1, (work * kBuckets) / (T * T + 1));
+      s_box[i] = rows ? (uint32_t)(x0 | (y0 << 8) | (x1 << 16) | (y1 << 24)) : 0x00000001u;
+      const int rc = rows ? min(kRowCls - 1, ((rows - 1) * kRowCls) / T) : 0;
+      const int lc = min(kLenCls - 1, (len * kLenCls) / (T + 1));
+      const int bucket = rows ? (kRowCls - 1 - rc) * kLenCls + (kLenCls - 1 - lc) : kBuckets - 1;
+      s_key[i] = (uint8_t)bucket;
       atomicAdd(&s_hist[bucket], 1u);
     }
     __syncthreads();
-    // phase 2: counting sort by work (descending)
-    if (t == 0) {
-      uint32_t a = 0;
-      for (int k = 0; k < kBuckets; ++k) {
-        const uint32_t cnt = s_hist[k];
-        s_hist[k] = a;
-        a += cnt;
-      }
+    // phase 2: counting sort by (rows, chord length), descending: one warp scans the 64
+    // bucket counts (two per lane), then every pair takes its rank
+    if (t < 32) {
+      const uint32_t a0 = s_hist[2 * t], a1 = s_hist[2 * t + 1];
+      const uint32_t incl = gsd::warp_inclusive_scan(a0 + a1);
+      const uint32_t excl = incl - (a0 + a1);
+      s_hist[2 * t] = excl;
+      s_hist[2 * t + 1] = excl + a0;
     }
     __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = t + h * kThreads;
+      if (i < m) s_perm[atomicAdd(&s_hist[s_key[i]], 1u)] = (uint16_t)i;
+    }
+    __syncthreads();
+    // phase 3: sorted pair t, and its light partner m - 1 - t when the batch is over-full
     if (t < m) {
-      const int work = s_work[t];
-      const int bucket = kBuckets - 1 - min(kBuckets - 1, (work * kBuckets) / (T * T + 1));
-      s_perm[atomicAdd(&s_hist[bucket], 1u)] = (uint16_t)t;
+      const int j = s_perm[t];
+      bwd_walk<T>(s_geo[j], s_con[j], s_box[j], tx0, ty0, s_g, s_rec[j], fpgrad);
     }
-    __syncthreads();
-    if (t >= m) continue;
-    // phase 3: walk pair j's chords row by row
-    const int j = s_perm[t];
-    const int work = s_work[j];
-    if (work == 0) continue;
-    const float4 g = s_geo[j];
-    const float4 c = s_con[j];
-    const int ya = s_y0[j], yb = s_y1[j];
-    float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-    for (int yy = ya; yy <= yb; ++yy) {
-      const uint32_t ch = s_ch[yy][j];
-      const int xa = ch & 0xFF, xb = ch >> 8;
-      const float dy = (float)(ty0 + yy) - g.y, czdy = c.z * dy;
-      float dx = (float)(tx0 + xa) - g.x;
-      float r0 = 0.f, rx = 0.f, rxx = 0.f;
-      for (int x = xa; x <= xb; ++x, dx += 1.f) {
-        const float e = fmaf(c.x * dx, dx, fmaf(c.y, dx, czdy) * dy);
-        if (e > g.w) {
-          const float G = s_g[yy][x] * ex2(e);
-          const float Gx = G * dx;
-          r0 += G;
-          rx += Gx;
-          rxx = fmaf(Gx, dx, rxx);
-        }
-      }
-      s0 += r0;
-      sx += rx;
-      sxx += rxx;
-      sy = fmaf(dy, r0, sy);
-      sxy = fmaf(dy, rx, sxy);
-      syy = fmaf(dy * dy, r0, syy);
-    }
-    if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
-      const uint32_t rec = s_rec[j];
-      atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(s0, sx, sy, sxx));
-      atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(sxy, syy, 0.f, 0.f));
+    const int t2 = m - 1 - t;
+    if (t2 >= kThreads) {
+      const int j = s_perm[t2];
+      bwd_walk<T>(s_geo[j], s_con[j], s_box[j], tx0, ty0, s_g, s_rec[j], fpgrad);
     }
   }
 }
@@ -628,7 +731,8 @@ int setup_and_preprocess(const Plan& p, const Layout& L, const float* mr, const 
                 views, p.total_v, L.frames, L.st));
   GS_TRY(launch("preprocess", k_preprocess, dim3(p.nblocks), dim3(kThreads), 0, s, p.b,
                 (const float4*)mr, (const float4*)sc, (const float4*)qt, p.items,
-                (const ViewFrame*)L.frames, L.geo, L.conic, L.rect, L.counts, L.block_sums));
+                (const ViewFrame*)L.frames, L.geo, L.conic, L.rect, L.tmask, L.counts,
+                L.block_sums));
   return scan_block_sums(L.block_sums, L.block_offs, p.nblocks, L.st, p.cap, s);
 }
 
@@ -653,7 +757,8 @@ int bin_pairs(const Plan& p, const Layout& L, const float* mr, const float* sc, 
   uint32_t* fk = odd ? L.keys_alt : L.keys;
   uint32_t* fv = odd ? L.vals_alt : L.vals;
   GS_TRY(launch("emit", k_emit, dim3(p.nblocks), dim3(kThreads), 0, s, p.b,
-                (const uint32_t*)L.counts, (const short4*)L.rect, (const uint32_t*)L.block_offs,
+                (const uint32_t*)L.counts, (const float4*)L.geo, (const float4*)L.conic,
+                (const short4*)L.rect, (const uint32_t*)L.tmask, (const uint32_t*)L.block_offs,
                 p.items, L.keys, L.vals, L.st, (int64_t)((char*)fk - (char*)ws),
                 (int64_t)((char*)fv - (char*)ws)));
   GS_TRY(radix_sort(&k, &v, L.keys_alt, L.vals_alt, L.hist, p.sort, L.st, p.cap, s));

@@ -99,9 +99,9 @@ def test_keys_and_sort_order_bit_exact(orc, gsct, tile):
     W = H = 64
     mr, sc, qt, views = _case(6, 2000, 8, W, H)
     P, V = orc.params64(mr, sc, qt), orc.views64(views)
-    keys_o, vals_o, counts_o = orc.keys(P, V, W, H, tile)
-    flags = orc.pair_flags(P, V, W, H, REL_BAND, px_band(W, H))
-    amb = (flags & 5) != 0  # box-edge or near-plane ambiguity changes keys
+    keys_o, vals_o, counts_o = orc.keys(P, V, W, H, tile)  # tight tile rule
+    flags = orc.pair_flags(P, V, W, H, REL_BAND, px_band(W, H), tile=tile)
+    amb = (flags & 21) != 0  # box-edge, near-plane or tile-rule ambiguity changes keys
     proj = gsct.Projector(views, W, H, tile=tile)
     proj.forward(*to_dev(mr, sc, qt))
     keys_g, recs_g = proj.read_pairs()
