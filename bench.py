@@ -289,6 +289,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras:
         out["time_to_psnr"] = time_to_psnr(device)
         out["learned_init"] = learned_vs_plain(device)
+        out["batched"] = batched_learned_vs_plain(device)
         out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
@@ -411,6 +412,138 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
     return out
 
 
+def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5,
+                             n_train=48, train_steps=3000, seq_steps=5):
+    """16 uneven reconstructions (synth.batch_specs: volumes 128^3-384^3, 25-75 views of
+    256^2-512^2, 10k-80k Gaussians, 40-ellipsoid phantoms) advanced together: one batched
+    rasterizer and voxelizer call per pass, the whole step in one CUDA graph.  Reports the
+    graph step time against the same instances stepped one by one (each in its own graph),
+    and the GPU time until every instance reaches target_db with the per-brick MLP
+    initializer (trained here on n_train phantoms of the same size distribution, other seeds)
+    against the FDK-gradient initialisation; initialisation time included."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300 import initializer as I
+    from paper_2604_01844_gb300.batch import BatchGraphStep, BatchReconstruction, batch_to_psnr
+    from paper_2604_01844_gb300.mlp import BrickMLP
+    from paper_2604_01844_gb300.recon import (GraphStep, PhantomProblem, ReconConfig,
+                                               Reconstruction, fdk_volume, gradient_init)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    # training set: phantoms drawn like the instances (other seeds)
+    e0 = ev()
+    Xs, Ts = [], []
+    for sp in synth.batch_specs(seeds=[10 ** 6 + j for j in range(n_train)]):
+        v = synth.cone_views(sp["n_views"], sp["det"], sp["det"])
+        X, T = I.training_set([sp["seed"]], v, sp["det"], sp["det"], synth.cube_grid(sp["side"]),
+                              device=device)
+        Xs.append(X)
+        Ts.append(T)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    mlp = BrickMLP(seed=0, device=device)
+    hist = I.train(mlp, X, T, steps=train_steps, batch=1024, lr=3e-4)
+    e1 = ev()
+    torch.cuda.synchronize()
+    out = {"workload": "16 uneven reconstructions (seeds 100-115): volumes 128^3-384^3, "
+                       "25-75 cone views of 256^2-512^2, 10k-80k Gaussians",
+           "train_ms": round(e0.elapsed_time(e1), 1), "train_bricks": int(X.shape[0]),
+           "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)]}
+    del X, T
+    specs = synth.batch_specs()
+    probs, grids, views = [], [], []
+    for sp in specs:
+        v = synth.cone_views(sp["n_views"], sp["det"], sp["det"])
+        g = synth.cube_grid(sp["side"])
+        probs.append(PhantomProblem(synth.ellipsoid_phantom(sp["seed"], sp["n_ellipsoids"]), v,
+                                    sp["det"], sp["det"], g, device=device))
+        grids.append(g)
+        views.append(v)
+    gts, peaks = [p.gt for p in probs], [p.peak for p in probs]
+    us = [np.random.default_rng(sp["seed"]).random((sp["n"], 4)).astype(np.float32)
+          for sp in specs]
+    # warm the MLP inference path once outside the timing
+    I.learned_init(mlp, fdk_volume(probs[0], grids[0]), grids[0], specs[0]["n"], us[0])
+
+    def init(kind):
+        torch.cuda.synchronize()
+        a = ev()
+        inst, n_mlp = [], 0
+        for sp, prob, g, v, u in zip(specs, probs, grids, views, us):
+            fdk = fdk_volume(prob, g)
+            if kind == "plain":
+                mr, sc, q = gradient_init(fdk, g, sp["n"], u)
+            else:
+                mr, sc, q, nm = I.learned_init(mlp, fdk, g, sp["n"], u)
+                n_mlp += nm
+            inst.append(dict(views=v, W=sp["det"], H=sp["det"], target=prob.proj, grid=g,
+                             mean_rho=mr, scale=sc, quat=q))
+        b = ev()
+        torch.cuda.synchronize()
+        for x in inst:
+            for key in ("mean_rho", "scale", "quat"):
+                x[key] = x[key].cpu().numpy()
+        return inst, a.elapsed_time(b), n_mlp
+
+    plain_lr = dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)
+    low_lr = dict(lr_mean=1e-4, lr_rho=2e-2, lr_scale=2.5e-3, lr_quat=1e-3)
+    # step time: batched graph vs the same instances one by one (each its own graph)
+    inst, _, _ = init("plain")
+    rec = BatchReconstruction(inst, cfg=ReconConfig(**plain_lr), device=device)
+    g = BatchGraphStep(rec, warmup=1)
+    g()
+    torch.cuda.synchronize()
+    a = ev()
+    for _ in range(seq_steps):
+        g()
+    b = ev()
+    torch.cuda.synchronize()
+    batched_ms = a.elapsed_time(b) / seq_steps
+    pairs = int(rec.projector.capacity)
+    del rec, g
+    seq_ms = 0.0
+    for x in inst:
+        r = Reconstruction(x["views"], x["W"], x["H"], x["target"], x["grid"], x["mean_rho"],
+                           x["scale"], x["quat"], cfg=ReconConfig(**plain_lr), device=device)
+        gs = GraphStep(r, warmup=1)
+        gs()
+        torch.cuda.synchronize()
+        a = ev()
+        for _ in range(seq_steps):
+            gs()
+        b = ev()
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(b) / seq_steps
+        del r, gs
+    out["step_ms_batched_graph"] = round(batched_ms, 3)
+    out["step_ms_one_by_one_graphs"] = round(seq_ms, 3)
+    out["pair_capacity"] = pairs
+    for kind, lr_sets in (("plain", [plain_lr]), ("learned", [plain_lr, low_lr])):
+        inst, init_ms, n_mlp = init(kind)
+        runs = []
+        for lrs in lr_sets:
+            rec = BatchReconstruction(inst, cfg=ReconConfig(**lrs), device=device)
+            reached, last, iters, ms = batch_to_psnr(rec, gts, peaks, max_iters, target_db,
+                                                     eval_every)
+            ok = all(r is not None for r in reached)
+            runs.append({"lr_mean": lrs["lr_mean"], "all_reached": ok, "iters": iters,
+                         "ms_optimise": round(ms, 1), "ms_total": round(ms + init_ms, 1),
+                         "iters_per_instance": [r[0] if r else None for r in reached],
+                         "psnr_final_min": round(min(last), 2)})
+            del rec
+        best = min((r for r in runs if r["all_reached"]), key=lambda r: r["ms_total"],
+                   default=None)
+        out[kind] = {"init_ms": round(init_ms, 1), "gaussians_from_mlp": n_mlp, "runs": runs,
+                     "best_ms_to_target": best["ms_total"] if best else None}
+    return out
+
+
 def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     """gs_fit_volume of n Gaussians to a side^3 ground truth (120-ellipsoid phantom):
     Gaussian-voxel evaluations per second of the fit iterations (forward voxelization's
@@ -444,6 +577,13 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
+    # per-kernel breakdown from one more (separately timed) pass of the same iterations
+    B.timing_reset()
+    B.timing_enable(True)
+    f.run(gt, iters, opts, None, loss)
+    per_kernel = {k: round(v[1] / iters, 3) for k, v in
+                  sorted(B.timing_read().items(), key=lambda kv: -kv[1][1])}
+    B.timing_enable(False)
     st = f.status()
     vox = g.Voxelizer(grid, device=device)
     evals = vox.count_evals(*f.params)
@@ -452,7 +592,8 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     return {"workload": f"gs_fit_volume, {n} Gaussians, {side}^3 ground truth, bricks 16^3",
             "ms_per_iter": round(ms, 3), "voxel_evals_per_iter": evals,
             "value": evals / (ms * 1e-3), "unit": "Gaussian-voxel evals/s",
-            "status": int(st.code), "loss_last": float(loss[-1].item())}
+            "status": int(st.code), "loss_last": float(loss[-1].item()),
+            "kernels_ms_per_iter": per_kernel}
 
 
 def read_traffic(kernel: str):

@@ -108,8 +108,6 @@ __global__ void __launch_bounds__(kThreads)
 // SSIM 2D
 // ------------------------------------------------------------------------------------------
 constexpr int kR = 5;            // window radius (11 taps)
-constexpr int kTile = 16;        // output tile side
-constexpr int kIn = kTile + 2 * kR;  // 26
 
 __device__ __forceinline__ void window_weights(float* w) {
   // normalised 11-tap Gaussian, sigma 1.5
@@ -124,89 +122,133 @@ __device__ __forceinline__ void window_weights(float* w) {
   }
 }
 
+// Both SSIM 2D kernels work on 32 x 32 output tiles with a 5-pixel halo staged in shared
+// memory and register blocking in the two separable passes: the horizontal pass gives each
+// thread 4 adjacent outputs of one row (14 staged inputs serve all 4), the vertical pass 4
+// adjacent outputs of one column (14 filtered rows serve all 4).
+constexpr int kT2 = 32;              // output tile side
+constexpr int kIn2 = kT2 + 2 * kR;   // 42
+constexpr int kG = 4;                // outputs per thread in each pass
+constexpr int kSsimThreads = 256;
+static_assert(kT2 * (kT2 / kG) == kSsimThreads, "vertical pass: one thread per 4-row group");
+
+__device__ __forceinline__ void window_regs(const float* w, float wr[2 * kR + 1]) {
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k) wr[k] = w[k];
+}
+
 // Kernel 1: moments, SSIM, and the maps m1 = dS/dmu_x - 2 mu_x dS/dsxx - mu_y dS/dsxy,
 // m2 = dS/dsxx, m3 = dS/dsxy, all multiplied by -weight / N (the loss is weight * (1 - SSIM)).
-__global__ void __launch_bounds__(kTile * kTile)
+__global__ void __launch_bounds__(kSsimThreads)
     k_ssim2d_fwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W, float C1,
                  float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
                  int64_t plane) {
   __shared__ float w[2 * kR + 1];
-  __shared__ float sx[kIn][kIn + 1], sy[kIn][kIn + 1];
-  __shared__ float hm[5][kIn][kTile + 1];
+  __shared__ float sx[kIn2][kIn2 + 1], sy[kIn2][kIn2 + 1];
+  __shared__ float hm[5][kIn2][kT2 + 1];
   window_weights(w);
   const int img = blockIdx.z;
-  const int x0 = blockIdx.x * kTile - kR, y0 = blockIdx.y * kTile - kR;
+  const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
   const float* Xi = X + (size_t)img * H * W;
   const float* Yi = Y + (size_t)img * H * W;
-  const int tid = threadIdx.y * kTile + threadIdx.x;
-  for (int p = tid; p < kIn * kIn; p += kTile * kTile) {
-    const int r = p / kIn, c = p % kIn, y = y0 + r, x = x0 + c;
+  const int tid = threadIdx.x;
+  for (int p = tid; p < kIn2 * kIn2; p += kSsimThreads) {
+    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
     const bool in = x >= 0 && x < W && y >= 0 && y < H;
     sx[r][c] = in ? Xi[(size_t)y * W + x] : 0.f;
     sy[r][c] = in ? Yi[(size_t)y * W + x] : 0.f;
   }
   __syncthreads();
-  for (int p = tid; p < kIn * kTile; p += kTile * kTile) {
-    const int r = p / kTile, c = p % kTile;
-    float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+  float wr[2 * kR + 1];
+  window_regs(w, wr);
+  // horizontal pass: kIn2 rows x (kT2 / kG) groups of kG outputs
+  for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
+    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
+    float acc[5][kG];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float u = sx[r][c + k], v = sy[r][c + k], wk = w[k];
-      a = fmaf(wk, u, a);
-      b = fmaf(wk, v, b);
-      aa = fmaf(wk, u * u, aa);
-      bb = fmaf(wk, v * v, bb);
-      ab = fmaf(wk, u * v, ab);
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < kG + 2 * kR; ++i) {
+      const float u = sx[r][c0 + i], v = sy[r][c0 + i];
+      const float uu = u * u, vv = v * v, uv = u * v;
+#pragma unroll
+      for (int j = 0; j < kG; ++j) {
+        const int k = i - j;
+        if (k < 0 || k > 2 * kR) continue;
+        acc[0][j] = fmaf(wr[k], u, acc[0][j]);
+        acc[1][j] = fmaf(wr[k], v, acc[1][j]);
+        acc[2][j] = fmaf(wr[k], uu, acc[2][j]);
+        acc[3][j] = fmaf(wr[k], vv, acc[3][j]);
+        acc[4][j] = fmaf(wr[k], uv, acc[4][j]);
+      }
     }
-    hm[0][r][c] = a; hm[1][r][c] = b; hm[2][r][c] = aa; hm[3][r][c] = bb; hm[4][r][c] = ab;
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
   }
   __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+  // vertical pass: column tx, rows ty0 .. ty0 + kG - 1
+  const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
+  float mo[5][kG];
 #pragma unroll
-  for (int k = 0; k <= 2 * kR; ++k) {
-    const float wk = w[k];
-    mx = fmaf(wk, hm[0][ty + k][tx], mx);
-    my = fmaf(wk, hm[1][ty + k][tx], my);
-    exx = fmaf(wk, hm[2][ty + k][tx], exx);
-    eyy = fmaf(wk, hm[3][ty + k][tx], eyy);
-    exy = fmaf(wk, hm[4][ty + k][tx], exy);
+  for (int m = 0; m < 5; ++m)
+#pragma unroll
+    for (int j = 0; j < kG; ++j) mo[m][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kG + 2 * kR; ++i) {
+    float h[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) h[m] = hm[m][ty0 + i][tx];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int k = i - j;
+      if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) mo[m][j] = fmaf(wr[k], h[m], mo[m][j]);
+    }
   }
-  const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-  const float A = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
-  const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
-  const float S = (A * Bn) / (C * D);
-  const int x = blockIdx.x * kTile + tx, y = blockIdx.y * kTile + ty;
-  const bool valid = x < W && y < H;
+  const int x = blockIdx.x * kT2 + tx;
   float contrib = 0.f;
-  if (valid) {
-    const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
-    const float dsxx = -S / D;
-    const float dsxy = 2.f * A / (C * D);
-    const size_t o = (size_t)img * H * W + (size_t)y * W + x;
-    maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
-    maps[plane + o] = gscale * dsxx;
-    maps[2 * plane + o] = gscale * dsxy;
-    contrib = 1.f - S;
+#pragma unroll
+  for (int j = 0; j < kG; ++j) {
+    const int y = blockIdx.y * kT2 + ty0 + j;
+    const float mx = mo[0][j], my = mo[1][j];
+    const float sxx = mo[2][j] - mx * mx, syy = mo[3][j] - my * my, sxy = mo[4][j] - mx * my;
+    const float A = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
+    const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
+    const float S = (A * Bn) / (C * D);
+    if (x < W && y < H) {
+      const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
+      const float dsxx = -S / D;
+      const float dsxy = 2.f * A / (C * D);
+      const size_t o = (size_t)img * H * W + (size_t)y * W + x;
+      maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
+      maps[plane + o] = gscale * dsxx;
+      maps[2 * plane + o] = gscale * dsxy;
+      contrib += 1.f - S;
+    }
   }
   if (loss) block_add(contrib * (-gscale), loss);
 }
 
 // Kernel 2: dL/dx = w * m1 + 2 x (w * m2) + y (w * m3).
-__global__ void __launch_bounds__(kTile * kTile)
+__global__ void __launch_bounds__(kSsimThreads)
     k_ssim2d_bwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W,
                  const float* __restrict__ maps, int64_t plane, float* __restrict__ grad,
                  int accumulate) {
   __shared__ float w[2 * kR + 1];
-  __shared__ float sm[3][kIn][kIn + 1];
-  __shared__ float hm[3][kIn][kTile + 1];
+  __shared__ float sm[3][kIn2][kIn2 + 1];
+  __shared__ float hm[3][kIn2][kT2 + 1];
   window_weights(w);
   const int img = blockIdx.z;
-  const int x0 = blockIdx.x * kTile - kR, y0 = blockIdx.y * kTile - kR;
-  const int tid = threadIdx.y * kTile + threadIdx.x;
+  const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
+  const int tid = threadIdx.x;
   const size_t base = (size_t)img * H * W;
-  for (int p = tid; p < kIn * kIn; p += kTile * kTile) {
-    const int r = p / kIn, c = p % kIn, y = y0 + r, x = x0 + c;
+  for (int p = tid; p < kIn2 * kIn2; p += kSsimThreads) {
+    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
     const bool in = x >= 0 && x < W && y >= 0 && y < H;
     const size_t o = base + (size_t)y * W + x;
     sm[0][r][c] = in ? maps[o] : 0.f;
@@ -214,33 +256,63 @@ __global__ void __launch_bounds__(kTile * kTile)
     sm[2][r][c] = in ? maps[2 * plane + o] : 0.f;
   }
   __syncthreads();
-  for (int p = tid; p < kIn * kTile; p += kTile * kTile) {
-    const int r = p / kTile, c = p % kTile;
-    float a = 0.f, b = 0.f, d = 0.f;
+  float wr[2 * kR + 1];
+  window_regs(w, wr);
+  for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
+    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
+    float acc[3][kG];
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float wk = w[k];
-      a = fmaf(wk, sm[0][r][c + k], a);
-      b = fmaf(wk, sm[1][r][c + k], b);
-      d = fmaf(wk, sm[2][r][c + k], d);
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < kG + 2 * kR; ++i) {
+      float u[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) u[m] = sm[m][r][c0 + i];
+#pragma unroll
+      for (int j = 0; j < kG; ++j) {
+        const int k = i - j;
+        if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[m][j] = fmaf(wr[k], u[m], acc[m][j]);
+      }
     }
-    hm[0][r][c] = a; hm[1][r][c] = b; hm[2][r][c] = d;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
   }
   __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * kTile + tx, y = blockIdx.y * kTile + ty;
-  if (x >= W || y >= H) return;
-  float f1 = 0.f, f2 = 0.f, f3 = 0.f;
+  const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
+  float f[3][kG];
 #pragma unroll
-  for (int k = 0; k <= 2 * kR; ++k) {
-    const float wk = w[k];
-    f1 = fmaf(wk, hm[0][ty + k][tx], f1);
-    f2 = fmaf(wk, hm[1][ty + k][tx], f2);
-    f3 = fmaf(wk, hm[2][ty + k][tx], f3);
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int j = 0; j < kG; ++j) f[m][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kG + 2 * kR; ++i) {
+    float h[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) h[m] = hm[m][ty0 + i][tx];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int k = i - j;
+      if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) f[m][j] = fmaf(wr[k], h[m], f[m][j]);
+    }
   }
-  const size_t o = base + (size_t)y * W + x;
-  const float g = f1 + 2.f * X[o] * f2 + Y[o] * f3;
-  grad[o] = accumulate ? grad[o] + g : g;
+  const int x = blockIdx.x * kT2 + tx;
+  if (x >= W) return;
+#pragma unroll
+  for (int j = 0; j < kG; ++j) {
+    const int y = blockIdx.y * kT2 + ty0 + j;
+    if (y >= H) continue;
+    const size_t o = base + (size_t)y * W + x;
+    const float g = f[0][j] + 2.f * X[o] * f[1][j] + Y[o] * f[2][j];
+    grad[o] = accumulate ? grad[o] + g : g;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -537,7 +609,7 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
-  dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, n_img), block(kTile, kTile);
+  dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img), block(kSsimThreads);
   float* maps = (float*)d_ws;
   GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
                 d_loss, maps, plane));
@@ -601,7 +673,7 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
-  dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, n_img), block(kTile, kTile);
+  dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img), block(kSsimThreads);
   // kernel 1 writes every map entry kernel 2 reads, so the array needs no clearing between calls
   GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
                 d_loss, maps, plane));
