@@ -305,8 +305,12 @@ int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* s
 int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,
                  float* d_grad, int accumulate, void* stream);
 
-/* Scratch bytes of the SSIM losses for n_elems image pixels or volume voxels. */
+/* Scratch bytes of gs_ssim2d_loss for n_elems image pixels (3 maps). */
 size_t gs_ssim_workspace_size(int64_t n_elems);
+
+/* Scratch bytes of gs_ssim3d_loss for n_voxels voxels: 3 maps plus 5 volumes of xy-filtered
+ * planes (the 3D filter runs as an xy pass per plane and a streaming z pass). */
+size_t gs_ssim3d_workspace_size(int64_t n_voxels);
 
 /* D-SSIM term of Eq. 5: weight * (1 - mean SSIM(x, y)) over n_img images of H x W, SSIM of
  * Wang et al. 2004 with an 11 x 11 Gaussian window (sigma 1.5), zero-padded 'same'
@@ -337,8 +341,10 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
                            float data_range, float weight, float* d_loss, float* d_grad,
                            int accumulate, void* stream);
 
-/* 3D SSIM term of Eq. 6 over a volume [z][y][x] with an 11 x 11 x 11 window; each thread
- * walks one z-row with a ring buffer of filtered planes (Sec. 3.5). */
+/* 3D SSIM term of Eq. 6: weight * (1 - mean SSIM) over a volume [z][y][x] with the separable
+ * 11 x 11 x 11 Gaussian window (sigma 1.5), zero-padded, constants as in 2D; gradient w.r.t.
+ * x written (accumulate = 0) or added.  d_ws: gs_ssim3d_workspace_size(nx ny nz) bytes, else
+ * GS_ERR_CAPACITY; nz <= 65535. */
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);

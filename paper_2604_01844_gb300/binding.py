@@ -122,6 +122,7 @@ SIGNATURES = {
     "gs_tv3d_loss": (_I, [_P, _I, _I, _I, ctypes.c_float, _P, _P, _I, _P]),
     "gs_sse": (_I, [_P, _P, _I64, _P, _P]),
     "gs_ssim_workspace_size": (_SZ, [_I64]),
+    "gs_ssim3d_workspace_size": (_SZ, [_I64]),
     "gs_ssim2d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
                             _SZ, _P]),
     "gs_ssim3d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,

@@ -71,7 +71,7 @@ FitLayout carve_fit(void* ws, int n, const gs_grid* g, int64_t max_pairs, size_t
   L.vmax = c.take<unsigned>(1);
   L.vol = c.take<float>(nvox);
   L.dvol = c.take<float>(nvox);
-  L.maps = c.take<float>(3 * nvox + 64);
+  L.maps = c.take<float>(8 * nvox + 64);
   L.init_bytes = grad_init_workspace(g, n);
   L.init_ws = c.take<char>(L.init_bytes);
   L.vox_bytes = vox_bytes;
@@ -153,7 +153,7 @@ int gs_fit_volume(const float* d_vol_gt, const gs_grid* grid, int n, int iters,
   ao.lr_quat = fo->lr_quat; ao.beta1 = fo->beta1; ao.beta2 = fo->beta2; ao.eps = fo->eps;
   ao.min_log_scale = fo->min_log_scale; ao.max_log_scale = fo->max_log_scale;
   ao.pad[0] = ao.pad[1] = ao.pad[2] = 0.f;
-  const size_t maps_bytes = 3 * (size_t)nvox * sizeof(float) + 256;
+  const size_t maps_bytes = 8 * (size_t)nvox * sizeof(float) + 256;
   for (int it = 0; it < iters; ++it) {
     GS_CUDA(cudaMemsetAsync(L.loss, 0, sizeof(float), s));
     GS_TRY(gs_voxelize(d_mean_rho, d_scale, d_quat, n, grid, lo, grid->dims, &o, L.vol, L.vox_ws,

@@ -132,6 +132,35 @@ constexpr int kG = 4;                // outputs per thread in each pass
 constexpr int kSsimThreads = 256;
 static_assert(kT2 * (kT2 / kG) == kSsimThreads, "vertical pass: one thread per 4-row group");
 
+// Stages the (kIn2 x kIn2) halo tile at (x0, y0) of NC channels (channel m at src[m] + m_off *
+// m, element (x, y) at + y * nx + x) into shared memory, zero outside [0, nx) x [0, ny).  All
+// of a thread's loads are issued before the first shared-memory store, so the tile costs one
+// memory round trip instead of one per row of threads.
+constexpr int kStageIters = (kIn2 * kIn2 + kSsimThreads - 1) / kSsimThreads;
+template <int NC>
+__device__ __forceinline__ void stage_halo(const float* const (&src)[NC], int x0, int y0,
+                                           int nx, int ny, float (*dst)[kIn2][kIn2 + 1]) {
+  float v[kStageIters][NC];
+#pragma unroll
+  for (int it = 0; it < kStageIters; ++it) {
+    const int p = threadIdx.x + it * kSsimThreads;
+    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
+    const bool ok = p < kIn2 * kIn2 && x >= 0 && x < nx && y >= 0 && y < ny;
+    const size_t o = (size_t)y * nx + x;
+#pragma unroll
+    for (int m = 0; m < NC; ++m) v[it][m] = ok ? src[m][o] : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < kStageIters; ++it) {
+    const int p = threadIdx.x + it * kSsimThreads;
+    if (p < kIn2 * kIn2) {
+      const int r = p / kIn2, c = p % kIn2;
+#pragma unroll
+      for (int m = 0; m < NC; ++m) dst[m][r][c] = v[it][m];
+    }
+  }
+}
+
 __device__ __forceinline__ void window_regs(const float* w, float wr[2 * kR + 1]) {
 #pragma unroll
   for (int k = 0; k <= 2 * kR; ++k) wr[k] = w[k];
@@ -144,19 +173,19 @@ __global__ void __launch_bounds__(kSsimThreads)
                  float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
                  int64_t plane) {
   __shared__ float w[2 * kR + 1];
-  __shared__ float sx[kIn2][kIn2 + 1], sy[kIn2][kIn2 + 1];
+  __shared__ float sxy_[2][kIn2][kIn2 + 1];
   __shared__ float hm[5][kIn2][kT2 + 1];
+  float (*sx)[kIn2 + 1] = sxy_[0];
+  float (*sy)[kIn2 + 1] = sxy_[1];
   window_weights(w);
   const int img = blockIdx.z;
   const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
   const float* Xi = X + (size_t)img * H * W;
   const float* Yi = Y + (size_t)img * H * W;
   const int tid = threadIdx.x;
-  for (int p = tid; p < kIn2 * kIn2; p += kSsimThreads) {
-    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
-    const bool in = x >= 0 && x < W && y >= 0 && y < H;
-    sx[r][c] = in ? Xi[(size_t)y * W + x] : 0.f;
-    sy[r][c] = in ? Yi[(size_t)y * W + x] : 0.f;
+  {
+    const float* const src[2] = {Xi, Yi};
+    stage_halo<2>(src, x0, y0, W, H, sxy_);
   }
   __syncthreads();
   float wr[2 * kR + 1];
@@ -247,13 +276,9 @@ __global__ void __launch_bounds__(kSsimThreads)
   const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
   const int tid = threadIdx.x;
   const size_t base = (size_t)img * H * W;
-  for (int p = tid; p < kIn2 * kIn2; p += kSsimThreads) {
-    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
-    const bool in = x >= 0 && x < W && y >= 0 && y < H;
-    const size_t o = base + (size_t)y * W + x;
-    sm[0][r][c] = in ? maps[o] : 0.f;
-    sm[1][r][c] = in ? maps[plane + o] : 0.f;
-    sm[2][r][c] = in ? maps[2 * plane + o] : 0.f;
+  {
+    const float* const src[3] = {maps + base, maps + plane + base, maps + 2 * plane + base};
+    stage_halo<3>(src, x0, y0, W, H, sm);
   }
   __syncthreads();
   float wr[2 * kR + 1];
@@ -316,157 +341,191 @@ __global__ void __launch_bounds__(kSsimThreads)
 }
 
 // ------------------------------------------------------------------------------------------
-// SSIM 3D: each thread owns one (x, y) column and walks z.  The xy-filtered moments of each
-// z-plane come from shared memory (tile 16x16 with a 5-voxel halo); the z filter uses an
-// 11-deep ring buffer of those filtered planes held in registers per thread.
+// SSIM 3D, separable in two passes over the volume:
+//   z pass   one thread per (x, y) column streams the inputs along z through an 11-plane
+//            register ring (each plane's ring slot is fixed by unrolling the walk 11 planes at
+//            a time, the next plane is prefetched) and writes the z-filtered channels: in the
+//            forward the five moments of X and Y (the ring holds only X and Y, products are
+//            formed per tap), in the backward the three maps;
+//   xy pass  every z-plane of those channels is filtered in x and y like the 2D kernels
+//            (32 x 32 tiles, 4-wide register blocking) and the voxel is finished: SSIM and the
+//            maps in the forward, the gradient in the backward.
+// Zero-padded 'same' filtering in all three directions, as in 2D.  The window weights travel
+// in the kernel parameters, so the FMAs read them from the constant bank.
 // ------------------------------------------------------------------------------------------
-constexpr int kT3 = 16;
-constexpr int kIn3 = kT3 + 2 * kR;
+struct Win {
+  float w[2 * kR + 1];
+};
 
-template <int NM>
-__device__ __forceinline__ void filter_plane_xy(float (*src)[kIn3][kIn3 + 1],
-                                                float (*tmp)[kIn3][kT3 + 1], const float* w,
-                                                int tid, float out[NM]) {
-  // horizontal pass over kIn3 rows x kT3 columns, then the vertical tap for this thread
-  for (int p = tid; p < kIn3 * kT3; p += kT3 * kT3) {
-    const int r = p / kT3, c = p % kT3;
-#pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      float a = 0.f;
-#pragma unroll
-      for (int k = 0; k <= 2 * kR; ++k) a = fmaf(w[k], src[m][r][c + k], a);
-      tmp[m][r][c] = a;
-    }
+Win host_window() {
+  // normalised 11-tap Gaussian, sigma 1.5 (evaluated in double, stored as float)
+  Win W;
+  double v[2 * kR + 1], s = 0.0;
+  for (int k = 0; k <= 2 * kR; ++k) {
+    const double d = (double)(k - kR);
+    v[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+    s += v[k];
   }
-  __syncthreads();
-  const int tx = tid % kT3, ty = tid / kT3;
-#pragma unroll
-  for (int m = 0; m < NM; ++m) {
-    float a = 0.f;
-#pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) a = fmaf(w[k], tmp[m][ty + k][tx], a);
-    out[m] = a;
-  }
+  for (int k = 0; k <= 2 * kR; ++k) W.w[k] = (float)(v[k] / s);
+  return W;
 }
 
-// Pass 1: moments -> SSIM -> maps (m1, m2, m3) like the 2D kernel.
-__global__ void __launch_bounds__(kT3 * kT3)
-    k_ssim3d_fwd(const float* __restrict__ X, const float* __restrict__ Y, int nx, int ny, int nz,
-                 float C1, float C2, float gscale, float* __restrict__ loss,
-                 float* __restrict__ maps, int64_t plane) {
-  __shared__ float w[2 * kR + 1];
-  __shared__ float src[5][kIn3][kIn3 + 1];
-  __shared__ float tmp[5][kIn3][kT3 + 1];
-  window_weights(w);
-  const int tid = threadIdx.y * kT3 + threadIdx.x;
-  const int x0 = blockIdx.x * kT3 - kR, y0 = blockIdx.y * kT3 - kR;
-  const int x = blockIdx.x * kT3 + threadIdx.x, y = blockIdx.y * kT3 + threadIdx.y;
-  const size_t sxy = (size_t)nx * ny;
-  float ring[2 * kR + 1][5];
+template <int NIN>  // 2: (X, Y) -> 5 moments; 3: maps -> 3 filtered maps
+__global__ void __launch_bounds__(kThreads)
+    k_ssim3d_z(const __grid_constant__ Win W, const float* __restrict__ A0,
+               const float* __restrict__ A1, const float* __restrict__ A2, int nx, int ny, int nz,
+               int64_t plane, float* __restrict__ out) {
+  constexpr int NOUT = NIN == 2 ? 5 : 3;
+  const int64_t sxy = (int64_t)nx * ny;
+  const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (col >= sxy) return;
+  const float* in[3] = {A0, A1, A2};
+  float ring[2 * kR + 1][NIN];
 #pragma unroll
   for (int k = 0; k <= 2 * kR; ++k)
 #pragma unroll
-    for (int m = 0; m < 5; ++m) ring[k][m] = 0.f;
-  float contrib = 0.f;
-  // plane zi enters the ring; output z = zi - kR is produced once its 11 planes are in
-  for (int zi = 0; zi < nz + kR; ++zi) {
-    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (zi < nz) {
-      __syncthreads();
-      for (int p = tid; p < kIn3 * kIn3; p += kT3 * kT3) {
-        const int r = p / kIn3, c = p % kIn3, yy = y0 + r, xx = x0 + c;
-        const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny;
-        const size_t o = (size_t)zi * sxy + (size_t)yy * nx + xx;
-        const float u = in ? X[o] : 0.f, v = in ? Y[o] : 0.f;
-        src[0][r][c] = u; src[1][r][c] = v; src[2][r][c] = u * u; src[3][r][c] = v * v;
-        src[4][r][c] = u * v;
+    for (int i = 0; i < NIN; ++i) ring[k][i] = 0.f;
+  float nxt[NIN];
+#pragma unroll
+  for (int i = 0; i < NIN; ++i) nxt[i] = in[i][col];
+  // plane zi enters ring slot zi % 11; output z = zi - kR is complete once plane zi is in
+  for (int zb = 0; zb < nz + kR; zb += 2 * kR + 1) {
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) {
+      const int zi = zb + k;
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) ring[k][i] = nxt[i];
+      const int zn = zi + 1;
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) nxt[i] = zn < nz ? in[i][(int64_t)zn * sxy + col] : 0.f;
+      const int z = zi - kR;
+      if (z < 0 || z >= nz) continue;
+      float acc[NOUT];
+#pragma unroll
+      for (int m = 0; m < NOUT; ++m) acc[m] = 0.f;
+#pragma unroll
+      for (int t = 0; t <= 2 * kR; ++t) {
+        const int slot = (k + 1 + t) % (2 * kR + 1);  // holds plane z - kR + t
+        const float wt = W.w[t];
+        if (NIN == 2) {
+          const float u = ring[slot][0], v = ring[slot][1];
+          acc[0] = fmaf(wt, u, acc[0]);
+          acc[1] = fmaf(wt, v, acc[1]);
+          acc[2] = fmaf(wt, u * u, acc[2]);
+          acc[3] = fmaf(wt, v * v, acc[3]);
+          acc[4] = fmaf(wt, u * v, acc[4]);
+        } else {
+#pragma unroll
+          for (int m = 0; m < NOUT; ++m) acc[m] = fmaf(wt, ring[slot][m], acc[m]);
+        }
       }
-      __syncthreads();
-      filter_plane_xy<5>(src, tmp, w, tid, f);
+      const int64_t o = (int64_t)z * sxy + col;
+#pragma unroll
+      for (int m = 0; m < NOUT; ++m) out[m * plane + o] = acc[m];
     }
-    // shift the ring (static indices keep it in registers)
+  }
+}
+
+// xy pass and completion.  MODE 0: five z-filtered moments -> SSIM -> maps and loss;
+// MODE 1: three z-filtered maps -> dL/dx = f1 + 2 x f2 + y f3.
+template <int MODE>
+__global__ void __launch_bounds__(kSsimThreads)
+    k_ssim3d_xy(const __grid_constant__ Win W, const float* __restrict__ in, int nx, int ny,
+                int64_t plane, float C1, float C2, float gscale, float* __restrict__ loss,
+                float* __restrict__ maps, const float* __restrict__ X,
+                const float* __restrict__ Y, float* __restrict__ grad, int accumulate) {
+  constexpr int NM = MODE == 0 ? 5 : 3;
+  extern __shared__ float dyn[];
+  float (*sin_)[kIn2][kIn2 + 1] = reinterpret_cast<float (*)[kIn2][kIn2 + 1]>(dyn);
+  float (*hm)[kIn2][kT2 + 1] =
+      reinterpret_cast<float (*)[kIn2][kT2 + 1]>(dyn + NM * kIn2 * (kIn2 + 1));
+  const int z = blockIdx.z;
+  const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
+  const size_t sxy = (size_t)nx * ny, zo = (size_t)z * sxy;
+  const int tid = threadIdx.x;
+  {
+    const float* src[NM];
 #pragma unroll
-    for (int k = 0; k < 2 * kR; ++k)
+    for (int m = 0; m < NM; ++m) src[m] = in + m * plane + zo;
+    stage_halo<NM>(src, x0, y0, nx, ny, sin_);
+  }
+  __syncthreads();
+  for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
+    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
+    float acc[NM][kG];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) ring[k][m] = ring[k + 1][m];
+    for (int m = 0; m < NM; ++m)
 #pragma unroll
-    for (int m = 0; m < 5; ++m) ring[2 * kR][m] = f[m];
-    const int z = zi - kR;
-    if (z < 0) continue;
-    float mo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k)
+    for (int i = 0; i < kG + 2 * kR; ++i) {
+      float u[NM];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) mo[m] = fmaf(w[k], ring[k][m], mo[m]);
-    const float mx = mo[0], my = mo[1];
-    const float sxx = mo[2] - mx * mx, syy = mo[3] - my * my, sxy2 = mo[4] - mx * my;
-    const float A = 2.f * mx * my + C1, Bn = 2.f * sxy2 + C2;
-    const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
-    const float S = (A * Bn) / (C * D);
-    if (x < nx && y < ny) {
+      for (int m = 0; m < NM; ++m) u[m] = sin_[m][r][c0 + i];
+#pragma unroll
+      for (int j = 0; j < kG; ++j) {
+        const int k = i - j;
+        if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m][j] = fmaf(W.w[k], u[m], acc[m][j]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+#pragma unroll
+      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
+  }
+  __syncthreads();
+  const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
+  float f[NM][kG];
+#pragma unroll
+  for (int m = 0; m < NM; ++m)
+#pragma unroll
+    for (int j = 0; j < kG; ++j) f[m][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kG + 2 * kR; ++i) {
+    float h[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) h[m] = hm[m][ty0 + i][tx];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int k = i - j;
+      if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) f[m][j] = fmaf(W.w[k], h[m], f[m][j]);
+    }
+  }
+  const int x = blockIdx.x * kT2 + tx;
+  float contrib = 0.f;
+#pragma unroll
+  for (int j = 0; j < kG; ++j) {
+    const int y = blockIdx.y * kT2 + ty0 + j;
+    if (x >= nx || y >= ny) continue;
+    const size_t o = zo + (size_t)y * nx + x;
+    if (MODE == 0) {
+      const float mx = f[0][j], my = f[1][j];
+      const float sxx = f[2][j] - mx * mx, syy = f[3][j] - my * my, sxy2 = f[4][j] - mx * my;
+      const float A = 2.f * mx * my + C1, Bn = 2.f * sxy2 + C2;
+      const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
+      const float S = (A * Bn) / (C * D);
       const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
       const float dsxx = -S / D;
       const float dsxy = 2.f * A / (C * D);
-      const size_t o = (size_t)z * sxy + (size_t)y * nx + x;
       maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
       maps[plane + o] = gscale * dsxx;
       maps[2 * plane + o] = gscale * dsxy;
       contrib += 1.f - S;
+    } else {
+      const float g = f[0][j] + 2.f * X[o] * f[1][j] + Y[o] * f[2][j];
+      grad[o] = accumulate ? grad[o] + g : g;
     }
   }
-  if (loss) block_add(contrib * (-gscale), loss);
+  if (MODE == 0 && loss) block_add(contrib * (-gscale), loss);
 }
 
-// Pass 2: filter the three maps with the 11^3 window; dL/dx = f1 + 2 x f2 + y f3.
-__global__ void __launch_bounds__(kT3 * kT3)
-    k_ssim3d_bwd(const float* __restrict__ X, const float* __restrict__ Y, int nx, int ny, int nz,
-                 const float* __restrict__ maps, int64_t plane, float* __restrict__ grad,
-                 int accumulate) {
-  __shared__ float w[2 * kR + 1];
-  __shared__ float src[3][kIn3][kIn3 + 1];
-  __shared__ float tmp[3][kIn3][kT3 + 1];
-  window_weights(w);
-  const int tid = threadIdx.y * kT3 + threadIdx.x;
-  const int x0 = blockIdx.x * kT3 - kR, y0 = blockIdx.y * kT3 - kR;
-  const int x = blockIdx.x * kT3 + threadIdx.x, y = blockIdx.y * kT3 + threadIdx.y;
-  const size_t sxy = (size_t)nx * ny;
-  float ring[2 * kR + 1][3];
-#pragma unroll
-  for (int k = 0; k <= 2 * kR; ++k)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) ring[k][m] = 0.f;
-  for (int zi = 0; zi < nz + kR; ++zi) {
-    float f[3] = {0.f, 0.f, 0.f};
-    if (zi < nz) {
-      __syncthreads();
-      for (int p = tid; p < kIn3 * kIn3; p += kT3 * kT3) {
-        const int r = p / kIn3, c = p % kIn3, yy = y0 + r, xx = x0 + c;
-        const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny;
-        const size_t o = (size_t)zi * sxy + (size_t)yy * nx + xx;
-        src[0][r][c] = in ? maps[o] : 0.f;
-        src[1][r][c] = in ? maps[plane + o] : 0.f;
-        src[2][r][c] = in ? maps[2 * plane + o] : 0.f;
-      }
-      __syncthreads();
-      filter_plane_xy<3>(src, tmp, w, tid, f);
-    }
-#pragma unroll
-    for (int k = 0; k < 2 * kR; ++k)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) ring[k][m] = ring[k + 1][m];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) ring[2 * kR][m] = f[m];
-    const int z = zi - kR;
-    if (z < 0 || x >= nx || y >= ny) continue;
-    float g3[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) g3[m] = fmaf(w[k], ring[k][m], g3[m]);
-    const size_t o = (size_t)z * sxy + (size_t)y * nx + x;
-    const float g = g3[0] + 2.f * X[o] * g3[1] + Y[o] * g3[2];
-    grad[o] = accumulate ? grad[o] + g : g;
-  }
+template <int MODE>
+constexpr size_t ssim3d_xy_smem() {
+  return sizeof(float) * (size_t)(MODE == 0 ? 5 : 3) * kIn2 * ((kIn2 + 1) + (kT2 + 1));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -681,23 +740,51 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
                 (const float*)maps, plane, d_grad, accumulate);
 }
 
+size_t gs_ssim3d_workspace_size(int64_t n_voxels) {
+  return (size_t)(8 * n_voxels) * sizeof(float) + 256;
+}
+
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream) {
   if (!d_x || !d_y || !d_grad || !d_ws || nx < 1 || ny < 1 || nz < 1 || !(data_range > 0.f))
     return GS_ERR_ARG;
+  if (nz > 65535) return GS_ERR_ARG;
   const int64_t plane = (int64_t)nx * ny * nz;
-  if (ws_bytes < gs_ssim_workspace_size(plane)) return GS_ERR_CAPACITY;
+  if (ws_bytes < gs_ssim3d_workspace_size(plane)) return GS_ERR_CAPACITY;
+  // the forward's xy kernel needs more than the default 48 KB of dynamic shared memory; the
+  // attribute is host-side state of the current device, set on every call
+  cudaError_t attr_err = cudaFuncSetAttribute(
+      k_ssim3d_xy<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssim3d_xy_smem<0>());
+  if (attr_err == cudaSuccess)
+    attr_err = cudaFuncSetAttribute(k_ssim3d_xy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ssim3d_xy_smem<1>());
+  if (attr_err != cudaSuccess) {
+    set_last_error("ssim3d_xy attributes", attr_err);
+    return GS_ERR_CUDA;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
-  dim3 grid((nx + kT3 - 1) / kT3, (ny + kT3 - 1) / kT3), block(kT3, kT3);
-  float* maps = (float*)d_ws;
-  GS_TRY(launch("ssim3d_fwd", k_ssim3d_fwd, grid, block, 0, s, d_x, d_y, nx, ny, nz, C1, C2,
-                gscale, d_loss, maps, plane));
-  return launch("ssim3d_bwd", k_ssim3d_bwd, grid, block, 0, s, d_x, d_y, nx, ny, nz,
-                (const float*)maps, plane, d_grad, accumulate);
+  const Win W = host_window();
+  float* maps = (float*)d_ws;         // 3 volumes, kept from the forward for the backward
+  float* tmp = maps + 3 * plane;      // 5 volumes of z-filtered channels
+  const dim3 gxy((nx + kT2 - 1) / kT2, (ny + kT2 - 1) / kT2, nz), bxy(kSsimThreads);
+  const int64_t cols = (int64_t)nx * ny;
+  const dim3 gz((unsigned)((cols + kThreads - 1) / kThreads)), bz(kThreads);
+  const float* nul = nullptr;
+  GS_TRY(launch("ssim3d_z_fwd", k_ssim3d_z<2>, gz, bz, 0, s, W, d_x, d_y, nul, nx, ny, nz, plane,
+                tmp));
+  GS_TRY(launch("ssim3d_xy_fwd", k_ssim3d_xy<0>, gxy, bxy, ssim3d_xy_smem<0>(), s, W,
+                (const float*)tmp, nx, ny, plane, C1, C2, gscale, d_loss, maps, nul, nul,
+                (float*)nullptr, 0));
+  GS_TRY(launch("ssim3d_z_bwd", k_ssim3d_z<3>, gz, bz, 0, s, W, (const float*)maps,
+                (const float*)(maps + plane), (const float*)(maps + 2 * plane), nx, ny, nz,
+                plane, tmp));
+  return launch("ssim3d_xy_bwd", k_ssim3d_xy<1>, gxy, bxy, ssim3d_xy_smem<1>(), s, W,
+                (const float*)tmp, nx, ny, plane, C1, C2, gscale, (float*)nullptr,
+                (float*)nullptr, d_x, d_y, d_grad, accumulate);
 }
 
 int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, float* d_m,

@@ -11,8 +11,9 @@
 //               whose box misses its 8x4 column patch; along a column the exponent is a
 //               quadratic in z evaluated with two FMAs per voxel
 //   vox_bwd     one CTA per brick with dL/dV of the brick in shared memory; one warp per
-//               (Gaussian, brick) pair accumulates the ten moment sums of g exp(-q/2),
-//               warp-shuffle reduced, then three float4 atomics per pair
+//               (Gaussian, brick) pair, lanes over the (x, y) columns of its box, each lane
+//               walking the exact z chord of its column; the ten moment sums of g exp(-q/2)
+//               are warp-shuffle reduced, then three float4 atomics per pair
 //   vox_chain   one thread per Gaussian: moments -> d(mean, rho, scale, quaternion)
 #include <algorithm>
 #include <cmath>
@@ -411,7 +412,6 @@ __global__ void __launch_bounds__(kThreads)
                 : 0.f;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int lx = lane & 7, ly = lane >> 3;
   for (uint32_t base = r.x; base < r.y; base += kThreads) {
     const int m = (int)min((uint32_t)kThreads, r.y - base);
     __syncthreads();
@@ -432,30 +432,51 @@ __global__ void __launch_bounds__(kThreads)
       const int za = max((int)a.z, z0b), zb = min((int)b.z, z0b + kB - 1);
       if (xa > xb || ya > yb || za > zb) continue;
       const float4 G = s_geo[j], c0 = s_c0[j], c1 = s_c1[j];
+      // lanes take the (x, y) columns of the box inside the brick; each walks the exact z
+      // chord of its column (closed-form roots of the exponent, widened by 1/100 voxel) and
+      // re-tests every voxel with the forward's expression and offsets
+      const int ncx = xb - xa + 1, ncols = ncx * (yb - ya + 1);
+      const float inv_ncx = 1.f / (float)ncx;
+      const float hz = g.h[2];
+      const float dz0 = (g.o[2] + ((float)z0b + 0.5f) * hz) - G.z;  // the forward's dz at z0b
+      const float inv2a = 0.5f / c1.y, inv_hz = 1.f / hz;
       float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
       float mxx = 0.f, mxy = 0.f, mxz = 0.f, myy = 0.f, myz = 0.f, mzz = 0.f;
-      for (int z = za; z <= zb; ++z) {
-        const float dz = g.o[2] + ((float)z + 0.5f) * g.h[2] - G.z;
-        for (int ys = ya; ys <= yb; ys += 4) {
-          const int y = ys + ly;
-          const float dy = g.o[1] + ((float)y + 0.5f) * g.h[1] - G.y;
-          for (int xs = xa; xs <= xb; xs += 8) {
-            const int x = xs + lx;
-            if (x <= xb && y <= yb) {
-              const float dx = g.o[0] + ((float)x + 0.5f) * g.h[0] - G.x;
-              const float qxy = fmaf(fmaf(c0.y, dy, c0.x * dx), dx, c0.w * dy * dy);
-              const float lin = fmaf(c0.z, dx, c1.x * dy);
-              const float e = fmaf(fmaf(c1.y, dz, lin), dz, qxy);
-              if (e > c1.z) {
-                const float q = s_g[((z - z0b) * kB + (y - y0b)) * kB + (x - x0b)] * ex2(e);
-                const float qx = q * dx, qy = q * dy, qz = q * dz;
-                m0 += q; mx += qx; my += qy; mz += qz;
-                mxx = fmaf(qx, dx, mxx); mxy = fmaf(qx, dy, mxy); mxz = fmaf(qx, dz, mxz);
-                myy = fmaf(qy, dy, myy); myz = fmaf(qy, dz, myz); mzz = fmaf(qz, dz, mzz);
-              }
-            }
+      for (int ci = lane; ci < ncols; ci += 32) {
+        const int yo = (int)(((float)ci + 0.5f) * inv_ncx);
+        const int x = xa + (ci - yo * ncx), y = ya + yo;
+        const float dx = g.o[0] + ((float)x + 0.5f) * g.h[0] - G.x;
+        const float dy = g.o[1] + ((float)y + 0.5f) * g.h[1] - G.y;
+        const float qxy = fmaf(fmaf(c0.y, dy, c0.x * dx), dx, c0.w * dy * dy);
+        const float lin = fmaf(c0.z, dx, c1.x * dy);
+        const float disc = lin * lin - 4.f * c1.y * (qxy - c1.z);
+        if (!(disc > 0.f)) continue;
+        const float ctr = -lin * inv2a, half = -sqrtf(disc) * inv2a;
+        const int k0 = max(za - z0b, (int)ceilf((ctr - half - dz0) * inv_hz - 0.01f));
+        const int k1 = min(zb - z0b, (int)floorf((ctr + half - dz0) * inv_hz + 0.01f));
+        const float* gcol = s_g + (y - y0b) * kB + (x - x0b);
+        float q0 = 0.f, qz = 0.f, qzz = 0.f;
+        for (int k = k0; k <= k1; ++k) {
+          const float dz = fmaf((float)k, hz, dz0);
+          const float e = fmaf(fmaf(c1.y, dz, lin), dz, qxy);
+          if (e > c1.z) {
+            const float q = gcol[k * kB * kB] * ex2(e);
+            const float qd = q * dz;
+            q0 += q;
+            qz += qd;
+            qzz = fmaf(qd, dz, qzz);
           }
         }
+        m0 += q0;
+        mx = fmaf(dx, q0, mx);
+        my = fmaf(dy, q0, my);
+        mz += qz;
+        mxx = fmaf(dx * dx, q0, mxx);
+        mxy = fmaf(dx * dy, q0, mxy);
+        mxz = fmaf(dx, qz, mxz);
+        myy = fmaf(dy * dy, q0, myy);
+        myz = fmaf(dy, qz, myz);
+        mzz += qzz;
       }
       m0 = gsd::warp_sum(m0); mx = gsd::warp_sum(mx); my = gsd::warp_sum(my);
       mz = gsd::warp_sum(mz); mxx = gsd::warp_sum(mxx); mxy = gsd::warp_sum(mxy);

@@ -84,7 +84,7 @@ def test_fit_first_iteration_is_the_composition(orc, gsct):
     dvol = torch.empty_like(vol)
     B.check(B.lib().gs_l1_loss(B.ptr(vol), B.ptr(dV), vol.numel(), 1.0, B.ptr(loss), B.ptr(dvol),
                                0, torch.cuda.current_stream().cuda_stream), "l1")
-    ws = torch.empty(B.lib().gs_ssim_workspace_size(vol.numel()), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(B.lib().gs_ssim3d_workspace_size(vol.numel()), dtype=torch.uint8, device="cuda")
     B.check(B.lib().gs_ssim3d_loss(B.ptr(vol), B.ptr(dV), 32, 32, 32, float(V.max()), o.alpha_ssim,
                                    B.ptr(loss), B.ptr(dvol), 1, B.ptr(ws), ws.numel(),
                                    torch.cuda.current_stream().cuda_stream), "ssim3d")

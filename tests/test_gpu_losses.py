@@ -44,7 +44,7 @@ def _run_loss(B, name, x, y, *extra, ws=None, weight=1.0, accumulate_into=None):
         rc = L.gs_ssim2d_loss(B.ptr(xd), B.ptr(yd), n, H, W, extra[0], weight, B.ptr(loss),
                               B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
     else:
-        wsb = torch.empty(L.gs_ssim_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
+        wsb = torch.empty(L.gs_ssim3d_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
         dz, dy, dx = x.shape
         rc = L.gs_ssim3d_loss(B.ptr(xd), B.ptr(yd), dx, dy, dz, extra[0], weight, B.ptr(loss),
                               B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
@@ -90,7 +90,7 @@ def test_ssim2d(B, shape):
     assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
 
 
-@pytest.mark.parametrize("shape", [(21, 19, 35), (12, 16, 16)])
+@pytest.mark.parametrize("shape", [(21, 19, 35), (12, 16, 16), (4, 40, 33), (1, 9, 70)])
 def test_ssim3d(B, shape):
     rng = np.random.default_rng(3)
     y = _x32(rng.random(shape))
