@@ -342,6 +342,11 @@ def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
             "note": "plain single-instance form; PSNR = 10 log10(max(V_gt)^2 / MSE) on 256^3"}
 
 
+# learned start: half of the Gaussian budget from the MLP (its outputs under 5 % of the peak
+# density dropped), the rest from gradient sampling
+LEARNED_INIT = dict(mlp_share=0.5, min_rho_frac=0.05)
+
+
 def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_steps=3000):
     """Per-brick MLP initializer (trained here on n_train phantoms with other seeds) against
     the FDK-gradient initialisation on the 40-ellipsoid phantom: PSNR after 10 iterations and
@@ -372,10 +377,11 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
     u = np.random.default_rng(7).random((50000, 4)).astype(np.float32)
     sse = torch.zeros(1, dtype=torch.float64, device=device)
     # warm the inference path once (module load, tensor-map set-up) outside the timing
-    I.learned_init(mlp, fdk_volume(prob, grid), grid, 50000, u)
+    I.learned_init(mlp, fdk_volume(prob, grid), grid, 50000, u, **LEARNED_INIT)
     out = {"train_ms": round(train_ms, 1),
            "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)],
-           "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3"}
+           "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3",
+           "learned_init": LEARNED_INIT}
     lr_sets = {"plain": [dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)],
                "learned": [dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3),
                            dict(lr_mean=1e-4, lr_rho=2e-2, lr_scale=2.5e-3, lr_quat=1e-3)]}
@@ -388,7 +394,7 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
             mr, sc, q = gradient_init(fdk, grid, 50000, u)
             n_mlp = 0
         else:
-            mr, sc, q, n_mlp = I.learned_init(mlp, fdk, grid, 50000, u)
+            mr, sc, q, n_mlp = I.learned_init(mlp, fdk, grid, 50000, u, **LEARNED_INIT)
         b.record()
         torch.cuda.synchronize()
         init_ms = a.elapsed_time(b)
@@ -480,7 +486,7 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
             if kind == "plain":
                 mr, sc, q = gradient_init(fdk, g, sp["n"], u)
             else:
-                mr, sc, q, nm = I.learned_init(mlp, fdk, g, sp["n"], u)
+                mr, sc, q, nm = I.learned_init(mlp, fdk, g, sp["n"], u, **LEARNED_INIT)
                 n_mlp += nm
             inst.append(dict(views=v, W=sp["det"], H=sp["det"], target=prob.proj, grid=g,
                              mean_rho=mr, scale=sc, quat=q))

@@ -105,7 +105,12 @@ __global__ void k_radix_digit_scan(uint32_t* __restrict__ hist, uint32_t* __rest
 
 // Stable scatter of one pass.  Items of a block's chunk are processed in tiles of 2048: warp w
 // owns items [w*256, w*256+256) of the tile in 8 rounds of 32 consecutive items, so item order
-// equals (tile, warp, round, lane) order and every rank below preserves it.
+// equals (tile, warp, round, lane) order and every rank below preserves it.  Each tile is first
+// reordered by digit in shared memory (stable), then written out in that order, so that the
+// lanes of a warp store consecutive addresses of one digit's run instead of 32 scattered ones.
+// Shared memory: run[D] (block's next global position per digit), wcnt[NW][D] (per-warp digit
+// counts, then their within-digit prefix), lstart[D] (tile-local start of each digit), and the
+// reordered tile (2048 keys, 2048 values).
 __global__ void __launch_bounds__(kSortThreads)
     k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const gs_status* st,
@@ -116,16 +121,20 @@ __global__ void __launch_bounds__(kSortThreads)
   const int D = 1 << dbits;
   const uint32_t mask = (uint32_t)D - 1u;
   constexpr int NW = kSortThreads / 32;
-  uint32_t* run = sh;           // [D] running global position of each digit for this block
-  uint32_t* wcnt = sh + D;      // [NW][D] per-warp digit counters of the current tile
+  uint32_t* run = sh;                    // [D]
+  uint32_t* wcnt = run + D;              // [NW][D]
+  uint32_t* lstart = wcnt + NW * D;      // [D]
+  uint32_t* tk = lstart + D;             // [kSortTile]
+  uint32_t* tv = tk + kSortTile;         // [kSortTile]
   __shared__ uint32_t part[kSortThreads];
+  __shared__ uint32_t wtot[NW];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 
   // digit bases: exclusive scan of totals, each thread owning a contiguous run of digits
   const int per = (D + kSortThreads - 1) / kSortThreads;
-  uint32_t s = 0;
-  for (int d = t * per; d < min(D, t * per + per); ++d) s += totals[d];
-  part[t] = s;
+  uint32_t s0 = 0;
+  for (int d = t * per; d < min(D, t * per + per); ++d) s0 += totals[d];
+  part[t] = s0;
   __syncthreads();
   if (t == 0) {
     uint32_t acc = 0;
@@ -136,10 +145,12 @@ __global__ void __launch_bounds__(kSortThreads)
     }
   }
   __syncthreads();
-  uint32_t acc = part[t];
-  for (int d = t * per; d < min(D, t * per + per); ++d) {
-    run[d] = acc + hist[(size_t)d * G + blockIdx.x];
-    acc += totals[d];
+  {
+    uint32_t acc = part[t];
+    for (int d = t * per; d < min(D, t * per + per); ++d) {
+      run[d] = acc + hist[(size_t)d * G + blockIdx.x];
+      acc += totals[d];
+    }
   }
   for (int i = t; i < NW * D; i += kSortThreads) wcnt[i] = 0;
   __syncthreads();
@@ -148,6 +159,7 @@ __global__ void __launch_bounds__(kSortThreads)
   chunk_of(st, G, lo, hi);
   const unsigned lt = gsd::lanemask_lt();
   for (int64_t tile = lo; tile < hi; tile += kSortTile) {
+    const int nvalid = (int)min((int64_t)kSortTile, hi - tile);
     uint32_t kk[kSortItemsPerThread], vv[kSortItemsPerThread], rk[kSortItemsPerThread];
 #pragma unroll
     for (int r = 0; r < kSortItemsPerThread; ++r) {
@@ -165,28 +177,61 @@ __global__ void __launch_bounds__(kSortThreads)
       rk[r] = base + __popc(peers & lt);
     }
     __syncthreads();
-    for (int d = t; d < D; d += kSortThreads) {
-      uint32_t a = run[d];
+    // within-digit warp prefix (in place) and the tile's count of each digit
+    uint32_t cnt_own = 0;  // sum of this thread's digits' counts
+    for (int d = t * per; d < min(D, t * per + per); ++d) {
+      uint32_t a = 0;
 #pragma unroll
       for (int ww = 0; ww < NW; ++ww) {
-        uint32_t c = wcnt[ww * D + d];
+        const uint32_t c = wcnt[ww * D + d];
         wcnt[ww * D + d] = a;
         a += c;
       }
-      run[d] = a;
+      lstart[d] = a;  // count for now, start after the scan below
+      cnt_own += a;
     }
+    // block-wide exclusive scan of the per-thread digit-run counts -> tile-local digit starts
+    const uint32_t incl = gsd::warp_inclusive_scan(cnt_own);
+    if (lane == 31) wtot[w] = incl;
     __syncthreads();
+    uint32_t wbase = 0;
 #pragma unroll
-    for (int r = 0; r < kSortItemsPerThread; ++r) {
-      const int64_t idx = tile + w * (32 * kSortItemsPerThread) + r * 32 + lane;
-      if (idx < hi) {
-        const uint32_t d = (kk[r] >> shift) & mask;
-        const uint32_t pos = wcnt[w * D + d] + rk[r];
-        kout[pos] = kk[r];
-        vout[pos] = vv[r];
+    for (int ww = 0; ww < NW; ++ww) wbase += ww < w ? wtot[ww] : 0u;
+    {
+      uint32_t acc = wbase + incl - cnt_own;
+      for (int d = t * per; d < min(D, t * per + per); ++d) {
+        const uint32_t c = lstart[d];
+        lstart[d] = acc;
+        acc += c;
       }
     }
     __syncthreads();
+    // reorder the tile by digit in shared memory
+#pragma unroll
+    for (int r = 0; r < kSortItemsPerThread; ++r) {
+      const int i = w * (32 * kSortItemsPerThread) + r * 32 + lane;
+      if (i < nvalid) {
+        const uint32_t d = (kk[r] >> shift) & mask;
+        const uint32_t lp = lstart[d] + wcnt[w * D + d] + rk[r];
+        tk[lp] = kk[r];
+        tv[lp] = vv[r];
+      }
+    }
+    __syncthreads();
+    // write out in digit order: item i of digit d goes to run[d] + (i - lstart[d])
+    for (int i = t; i < nvalid; i += kSortThreads) {
+      const uint32_t k = tk[i];
+      const uint32_t d = (k >> shift) & mask;
+      const uint32_t pos = run[d] + ((uint32_t)i - lstart[d]);
+      kout[pos] = k;
+      vout[pos] = tv[i];
+    }
+    __syncthreads();
+    // advance the block's digit positions by the tile's counts and clear the warp counters
+    for (int d = t * per; d < min(D, t * per + per); ++d) {
+      const uint32_t next = d + 1 < D ? lstart[d + 1] : (uint32_t)nvalid;
+      run[d] += next - lstart[d];
+    }
     for (int i = t; i < NW * D; i += kSortThreads) wcnt[i] = 0;
     __syncthreads();
   }
@@ -244,9 +289,18 @@ int scan_block_sums(const uint32_t* block_sums, uint32_t* block_offsets, int nbl
                 block_offsets, nblocks, st, cap);
 }
 
+size_t scatter_smem_bytes(int dbits) {
+  const size_t D = (size_t)1 << dbits;
+  return sizeof(uint32_t) * (D * (2 + kSortThreads / 32) + 2 * (size_t)kSortTile);
+}
+
 int radix_sort(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt, uint32_t* vals_alt,
                uint32_t* hist, const SortPlan& plan, gs_status* st, int64_t cap, cudaStream_t s) {
   (void)cap;
+  // the scatter of the widest digit needs more than the default 48 KB of dynamic shared memory
+  // (host-side state of the current device, set on every call)
+  GS_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)scatter_smem_bytes(kMaxDigitBits)));
   const int G = plan.grid;
   for (int pass = 0; pass < plan.passes; ++pass) {
     const int db = plan.dbits[pass], sh = plan.shift[pass];
@@ -257,7 +311,7 @@ int radix_sort(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt, uint32_t* v
     const int scan_threads = (G + 31) / 32 * 32;
     GS_TRY(launch("radix_digit_scan", k_radix_digit_scan, dim3(D), dim3(scan_threads), 0, s,
                   hist, totals, (const gs_status*)st, G));
-    const size_t smem = (size_t)D * sizeof(uint32_t) * (1 + kSortThreads / 32);
+    const size_t smem = scatter_smem_bytes(db);
     GS_TRY(launch("radix_scatter", k_radix_scatter, dim3(G), dim3(kSortThreads), smem, s,
                   (const uint32_t*)*keys, (const uint32_t*)*vals, keys_alt, vals_alt,
                   (const gs_status*)st, sh, db, (const uint32_t*)hist, (const uint32_t*)totals,

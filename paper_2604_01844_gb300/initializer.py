@@ -56,16 +56,17 @@ def train(mlp: BrickMLP, x16, target, steps=1500, batch=1024, lr=1e-3, seed=0):
 
 
 def learned_init(mlp: BrickMLP, fdk: torch.Tensor, grid, budget: int, uniforms: np.ndarray,
-                 frac=0.05):
+                 frac=0.05, mlp_share: float = 1.0, min_rho_frac: float = 0.0):
     """Gaussians for a new scan: MLP on the non-empty bricks of its FDK volume (the
-    `budget / 32` brightest bricks if there are more), topped up by gradient sampling."""
+    `mlp_share * budget / 32` brightest bricks if there are more), dropping MLP Gaussians whose
+    density is below `min_rho_frac` of the largest, topped up by gradient sampling."""
     dev = fdk.device
     nz, ny, nx = fdk.shape
     fmax = max(float(fdk.max()), 1e-6)
     nb = (nx // 16, ny // 16, nz // 16)
     vmax = fdk.reshape(nz // 16, 16, ny // 16, 16, nx // 16, 16).amax(dim=(1, 3, 5)).reshape(-1)
     order = torch.argsort(vmax, descending=True).cpu().numpy()
-    keep_n = int(min((vmax > frac * fmax).sum().item(), budget // 32))
+    keep_n = int(min((vmax > frac * fmax).sum().item(), int(budget * mlp_share) // 32))
     keep_n -= keep_n % 128  # the GEMM tiles 128 rows
     keep_n = max(keep_n, 128)
     sel = np.zeros(vmax.numel(), dtype=bool)
@@ -78,6 +79,9 @@ def learned_init(mlp: BrickMLP, fdk: torch.Tensor, grid, budget: int, uniforms: 
     geo = np.stack([o[0] + ids_np[:, 0] * 16 * h, o[1] + ids_np[:, 1] * 16 * h,
                     o[2] + ids_np[:, 2] * 16 * h, np.full(len(ids_np), h)], 1).astype(np.float32)
     mr, sc, q = mlp.infer_gaussians(x16, torch.from_numpy(geo).to(dev), amp=fmax)
+    if min_rho_frac > 0.0:
+        keep = mr[:, 3] > min_rho_frac * mr[:, 3].max()
+        mr, sc, q = mr[keep], sc[keep], q[keep]
     n_mlp = mr.shape[0]
     if n_mlp < budget:
         extra = gradient_init(fdk, grid, budget - n_mlp, uniforms[: budget - n_mlp])
