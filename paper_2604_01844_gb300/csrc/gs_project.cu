@@ -474,79 +474,33 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
 }
 
 // ------------------------------------------------------------------------------------------
-// raster backward, per Gaussian (Sec. 3.5): one thread per (Gaussian, tile) pair, in three
-// phases per batch of up to 2 x kThreads pairs of a tile:
-//   1. staging: the pair's record and its box clipped to the tile; a work estimate (rows in
-//      the tile x the chord length at the middle row);
-//   2. a counting sort of the batch by (rows, chord length), largest first;
-//   3. thread t walks sorted pair t and, when the batch holds more than kThreads pairs, also
-//      pair (m - 1 - t) from the light end: the 32 pairs a warp walks together have nearly
-//      the same loop shape, and every warp carries about the same total work, so no warp
-//      holds the block at its barrier for long.  Per row, the pixel interval where the
-//      exponent exceeds the cut is solved in closed form (widened by 1/100 pixel so that it
-//      contains every pixel the forward's test accepts), each pixel is re-tested exactly like
-//      the forward (same offsets, same expression), and the six moments of g exp(-q/2) are
-//      accumulated with dy factored out per row; one pair of float4 atomics per pair.
+// raster backward, per Gaussian (Sec. 3.5), with records on lanes.  The CTA shape is the
+// forward's: warps own blocks of 4 rows x BW columns of the (view, tile).  Per batch of staged
+// records, each warp lists the records whose cut ellipse reaches its block (closed-form test
+// of the ellipse against the block's rectangle, a superset of the per-pixel test) and takes
+// them 32 at a time, one per lane.  Every lane walks the block's 4 x BW pixels in the same
+// fully unrolled order, so the warp never diverges: dL/dI comes from shared memory as a
+// broadcast, the cut is decided exactly as in the forward (same offsets, same expression), and
+// the six moments of g exp(-q/2) stay in the lane's registers (row sums folded with dy).  A
+// lane then adds its six sums to the record's shared accumulators; after the batch one thread
+// per record adds them to the record's moments (two float4 atomics).
 // ------------------------------------------------------------------------------------------
 template <int T>
-__device__ __forceinline__ void bwd_walk(const float4 g, const float4 c, uint32_t box, int tx0,
-                                         int ty0, const float (*s_g)[T + 1], uint32_t rec,
-                                         float4* __restrict__ fpgrad) {
-  const int x0 = box & 0xFF, y0 = (box >> 8) & 0xFF, x1 = (box >> 16) & 0xFF, y1 = box >> 24;
-  if (x0 > x1) return;
-  const float inv2a = 0.5f / c.x;
-  float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-  for (int yy = y0; yy <= y1; ++yy) {
-    const float dy = (float)(ty0 + yy) - g.y;
-    const float B = row_b(c, dy), cdy2 = row_c(c, dy);
-    const float disc = B * B - 4.f * c.x * (cdy2 - g.w);
-    if (!(disc > 0.f)) continue;
-    const float ctr = g.x - (float)tx0 - B * inv2a, half = -sqrtf(disc) * inv2a;
-    const int xa = max(x0, (int)ceilf(ctr - half - 0.01f));
-    const int xb = min(x1, (int)floorf(ctr + half + 0.01f));
-    float r0 = 0.f, rx = 0.f, rxx = 0.f;
-    float fx = (float)(tx0 + xa);
-    for (int x = xa; x <= xb; ++x, fx += 1.f) {
-      const float dx = fx - g.x;
-      const float e = expo(c, dx, B, cdy2);
-      if (e > g.w) {
-        const float G = s_g[yy][x] * ex2(e);
-        const float Gx = G * dx;
-        r0 += G;
-        rx += Gx;
-        rxx = fmaf(Gx, dx, rxx);
-      }
-    }
-    s0 += r0;
-    sx += rx;
-    sxx += rxx;
-    sy = fmaf(dy, r0, sy);
-    sxy = fmaf(dy, rx, sxy);
-    syy = fmaf(dy * dy, r0, syy);
-  }
-  if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
-    atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(s0, sx, sy, sxx));
-    atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(sxy, syy, 0.f, 0.f));
-  }
-}
-
-template <int T>
-__global__ void __launch_bounds__(kThreads, 6)
+__global__ void __launch_bounds__(RasterShape<T>::NT)
     k_raster_bwd(const __grid_constant__ Batch b, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ vals, const float4* __restrict__ geo,
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
                  const float* __restrict__ dimg, float4* __restrict__ fpgrad,
                  const gs_status* st) {
-  constexpr int kRowCls = 16, kLenCls = 4, kBuckets = kRowCls * kLenCls;
-  constexpr int kBatch = 2 * kThreads;
+  using S = RasterShape<T>;
+  constexpr int BW = S::BW;
   __shared__ float s_g[T][T + 1];
-  __shared__ float4 s_geo[kBatch];
-  __shared__ float4 s_con[kBatch];
-  __shared__ uint32_t s_rec[kBatch];
-  __shared__ uint32_t s_box[kBatch];  // tile-local x0 | y0 << 8 | x1 << 16 | y1 << 24
-  __shared__ uint8_t s_key[kBatch];
-  __shared__ uint16_t s_perm[kBatch];
-  __shared__ uint32_t s_hist[kBuckets];
+  __shared__ float4 s_geo[S::NT];
+  __shared__ float4 s_con[S::NT];
+  __shared__ uint32_t s_rec[S::NT];
+  __shared__ uint32_t s_mask[S::NT];
+  __shared__ float s_acc[6][S::NT];
+  __shared__ uint16_t s_list[S::NW][S::NT];
   if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
   const uint2 r = ranges[key];
@@ -557,71 +511,106 @@ __global__ void __launch_bounds__(kThreads, 6)
   const int W = I.W, H = I.H;
   const int tx0 = (tile % I.TW) * T, ty0 = (tile / I.TW) * T;
   const float* dv = dimg + I.img_off + (int64_t)v * H * W;
-  const int t = threadIdx.x;
-  for (int p = t; p < T * T; p += kThreads) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int p = t; p < T * T; p += S::NT) {
     const int x = tx0 + p % T, y = ty0 + p / T;
     s_g[p / T][p % T] = (x < W && y < H) ? dv[(size_t)y * W + x] : 0.f;
   }
-  for (uint32_t base = r.x; base < r.y; base += kBatch) {
-    const int m = (int)min((uint32_t)kBatch, r.y - base);
+  const unsigned lt = gsd::lanemask_lt();
+  for (uint32_t base = r.x; base < r.y; base += S::NT) {
+    const int m = (int)min((uint32_t)S::NT, r.y - base);
     __syncthreads();
-    if (t < kBuckets) s_hist[t] = 0;
-    __syncthreads();
-    // phase 1: staging and work estimate of pairs t and t + kThreads
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = t + h * kThreads;
-      if (i >= m) break;
-      const uint32_t rec = vals[base + i];
-      const short4 bx = rect[rec];
-      const float4 g = geo[rec];
-      const float4 c = conic[rec];  // e = c.x dx^2 + c.y dx dy + c.z dy^2 with c.x < 0
-      s_rec[i] = rec;
-      s_geo[i] = g;
-      s_con[i] = c;
-      const int x0 = max((int)bx.x, tx0) - tx0, x1 = min((int)bx.z, tx0 + T - 1) - tx0;
-      const int y0 = max((int)bx.y, ty0) - ty0, y1 = min((int)bx.w, ty0 + T - 1) - ty0;
-      int rows = 0, len = 0;
-      if (x0 <= x1 && y0 <= y1) {
-        rows = y1 - y0 + 1;
-        const float dy = (float)(ty0 + ((y0 + y1) >> 1)) - g.y;
-        const float B = row_b(c, dy);
-        const float disc = B * B - 4.f * c.x * (row_c(c, dy) - g.w);
-        len = disc > 0.f ? min(x1 - x0 + 1, (int)(-sqrtf(disc) / c.x) + 1) : 1;
-      }
-      s_box[i] = rows ? (uint32_t)(x0 | (y0 << 8) | (x1 << 16) | (y1 << 24)) : 0x00000001u;
-      const int rc = rows ? min(kRowCls - 1, ((rows - 1) * kRowCls) / T) : 0;
-      const int lc = min(kLenCls - 1, (len * kLenCls) / (T + 1));
-      const int bucket = rows ? (kRowCls - 1 - rc) * kLenCls + (kLenCls - 1 - lc) : kBuckets - 1;
-      s_key[i] = (uint8_t)bucket;
-      atomicAdd(&s_hist[bucket], 1u);
-    }
-    __syncthreads();
-    // phase 2: counting sort by (rows, chord length), descending: one warp scans the 64
-    // bucket counts (two per lane), then every pair takes its rank
-    if (t < 32) {
-      const uint32_t a0 = s_hist[2 * t], a1 = s_hist[2 * t + 1];
-      const uint32_t incl = gsd::warp_inclusive_scan(a0 + a1);
-      const uint32_t excl = incl - (a0 + a1);
-      s_hist[2 * t] = excl;
-      s_hist[2 * t + 1] = excl + a0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = t + h * kThreads;
-      if (i < m) s_perm[atomicAdd(&s_hist[s_key[i]], 1u)] = (uint16_t)i;
-    }
-    __syncthreads();
-    // phase 3: sorted pair t, and its light partner m - 1 - t when the batch is over-full
     if (t < m) {
-      const int j = s_perm[t];
-      bwd_walk<T>(s_geo[j], s_con[j], s_box[j], tx0, ty0, s_g, s_rec[j], fpgrad);
+      const uint32_t rec = vals[base + t];
+      const float4 g = geo[rec], c = conic[rec];
+      const short4 bx = rect[rec];
+      s_rec[t] = rec;
+      s_geo[t] = g;
+      s_con[t] = c;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s_acc[q][t] = 0.f;
+      const Ell E = make_ell(g, c);
+      const int bx0 = max(0, (bx.x - tx0) >> S::LBW), bx1 = min(S::NBX - 1, (bx.z - tx0) >> S::LBW);
+      const int by0 = max(0, (bx.y - ty0) >> 2), by1 = min(S::NBY - 1, (bx.w - ty0) >> 2);
+      uint32_t mask = 0u;
+      for (int by = by0; by <= by1; ++by)
+        for (int bxi = bx0; bxi <= bx1; ++bxi) {
+          const float x0 = (float)(tx0 + bxi * BW), y0 = (float)(ty0 + by * 4);
+          if (ellipse_meets_rect(E, x0, x0 + (float)(BW - 1), y0, y0 + 3.f))
+            mask |= 1u << (by * S::NBX + bxi);
+        }
+      s_mask[t] = mask;
     }
-    const int t2 = m - 1 - t;
-    if (t2 >= kThreads) {
-      const int j = s_perm[t2];
-      bwd_walk<T>(s_geo[j], s_con[j], s_box[j], tx0, ty0, s_g, s_rec[j], fpgrad);
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < S::BPW; ++k) {
+      const int wb = w + k * S::NW;
+      const int bxl = (wb % S::NBX) * BW, byl = (wb / S::NBX) * 4;  // block origin in the tile
+      // this warp's list of the records that reach its block
+      int cnt = 0;
+      for (int j0 = 0; j0 < m; j0 += 32) {
+        const int jl = j0 + lane;
+        const bool hit = jl < m && ((s_mask[jl] >> wb) & 1u);
+        const unsigned bits = __ballot_sync(0xffffffffu, hit);
+        if (hit) s_list[w][cnt + __popc(bits & lt)] = (uint16_t)jl;
+        cnt += __popc(bits);
+      }
+      __syncwarp();
+      for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int li = c0 + lane;
+        const bool active = li < cnt;
+        const int j = active ? s_list[w][li] : 0;
+        const float4 g = s_geo[j];
+        const float4 c = s_con[j];
+        const float cut = active ? g.w : 1.f;  // e <= 0 < 1: an idle lane never passes
+        float dx[BW];
+#pragma unroll
+        for (int q = 0; q < BW; ++q) dx[q] = (float)(tx0 + bxl + q) - g.x;
+        float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+        for (int ry = 0; ry < 4; ++ry) {
+          const float dy = (float)(ty0 + byl + ry) - g.y;
+          const float B = row_b(c, dy), cdy2 = row_c(c, dy);
+          const float* grow = &s_g[byl + ry][bxl];
+          float r0 = 0.f, rx = 0.f, rxx = 0.f;
+#pragma unroll
+          for (int q = 0; q < BW; ++q) {
+            const float e = expo(c, dx[q], B, cdy2);
+            if (e > cut) {
+              const float G = grow[q] * ex2(e);
+              const float Gx = G * dx[q];
+              r0 += G;
+              rx += Gx;
+              rxx = fmaf(Gx, dx[q], rxx);
+            }
+          }
+          s0 += r0;
+          sx += rx;
+          sxx += rxx;
+          sy = fmaf(dy, r0, sy);
+          sxy = fmaf(dy, rx, sxy);
+          syy = fmaf(dy * dy, r0, syy);
+        }
+        if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
+          atomicAdd(&s_acc[0][j], s0);
+          atomicAdd(&s_acc[1][j], sx);
+          atomicAdd(&s_acc[2][j], sy);
+          atomicAdd(&s_acc[3][j], sxx);
+          atomicAdd(&s_acc[4][j], sxy);
+          atomicAdd(&s_acc[5][j], syy);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (t < m) {
+      const float a0 = s_acc[0][t], a1 = s_acc[1][t], a2 = s_acc[2][t];
+      const float a3 = s_acc[3][t], a4 = s_acc[4][t], a5 = s_acc[5][t];
+      if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f) {
+        const uint32_t rec = s_rec[t];
+        atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(a0, a1, a2, a3));
+        atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(a4, a5, 0.f, 0.f));
+      }
     }
   }
 }
@@ -784,7 +773,8 @@ int raster_fwd(const Plan& p, const Layout& L, const uint32_t* vals, float* img,
 template <int T>
 int raster_bwd(const Plan& p, const Layout& L, const uint32_t* vals, const float* dimg,
                cudaStream_t s) {
-  return launch("raster_bwd", k_raster_bwd<T>, dim3((unsigned)p.n_keys), dim3(kThreads), 0, s,
+  return launch("raster_bwd", k_raster_bwd<T>, dim3((unsigned)p.n_keys),
+                dim3(RasterShape<T>::NT), 0, s,
                 p.b, (const uint2*)L.ranges, vals, (const float4*)L.geo, (const float4*)L.conic,
                 (const short4*)L.rect, dimg, L.fpgrad, (const gs_status*)L.st);
 }
