@@ -85,21 +85,25 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_tv3d(const float* __restrict__ v, int nx, int ny, int nz, float scale,
            float* __restrict__ loss, float* __restrict__ grad, int accumulate) {
-  const int64_t total = (int64_t)nx * ny * nz;
+  // blocks stride over the (y, z) rows, threads over x: one index division per row
+  const int64_t rows = (int64_t)ny * nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny;
   float s = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / sz);
-    const float c = v[i];
-    float g = 0.f;
-    if (x + 1 < nx) { const float d = v[i + 1] - c; s += fabsf(d); g -= sgnf(d); }
-    if (x > 0) g += sgnf(c - v[i - 1]);
-    if (y + 1 < ny) { const float d = v[i + sy] - c; s += fabsf(d); g -= sgnf(d); }
-    if (y > 0) g += sgnf(c - v[i - sy]);
-    if (z + 1 < nz) { const float d = v[i + sz] - c; s += fabsf(d); g -= sgnf(d); }
-    if (z > 0) g += sgnf(c - v[i - sz]);
-    if (grad) grad[i] = (accumulate ? grad[i] : 0.f) + scale * g;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const int64_t r0 = row * nx;
+    for (int x = threadIdx.x; x < nx; x += kThreads) {
+      const int64_t i = r0 + x;
+      const float c = v[i];
+      float g = 0.f;
+      if (x + 1 < nx) { const float d = v[i + 1] - c; s += fabsf(d); g -= sgnf(d); }
+      if (x > 0) g += sgnf(c - v[i - 1]);
+      if (y + 1 < ny) { const float d = v[i + sy] - c; s += fabsf(d); g -= sgnf(d); }
+      if (y > 0) g += sgnf(c - v[i - sy]);
+      if (z + 1 < nz) { const float d = v[i + sz] - c; s += fabsf(d); g -= sgnf(d); }
+      if (z > 0) g += sgnf(c - v[i - sz]);
+      if (grad) grad[i] = (accumulate ? grad[i] : 0.f) + scale * g;
+    }
   }
   if (loss) block_add(s * scale, loss);
 }
@@ -649,7 +653,9 @@ int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float
                  float* d_grad, int accumulate, void* stream) {
   if (!d_vol || nx < 1 || ny < 1 || nz < 1) return GS_ERR_ARG;
   const int64_t total = (int64_t)nx * ny * nz;
-  return launch("tv3d_loss", k_tv3d, dim3(grid_for(total)), dim3(kThreads), 0,
+  const int64_t rows = (int64_t)ny * nz;
+  const int blocks = (int)std::min<int64_t>(rows, 8 * (int64_t)num_sms());
+  return launch("tv3d_loss", k_tv3d, dim3(blocks), dim3(kThreads), 0,
                 (cudaStream_t)stream, d_vol, nx, ny, nz, weight / (float)total, d_loss, d_grad,
                 accumulate);
 }
