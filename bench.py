@@ -152,6 +152,7 @@ def run_ours(args, ws, rank, local):
     import paper_2604_01844_gb300 as g
     from paper_2604_01844_gb300 import binding as B
     from paper_2604_01844_gb300 import build as gbuild
+    from paper_2604_01844_gb300 import replicas as R
 
     gbuild.build()
     torch.cuda.set_device(local)
@@ -194,13 +195,7 @@ def run_ours(args, ws, rank, local):
     B.timing_enable(False)
     launches = B.launch_count() - launches0
     per_kernel = B.timing_read()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = R.slowest(e0.elapsed_time(e1) / args.steps, device)
     loss = float(rec.loss.item())
 
     # end to end through the public API with host buffers: per step the parameters and the
@@ -227,13 +222,7 @@ def run_ours(args, ws, rank, local):
         h_loss.copy_(rec.loss, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_e2e], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = R.slowest(e2.elapsed_time(e3) / args.steps, device)
 
     if rank != 0:
         if ws > 1:
@@ -265,7 +254,20 @@ def run_ours(args, ws, rank, local):
                 "unit": "GB/s", "frac": None, "traffic": read_traffic(name),
                 "avg_launch_ms": round(avg_ms, 4), "launches": nl}
 
-    value = evals_px / (ms * 1e-3) * ws
+    # the same ALU roofline for every evaluation kernel of the step
+    kernel_roofs = {}
+    for kname, per_clk in EVALS_PER_SM_CLK.items():
+        if kname not in per_kernel:
+            continue
+        kl, kt = per_kernel[kname]
+        units = evals_px if kname.startswith("raster") else evals_vox
+        kpeak = sms * f_mhz * 1e6 * per_clk / 1e9
+        kach = units / ((kt / max(kl, 1)) * 1e-3) / 1e9
+        kernel_roofs[kname] = {"achieved": round(kach, 2), "peak": round(kpeak, 2),
+                               "unit": "Geval/s", "frac": round(kach / kpeak, 4),
+                               "evals_per_launch": units}
+
+    value = R.job_rate(evals_px, ms, ws)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -277,10 +279,10 @@ def run_ours(args, ws, rank, local):
                    "target": "projections of a second seeded Gaussian set",
                    "l2": "working set per step > 0.5 GB (images, SSIM maps, 256^3 volume) > L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "roofline": roof,
+        "roofline": roof, "kernel_rooflines": kernel_roofs,
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in
                                 sorted(per_kernel.items(), key=lambda kv: -kv[1][1])},
-        "e2e": {"value": evals_px / (ms_e2e * 1e-3) * ws, "unit": UNIT, "ms_per_step": ms_e2e,
+        "e2e": {"value": R.job_rate(evals_px, ms_e2e, ws), "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
@@ -291,6 +293,7 @@ def run_ours(args, ws, rank, local):
         out["learned_init"] = learned_vs_plain(device)
         out["batched"] = batched_learned_vs_plain(device)
         out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
+        out["scale_up"] = scale_up(device)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -550,6 +553,59 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
                    default=None)
         out[kind] = {"init_ms": round(init_ms, 1), "gaussians_from_mlp": n_mlp, "runs": runs,
                      "best_ms_to_target": best["ms_total"] if best else None}
+    return out
+
+
+def scale_up(device, steps=5, warmup=3):
+    """Reconstruction steps at the larger detector sizes: 75 cone views of 1024^2 with 200k
+    Gaussians, TV on 512^3 and the sorted lists rebuilt in the backward; 75 views of 2048^2
+    with 500k Gaussians, TV on the voxelized 1024^3 volume, raster tile chosen by the
+    autotuner.  Gaussian scales give footprints of about 4 and 6 pixels (sigma)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300.autotune import tune_tile
+    from paper_2604_01844_gb300.projector import Projector
+    from paper_2604_01844_gb300.recon import ReconConfig, Reconstruction
+
+    out = {}
+    for name, side, n, vol, median, recompute, tuned in (
+            ("75x1024^2, 200k Gaussians, TV 512^3, lists rebuilt in backward", 1024, 200000,
+             512, 0.0123, True, False),
+            ("75x2048^2, 500k Gaussians, TV 1024^3, autotuned tile", 2048, 500000, 1024,
+             0.0088, False, True)):
+        views = synth.cone_views(75, side, side)
+        model = synth.gaussians(21, n, radius=0.8, scale_median=median, scale_sigma_log=0.4)
+        tgt = synth.gaussians(22, n, radius=0.8, scale_median=median, scale_sigma_log=0.4)
+        d_tgt = [torch.from_numpy(a).to(device) for a in tgt]
+        tile, tune_ms = 16, None
+        if tuned:
+            d_model = [torch.from_numpy(a).to(device) for a in model]
+            tile, tune_ms = tune_tile(views, side, side, *d_model, device=device)
+            del d_model
+        target = Projector(views, side, side, tile=tile, device=device).forward(*d_tgt).clone()
+        del d_tgt
+        cfg = ReconConfig(tile=tile, recompute_lists=recompute)
+        rec = Reconstruction(views, side, side, target, synth.cube_grid(vol), *model, cfg=cfg,
+                             device=device)
+        evals = rec.projector.count_evals(*rec.act)
+        rec.plan()
+        for _ in range(warmup):
+            rec.step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            rec.step()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": round(ms, 3), "evals_per_step": evals,
+                     "value": evals / (ms * 1e-3), "unit": "evals/s", "tile": tile,
+                     "tile_timings_ms": tune_ms, "status": int(rec.projector.status().code)}
+        del rec, target
+        torch.cuda.empty_cache()
     return out
 
 

@@ -122,7 +122,9 @@ int gs_memset(void* d_ptr, int value, size_t bytes, void* stream);
 
 /* Bytes of workspace for projecting n Gaussians to n_views views of W x H pixels with room
  * for max_pairs (view, tile) pairs, including what gs_project_backward needs.  Returns 0 for
- * invalid sizes. */
+ * invalid sizes.  One call sorts at most 2^31 - 1 pairs (32-bit positions): callers split the
+ * views of larger problems into chunks (views are independent; images of a chunk are a
+ * contiguous slice, gradients accumulate with accumulate = 1). */
 size_t gs_project_workspace_size(int n, int n_views, int W, int H, const gs_opts* opts,
                                  int64_t max_pairs);
 

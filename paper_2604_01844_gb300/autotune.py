@@ -7,6 +7,7 @@ import math
 
 import torch
 
+from . import binding as B
 from .projector import Projector
 
 _CACHE: dict = {}
@@ -41,8 +42,11 @@ def tune_tile(views, W: int, H: int, mean_rho, scale, quat, candidates=(8, 16, 3
             proj.backward(mean_rho, scale, quat, dimg, reuse=True)
         e1.record()
         torch.cuda.synchronize()
-        times[t] = e0.elapsed_time(e1) / repeats
+        if proj.status().code == B.GS_OK:  # a run that skipped work is no candidate
+            times[t] = e0.elapsed_time(e1) / repeats
         del proj
+    if not times:
+        raise B.GsError("no raster tile size ran without error")
     best = min(times, key=times.get)
     _CACHE[key] = (best, times)
     return best, times

@@ -23,11 +23,19 @@ def views_to_device(views, device) -> torch.Tensor:
     return raw.to(device)
 
 
+# One library call sorts at most 2^31 - 1 (view, tile) pairs (32-bit positions); the projector
+# splits its views into chunks whose planned capacity stays below this.
+MAX_PAIRS_PER_CALL = (1 << 31) - (1 << 24)
+
+
 class Projector:
     """Projects Gaussians to a fixed set of views of a W x H detector.
 
     The workspace (device scratch owned by this object) is sized by counting the (view, tile)
-    pairs of the parameters first seen, times `headroom`; `ensure_capacity` re-plans it.
+    pairs of the parameters first seen, times `headroom`; `ensure_capacity` re-plans it.  When
+    the views would need more pairs than one call can sort, they are split into chunks of
+    consecutive views, each with its own workspace; the forward writes each chunk's images,
+    the backward accumulates the chunks' gradients.
     """
 
     def __init__(self, views, W: int, H: int, cut: float = 3.0, eps: float = 0.0,
@@ -38,10 +46,37 @@ class Projector:
         self.W, self.H = int(W), int(H)
         self.opts = B.opts(cut=cut, eps=eps, znear=znear, tile=tile)
         self.headroom = float(headroom)
+        self._kw = dict(cut=cut, eps=eps, znear=znear, tile=tile, device=device,
+                        headroom=headroom)
         self.ws = None
         self.ws_n = -1
         self.capacity = 0
         self._fwd_token = None
+        self.chunks = None  # [(v0, v1, Projector)] when the views are split
+
+    def _split(self, mean_rho, scale, quat, pairs: int):
+        """Splits the views into chunks of consecutive views whose capacity fits one call."""
+        n_chunks = 2
+        while True:
+            bounds = np.linspace(0, self.n_views, n_chunks + 1).round().astype(int)
+            chunks, ok = [], True
+            for v0, v1 in zip(bounds[:-1], bounds[1:]):
+                if v1 <= v0:
+                    continue
+                sub = Projector(self.views[v0:v1], self.W, self.H, **self._kw)
+                p = sub.count_pairs(mean_rho, scale, quat)
+                if p * self.headroom + 1024 > MAX_PAIRS_PER_CALL:
+                    ok = False
+                    break
+                sub._alloc(mean_rho.shape[0], int(p * self.headroom) + 1024)
+                chunks.append((int(v0), int(v1), sub))
+            if ok:
+                self.chunks = chunks
+                self.ws = None
+                return pairs
+            if n_chunks >= self.n_views:
+                raise B.GsError("a single view needs more pairs than one call can sort")
+            n_chunks = min(self.n_views, n_chunks * 2)
 
     # -- workspace -----------------------------------------------------------------------
     def workspace_bytes(self, n: int, pairs: int) -> int:
@@ -71,23 +106,39 @@ class Projector:
 
     def ensure_capacity(self, mean_rho, scale, quat) -> int:
         """Re-plans the workspace if the current parameters need more pairs; returns the count."""
+        if self.chunks is not None:
+            return sum(sub.ensure_capacity(mean_rho, scale, quat) for _, _, sub in self.chunks)
         pairs = self.count_pairs(mean_rho, scale, quat)
         n = mean_rho.shape[0]
+        if pairs * self.headroom + 1024 > MAX_PAIRS_PER_CALL:
+            return self._split(mean_rho, scale, quat, pairs)
         if self.ws_n != n or pairs > self.capacity:
             self._alloc(n, int(pairs * self.headroom) + 1024)
         return pairs
 
     def status(self) -> B.GsStatus:
+        """Status block of the last call (the first chunk reporting an error, if split)."""
+        if self.chunks is not None:
+            for _, _, sub in self.chunks:
+                st = sub.status()
+                if st.code != B.GS_OK:
+                    return st
+            return st
         return B.read_status(self.ws)
 
     # -- passes --------------------------------------------------------------------------
     def forward(self, mean_rho, scale, quat, out: torch.Tensor | None = None) -> torch.Tensor:
         mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
         n = mean_rho.shape[0]
-        if self.ws is None or self.ws_n != n or self.capacity == 0:
+        if self.chunks is None and (self.ws is None or self.ws_n != n or self.capacity == 0):
             self.ensure_capacity(mean_rho, scale, quat)
         if out is None:
             out = torch.empty((self.n_views, self.H, self.W), dtype=torch.float32, device=self.device)
+        if self.chunks is not None:
+            for v0, v1, sub in self.chunks:
+                sub.forward(mean_rho, scale, quat, out=out[v0:v1])
+            self._fwd_token = self._token(mean_rho, scale, quat)
+            return out
         B.check(B.lib().gs_project(
             B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
             self.W, self.H, ctypes.byref(self.opts), B.ptr(out), B.ptr(self.ws), self.ws.numel(),
@@ -100,13 +151,18 @@ class Projector:
         mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
         dimg = dimg.contiguous()
         n = mean_rho.shape[0]
-        if self.ws is None or self.ws_n != n or self.capacity == 0:
+        if self.chunks is None and (self.ws is None or self.ws_n != n or self.capacity == 0):
             self.ensure_capacity(mean_rho, scale, quat)
         if reuse is None:
             reuse = self._fwd_token == self._token(mean_rho, scale, quat)
         if grads is None:
             grads = tuple(torch.empty_like(t) for t in (mean_rho, scale, quat))
             accumulate = False
+        if self.chunks is not None:
+            for k, (v0, v1, sub) in enumerate(self.chunks):
+                sub.backward(mean_rho, scale, quat, dimg[v0:v1], grads=grads,
+                             accumulate=accumulate or k > 0, reuse=reuse)
+            return grads
         g_mr, g_sc, g_q = grads
         B.check(B.lib().gs_project_backward(
             B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
@@ -119,6 +175,10 @@ class Projector:
         """In-cut (pixel, Gaussian) evaluations of one forward (synchronises)."""
         n = mean_rho.shape[0]
         self.ensure_capacity(mean_rho, scale, quat)
+        if self.chunks is not None:
+            total = sum(sub.count_evals(mean_rho, scale, quat) for _, _, sub in self.chunks)
+            self._fwd_token = None
+            return total
         B.check(B.lib().gs_project_count_evals(
             B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
             self.W, self.H, ctypes.byref(self.opts), B.ptr(self.ws), self.ws.numel(),

@@ -34,6 +34,7 @@ class ReconConfig:
     tile: int = 16
     cut: float = 3.0
     tv_roi: tuple | None = None  # (lo, dim) of the TV region; None = whole grid
+    recompute_lists: bool = False  # backward rebuilds the sorted lists instead of reusing them
 
 
 def inverse_softplus(x: np.ndarray) -> np.ndarray:
@@ -111,7 +112,7 @@ class Reconstruction:
                                      B.ptr(self.loss), B.ptr(self.dimg), 1, B.ptr(self.ssim_ws),
                                      self.ssim_ws.numel(), s), "gs_ssim2d_loss")
         self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=False,
-                                reuse=True)
+                                reuse=not cfg.recompute_lists)
         if cfg.alpha_tv > 0:
             self.voxelizer.forward(*self.act, out=self.vol)
             dz, dy, dx = self.vol.shape

@@ -281,3 +281,29 @@ def test_full_size_sampled_pixels(orc, gsct):
     peak = float(np.abs(img).max())
     assert np.all(np.abs(got - want) <= IMG_TOL * peak + 2e-3 * np.abs(want)), \
         float(np.abs(got - want).max() / peak)
+
+
+def test_view_chunking_matches_single_call(gsct, monkeypatch):
+    """When the views need more pairs than one call can sort, the projector splits them into
+    chunks: images are identical to the single call, gradients agree (unordered atomics)."""
+    import torch
+
+    from paper_2604_01844_gb300 import projector as P
+
+    mr, sc, qt, views = _case(31, 3000, 12, 64, 64)
+    d = to_dev(mr, sc, qt)
+    one = gsct.Projector(views, 64, 64)
+    img1 = one.forward(*d)
+    w = torch.randn_like(img1)
+    g1 = one.backward(*d, w)
+    pairs = one.count_pairs(*d)
+    monkeypatch.setattr(P, "MAX_PAIRS_PER_CALL", pairs // 3)
+    many = gsct.Projector(views, 64, 64)
+    img2 = many.forward(*d)
+    assert many.chunks is not None and len(many.chunks) >= 3
+    assert torch.equal(img1, img2)
+    g2 = many.backward(*d, w)
+    for a, b in zip(g1, g2):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(a.abs().max()))
+    assert many.count_evals(*d) == one.count_evals(*d)
+    assert many.status().code == 0
