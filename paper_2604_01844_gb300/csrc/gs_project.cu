@@ -357,6 +357,56 @@ __device__ __forceinline__ float expo(const float4 c, float dx, float bdy, float
   return fmaf(fmaf(c.x, dx, bdy), dx, cdy2);
 }
 
+// Rows [ylo, yhi] (tile-local, clamped to [0, T-1]; ylo > yhi if none) that a record's cut
+// ellipse, enlarged like the tight tile rule (e > 1.001 e_cut), reaches inside the column
+// slab of pixel centres [x0, x1].  The ellipse's section by the slab is convex, so its rows
+// form an interval: its top (bottom) is the ellipse's own top (bottom) point when that lies in
+// the slab, else the boundary at the slab's nearer edge (the upper boundary is concave).
+// Widened by 1/100 pixel: a superset of the rows the per-pixel test accepts.
+struct SlabExt {
+  float dyt, dxt;  // the ellipse's top point relative to its centre (bottom = -top)
+};
+__device__ __forceinline__ SlabExt make_slab(const float4 c, float cm) {
+  const float kz = c.z - c.y * c.y * (0.25f / c.x);  // < 0
+  const float dyt = sqrtf(fmaxf(cm / kz, 0.f));
+  return SlabExt{dyt, -c.y * dyt * (0.5f / c.x)};
+}
+__device__ __forceinline__ void slab_rows(const float4 g, const float4 c, float cm,
+                                          const SlabExt& X, float x0, float x1, int ty0, int T,
+                                          int& ylo, int& yhi) {
+  const float u0 = x0 - g.x, u1 = x1 - g.x;
+  const float inv2c = 0.5f / c.z;  // < 0
+  const float xu = fminf(fmaxf(X.dxt, u0), u1), xl = fminf(fmaxf(-X.dxt, u0), u1);
+  const float Du = fmaxf(fmaf(c.y * xu, c.y * xu, -4.f * c.z * fmaf(c.x * xu, xu, -cm)), 0.f);
+  const float Dl = fmaxf(fmaf(c.y * xl, c.y * xl, -4.f * c.z * fmaf(c.x * xl, xl, -cm)), 0.f);
+  const float ymax = (-c.y * xu - sqrtf(Du)) * inv2c;
+  const float ymin = (-c.y * xl + sqrtf(Dl)) * inv2c;
+  ylo = max(0, (int)ceilf(g.y + ymin - 0.01f) - ty0);
+  yhi = min(T - 1, (int)floorf(g.y + ymax + 0.01f) - ty0);
+}
+
+// Bit mask of the (4-row x BW-column) blocks of a (T x T) tile at (tx0, ty0) that a record's
+// cut ellipse reaches: per column slab of its box, the reached rows (slab_rows) turned into
+// row bands.
+template <int T, int BW, int LBW, int NBX, int NBY>
+__device__ __forceinline__ uint32_t block_mask(const float4 g, const float4 c, const short4 bx,
+                                               int tx0, int ty0) {
+  const float cm = g.w * 1.001f;
+  const SlabExt X = make_slab(c, cm);
+  const int bx0 = max(0, (bx.x - tx0) >> LBW), bx1 = min(NBX - 1, (bx.z - tx0) >> LBW);
+  const int ry0 = max(0, bx.y - ty0), ry1 = min(T - 1, bx.w - ty0);
+  uint32_t mask = 0u;
+  for (int bxi = bx0; bxi <= bx1; ++bxi) {
+    const float x0 = (float)(tx0 + bxi * BW);
+    int ylo, yhi;
+    slab_rows(g, c, cm, X, x0, x0 + (float)(BW - 1), ty0, T, ylo, yhi);
+    ylo = max(ylo, ry0);
+    yhi = min(yhi, ry1);
+    for (int by = ylo >> 2; by <= (yhi >> 2) && ylo <= yhi; ++by) mask |= 1u << (by * NBX + bxi);
+  }
+  return mask;
+}
+
 // Raster CTA shape: warps own blocks of 4 rows x (8 PX) columns; a lane owns PX pixels of one
 // row, 8 columns apart, so that one record's row terms serve PX pixels.
 template <int T>
@@ -426,17 +476,11 @@ __global__ void __launch_bounds__(RasterShape<T>::NT)
     __syncthreads();
     if ((int)threadIdx.x < m) {
       const uint32_t rec = vals[base + threadIdx.x];
-      s_geo[threadIdx.x] = geo[rec];
-      s_con[threadIdx.x] = conic[rec];
-      const short4 bx = rect[rec];
-      const int bx0 = max(0, (bx.x - tx0) >> S::LBW), bx1 = min(S::NBX - 1, (bx.z - tx0) >> S::LBW);
-      const int by0 = max(0, (bx.y - ty0) >> 2), by1 = min(S::NBY - 1, (bx.w - ty0) >> 2);
-      uint32_t mask = 0u;
-      if (bx0 <= bx1) {
-        const uint32_t row = (2u << bx1) - (1u << bx0);
-        for (int by = by0; by <= by1; ++by) mask |= row << (by * S::NBX);
-      }
-      s_mask[threadIdx.x] = mask;
+      const float4 g = geo[rec], c = conic[rec];
+      s_geo[threadIdx.x] = g;
+      s_con[threadIdx.x] = c;
+      s_mask[threadIdx.x] =
+          block_mask<T, S::BW, S::LBW, S::NBX, S::NBY>(g, c, rect[rec], tx0, ty0);
     }
     __syncthreads();
 #pragma unroll
@@ -544,17 +588,7 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT)
       s_con[t] = c;
 #pragma unroll
       for (int q = 0; q < 6; ++q) s_acc[q][t] = 0.f;
-      const Ell E = make_ell(g, c);
-      const int bx0 = max(0, (bx.x - tx0) >> S::LBW), bx1 = min(S::NBX - 1, (bx.z - tx0) >> S::LBW);
-      const int by0 = max(0, (bx.y - ty0) >> 2), by1 = min(S::NBY - 1, (bx.w - ty0) >> 2);
-      uint32_t mask = 0u;
-      for (int by = by0; by <= by1; ++by)
-        for (int bxi = bx0; bxi <= bx1; ++bxi) {
-          const float x0 = (float)(tx0 + bxi * BW), y0 = (float)(ty0 + by * 4);
-          if (ellipse_meets_rect(E, x0, x0 + (float)(BW - 1), y0, y0 + 3.f))
-            mask |= 1u << (by * S::NBX + bxi);
-        }
-      s_mask[t] = mask;
+      s_mask[t] = block_mask<T, S::BW, S::LBW, S::NBX, S::NBY>(g, c, bx, tx0, ty0);
     }
     __syncthreads();
 #pragma unroll 1
