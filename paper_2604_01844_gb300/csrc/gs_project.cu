@@ -436,7 +436,7 @@ template <int T>
 using BwdBlocks = BlockShape<T, (T >= 16 ? 16 : 8)>;
 
 template <int T, bool COUNT>
-__global__ void __launch_bounds__(RasterShape<T>::NT)
+__global__ void __launch_bounds__(RasterShape<T>::NT, 2048 / RasterShape<T>::NT)
     k_raster_fwd(const __grid_constant__ Batch b, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ vals, const float4* __restrict__ geo,
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
