@@ -314,30 +314,62 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   __syncthreads();
-  if (cnt == 0) return;
-  uint32_t off = block_offs[blockIdx.x] + warp_pre[w] + incl - cnt;
-  const Inst& I = b.in[inst_of_item(b, idx)];
-  const int v = (int)((idx - I.item_off) / I.n);
-  const short4 r = rect[idx];
-  const int T = b.T;
-  const uint32_t kbase = (uint32_t)(I.key_off + (int64_t)v * I.TW * I.TH);
-  const int ntx = r.z / T - r.x / T + 1, nty = r.w / T - r.y / T + 1;
-  if (ntx * nty <= kMaskTiles) {
-    uint32_t tm = tmask[idx];
-    while (tm) {
-      const int bit = __ffs(tm) - 1;
-      tm &= tm - 1u;
-      const int ty = r.y / T + bit / ntx, tx = r.x / T + bit % ntx;
-      keys[off] = kbase + (uint32_t)(ty * I.TW + tx);
-      vals[off] = (uint32_t)idx;
-      ++off;
+  const uint32_t wbase = block_offs[blockIdx.x] + warp_pre[w];  // the warp's first pair
+  const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+  if (wtotal == 0) return;
+  // this lane's record (meaningful where cnt > 0)
+  int T = b.T, TW = 1, ntx = 1, tx0i = 0, ty0i = 0;
+  uint32_t kbase = 0, tm = 0;
+  bool small = true;
+  short4 r = make_short4(0, 0, 0, 0);
+  if (cnt > 0) {
+    const Inst& I = b.in[inst_of_item(b, idx)];
+    const int v = (int)((idx - I.item_off) / I.n);
+    r = rect[idx];
+    TW = I.TW;
+    kbase = (uint32_t)(I.key_off + (int64_t)v * I.TW * I.TH);
+    tx0i = r.x / T;
+    ty0i = r.y / T;
+    ntx = r.z / T - tx0i + 1;
+    const int nty = r.w / T - ty0i + 1;
+    small = ntx * nty <= kMaskTiles;
+    tm = tmask[idx];
+  }
+  // records with at most 32 box tiles: the warp writes its contiguous range of pairs
+  // cooperatively, pair p going to lane p % 32, which finds the owning record by a binary
+  // search over the lanes' inclusive counts and the tile as the owner's k-th listed tile
+  const uint32_t excl = incl - cnt;
+  for (uint32_t p0 = 0; p0 < wtotal; p0 += 32) {
+    const uint32_t p = p0 + lane;
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t ci = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      if (ci <= p) o += step;
     }
-  } else {
+    const uint32_t oe = __shfl_sync(0xffffffffu, excl, o);
+    const uint32_t otm = __shfl_sync(0xffffffffu, tm, o);
+    const uint32_t okb = __shfl_sync(0xffffffffu, kbase, o);
+    const int ontx = __shfl_sync(0xffffffffu, ntx, o);
+    const int otx0 = __shfl_sync(0xffffffffu, tx0i, o);
+    const int oty0 = __shfl_sync(0xffffffffu, ty0i, o);
+    const int otw = __shfl_sync(0xffffffffu, TW, o);
+    const bool osmall = __shfl_sync(0xffffffffu, small ? 1 : 0, o) != 0;
+    if (p < wtotal && osmall) {
+      const int bit = (int)__fns(otm, 0, (int)(p - oe) + 1);
+      const int ty = oty0 + bit / ontx, tx = otx0 + bit % ontx;
+      keys[wbase + p] = okb + (uint32_t)(ty * otw + tx);
+      vals[wbase + p] = (uint32_t)(idx - lane + o);
+    }
+  }
+  if (cnt == 0 || small) return;
+  uint32_t off = wbase + excl;
+  {
     const Ell E = make_ell(geo[idx], conic[idx]);
     for (int ty = r.y / T; ty <= r.w / T; ++ty)
       for (int tx = r.x / T; tx <= r.z / T; ++tx) {
         if (!tile_listed(E, T, tx, ty, r.x, r.y, r.z, r.w)) continue;
-        keys[off] = kbase + (uint32_t)(ty * I.TW + tx);
+        keys[off] = kbase + (uint32_t)(ty * TW + tx);
         vals[off] = (uint32_t)idx;
         ++off;
       }
