@@ -252,11 +252,12 @@ __global__ void __launch_bounds__(kSsimThreads)
     const float sxx = mo[2][j] - mx * mx, syy = mo[3][j] - my * my, sxy = mo[4][j] - mx * my;
     const float A = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
     const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
-    const float S = (A * Bn) / (C * D);
+    const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
+    const float S = (A * Bn) * inv;
     if (x < W && y < H) {
-      const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
-      const float dsxx = -S / D;
-      const float dsxy = 2.f * A / (C * D);
+      const float dmu = (2.f * my * Bn) * inv - S * (2.f * mx) * (D * inv);
+      const float dsxx = -S * (C * inv);
+      const float dsxy = 2.f * A * inv;
       const size_t o = (size_t)img * H * W + (size_t)y * W + x;
       maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
       maps[plane + o] = gscale * dsxx;
@@ -511,10 +512,11 @@ __global__ void __launch_bounds__(kSsimThreads)
       const float sxx = f[2][j] - mx * mx, syy = f[3][j] - my * my, sxy2 = f[4][j] - mx * my;
       const float A = 2.f * mx * my + C1, Bn = 2.f * sxy2 + C2;
       const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
-      const float S = (A * Bn) / (C * D);
-      const float dmu = (2.f * my * Bn) / (C * D) - S * (2.f * mx) / C;
-      const float dsxx = -S / D;
-      const float dsxy = 2.f * A / (C * D);
+      const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
+      const float S = (A * Bn) * inv;
+      const float dmu = (2.f * my * Bn) * inv - S * (2.f * mx) * (D * inv);
+      const float dsxx = -S * (C * inv);
+      const float dsxy = 2.f * A * inv;
       maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
       maps[plane + o] = gscale * dsxx;
       maps[2 * plane + o] = gscale * dsxy;
