@@ -294,6 +294,7 @@ def run_ours(args, ws, rank, local):
         out["batched"] = batched_learned_vs_plain(device)
         out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
         out["scale_up"] = scale_up(device)
+        out["warm_start"] = warm_start_study(device, side=args.warm_side, det=args.warm_det)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -556,6 +557,78 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
     return out
 
 
+def warm_start_study(device, side=512, det=1024, n_views=50, n=100000, fit_iters=50,
+                     n_iter=400, eval_every=5, factor=5, seed=1, n_ell=120):
+    """Prior-volume warm start against the cold (FDK-gradient) start, on the protocol of the
+    paper's warm-start study: target = projections of a phantom (n_views cone views of det^2,
+    side^3 grid), prior = the same phantom at a `factor` times coarser slice spacing resized to
+    the grid, fit of n Gaussians to the prior for fit_iters iterations (Eq. 6), then n_iter
+    reconstruction iterations (Eq. 5) from each start.  Reports both trajectories' best PSNR and
+    3D SSIM and tau_iter, the fraction of the n_iter iterations the warm start needs to reach
+    the cold start's best."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300.recon import (PhantomProblem, ReconConfig, Reconstruction,
+                                               fdk_volume, gradient_init)
+    from paper_2604_01844_gb300.warmstart import (VolumeScore, fit_prior, tau_iter,
+                                                   trajectory)
+
+    views = synth.cone_views(n_views, det, det)
+    grid = synth.cube_grid(side)
+    prob = PhantomProblem(synth.ellipsoid_phantom(seed, n_ell), views, det, det, grid,
+                          device=device)
+    prior = torch.from_numpy(synth.thick_slices(prob.gt.cpu().numpy(), factor)).to(device)
+    score = VolumeScore(prob.gt, prob.peak)
+    prior_db = score.psnr(prior)
+    prior_ssim = score.ssim(prior)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    u = np.random.default_rng(7).random((n, 4)).astype(np.float32)
+    ev[0].record()
+    fdk = fdk_volume(prob, grid)
+    cold0 = gradient_init(fdk, grid, n, u)
+    ev[1].record()
+    ev[2].record()
+    (mr, sc, q), fit = fit_prior(prior, grid, n, fit_iters, torch.from_numpy(u).to(device))
+    ev[3].record()
+    torch.cuda.synchronize()
+    fit_ok = fit.status().code == 0
+    del fdk
+    cfg = ReconConfig(**LR_FAST)
+    res = {}
+    for name, start in (("cold", cold0), ("warm", (mr, sc, q))):
+        rec = Reconstruction(views, det, det, prob.proj, grid, *[t.cpu().numpy() for t in start],
+                             cfg=cfg, device=device)
+        traj, replans = trajectory(rec, score, n_iter, eval_every, graph=True)
+        res[name] = traj
+        res[name + "_replans"] = replans
+        del rec
+        torch.cuda.empty_cache()
+    cold, warm = res["cold"], res["warm"]
+
+    def best(t, c):
+        return max(r[c] for r in t)
+
+    def summary(t):
+        return {"psnr_start_db": round(t[0][2], 2), "ssim_start": round(t[0][3], 4),
+                "psnr_best_db": round(best(t, 2), 2), "ssim_best": round(best(t, 3), 4),
+                "ms_per_iteration": round(t[-1][1] / n_iter, 3),
+                "psnr_db_every": [round(r[2], 2) for r in t[::max(1, len(t) // 8)]]}
+
+    return {"workload": f"{n_ell}-ellipsoid phantom, {n_views} cone views x {det}^2, {side}^3, "
+                        f"{n} Gaussians; prior = the phantom at {factor}x slice spacing",
+            "prior_psnr_db": round(prior_db, 2), "prior_ssim": round(prior_ssim, 4),
+            "fit_iters": fit_iters, "fit_ms": round(ev[2].elapsed_time(ev[3]), 2),
+            "fit_ok": fit_ok, "fdk_init_ms": round(ev[0].elapsed_time(ev[1]), 2),
+            "n_iter": n_iter, "eval_every": eval_every, "cold": summary(cold),
+            "warm": summary(warm), "replans": [res["cold_replans"], res["warm_replans"]],
+            "tau_iter_psnr": tau_iter(cold, warm, n_iter, 2),
+            "tau_iter_ssim": tau_iter(cold, warm, n_iter, 3),
+            "note": "tau_iter = first evaluated warm iteration reaching the cold start's best "
+                    "within n_iter, / n_iter; trajectories evaluated every eval_every iterations"}
+
+
 def scale_up(device, steps=5, warmup=3):
     """Reconstruction steps at the larger detector sizes: 75 cone views of 1024^2 with 200k
     Gaussians, TV on 512^3 and the sorted lists rebuilt in the backward; 75 views of 2048^2
@@ -760,6 +833,8 @@ def main():
                     help="skip the time-to-PSNR and volume-fit measurements")
     ap.add_argument("--fit-side", type=int, default=1024)
     ap.add_argument("--fit-gaussians", type=int, default=500000)
+    ap.add_argument("--warm-side", type=int, default=512)
+    ap.add_argument("--warm-det", type=int, default=1024)
     ap.add_argument("--workload", choices=["recon512", "small"], default="recon512",
                     help="small: 16-view case of the same kernels, for profiler captures")
     args = ap.parse_args()

@@ -345,8 +345,9 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
 
 /* 3D SSIM term of Eq. 6: weight * (1 - mean SSIM) over a volume [z][y][x] with the separable
  * 11 x 11 x 11 Gaussian window (sigma 1.5), zero-padded, constants as in 2D; gradient w.r.t.
- * x written (accumulate = 0) or added.  d_ws: gs_ssim3d_workspace_size(nx ny nz) bytes, else
- * GS_ERR_CAPACITY; nz <= 65535. */
+ * x written (accumulate = 0) or added; d_grad = NULL evaluates the value only (d_loss then
+ * required).  d_ws: gs_ssim3d_workspace_size(nx ny nz) bytes, else GS_ERR_CAPACITY;
+ * nz <= 65535. */
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);

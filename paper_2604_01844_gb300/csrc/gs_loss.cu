@@ -755,9 +755,10 @@ size_t gs_ssim3d_workspace_size(int64_t n_voxels) {
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream) {
-  if (!d_x || !d_y || !d_grad || !d_ws || nx < 1 || ny < 1 || nz < 1 || !(data_range > 0.f))
+  if (!d_x || !d_y || !d_ws || nx < 1 || ny < 1 || nz < 1 || !(data_range > 0.f))
     return GS_ERR_ARG;
   if (nz > 65535) return GS_ERR_ARG;
+  if (!d_grad && !d_loss) return GS_ERR_ARG;
   const int64_t plane = (int64_t)nx * ny * nz;
   if (ws_bytes < gs_ssim3d_workspace_size(plane)) return GS_ERR_CAPACITY;
   // the forward's xy kernel needs more than the default 48 KB of dynamic shared memory; the
@@ -787,6 +788,7 @@ int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, f
   GS_TRY(launch("ssim3d_xy_fwd", k_ssim3d_xy<0>, gxy, bxy, ssim3d_xy_smem<0>(), s, W,
                 (const float*)tmp, nx, ny, plane, C1, C2, gscale, d_loss, maps, nul, nul,
                 (float*)nullptr, 0));
+  if (!d_grad) return GS_OK;  // value only
   GS_TRY(launch("ssim3d_z_bwd", k_ssim3d_z<3>, gz, bz, 0, s, W, (const float*)maps,
                 (const float*)(maps + plane), (const float*)(maps + 2 * plane), nx, ny, nz,
                 plane, tmp));

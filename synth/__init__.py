@@ -193,3 +193,46 @@ def batch_specs(seeds=range(100, 116), sides=(128, 192, 256, 320, 384),
                         n=int(rng.integers(gaussians[0], gaussians[1] + 1)),
                         n_ellipsoids=int(n_ellipsoids)))
     return out
+
+
+def perturbed_phantom(ell: np.ndarray, seed: int, att_jitter: float = 0.2,
+                      shift: float = 0.01, axis_jitter: float = 0.05,
+                      drop_frac: float = 0.1) -> np.ndarray:
+    """A prior for a phantom (an earlier scan of the same object): every ellipsoid's
+    attenuation scaled by U(1 - att_jitter, 1 + att_jitter), its centre shifted by
+    N(0, shift^2) per axis, its semi-axes scaled by U(1 - axis_jitter, 1 + axis_jitter), and a
+    fraction drop_frac of the ellipsoids removed.  Rows as in ellipsoid_phantom."""
+    rng = _rng(seed)
+    e = np.array(ell, dtype=np.float64, copy=True)
+    n = e.shape[0]
+    e[:, 10] *= rng.uniform(1.0 - att_jitter, 1.0 + att_jitter, n)
+    e[:, 0:3] += rng.normal(0.0, shift, (n, 3))
+    e[:, 3:6] *= rng.uniform(1.0 - axis_jitter, 1.0 + axis_jitter, (n, 3))
+    keep = rng.random(n) >= drop_frac
+    return e[keep]
+
+
+def thick_slices(vol: np.ndarray, factor: int) -> np.ndarray:
+    """A lower longitudinal resolution scan of the same volume ([z][y][x]), resized back to its
+    grid: slices averaged in consecutive groups of `factor` (a trailing partial group over its
+    own slices), then linearly interpolated in z from the groups' centres to every slice's
+    centre (held constant beyond the first and last group centre).  Works slice by slice, so
+    a 512^3 volume needs no more than its output's memory."""
+    v = np.asarray(vol)
+    nz = v.shape[0]
+    starts = list(range(0, nz, factor))
+    groups = [v[a:a + factor].astype(np.float64).mean(axis=0) for a in starts]
+    centres = [a + (min(a + factor, nz) - a - 1) / 2.0 for a in starts]
+    out = np.empty(v.shape, dtype=np.float32)
+    g = 0
+    for z in range(nz):
+        while g + 2 < len(starts) and centres[g + 1] <= z:
+            g += 1
+        if len(starts) == 1 or z <= centres[0]:
+            out[z] = groups[0]
+        elif z >= centres[-1]:
+            out[z] = groups[-1]
+        else:
+            t = (z - centres[g]) / (centres[g + 1] - centres[g])
+            out[z] = (1.0 - t) * groups[g] + t * groups[g + 1]
+    return out
