@@ -149,13 +149,30 @@ int gs_project(const float* d_mean_rho, const float* d_scale, const float* d_qua
  * the gradient arrays instead of overwriting them.  reuse = 1: the workspace still holds the
  * lists of a gs_project call with the same parameters and geometry; reuse = 0 rebuilds them
  * (recompute, no stored lists needed).  The truncation mask is held constant (its boundary is
- * not differentiated).  Per-Gaussian backward (Sec. 3.5): one thread per (Gaussian, tile)
- * pair walks the exact chords of its ellipse and issues one set of atomics per pair. */
+ * not differentiated).  Per-Gaussian backward (Sec. 3.5): each pixel block of a tile lists
+ * the (Gaussian, view) records whose ellipse reaches it, lanes take records and sum each
+ * record's six footprint moments over the block's pixels (one set of atomics per record and
+ * block); a final pass chains the moments of all views to each Gaussian's parameters. */
 int gs_project_backward(const float* d_mean_rho, const float* d_scale, const float* d_quat,
                         int n, const gs_view* d_views, int n_views, int W, int H,
                         const gs_opts* opts, const float* d_dimg, float* d_g_mean_rho,
                         float* d_g_scale, float* d_g_quat, int accumulate, int reuse,
                         void* d_ws, size_t ws_bytes, void* stream);
+
+/* gs_project_backward that also accumulates the statistics of adaptive density control (the
+ * prune / clone / split step of the optimisation loop, Sec. 3.4; see gs_densify): for every
+ * Gaussian i and every view in which (i, view) has at least one listed tile,
+ *   d_grad_stat[i] += |(W/2 dL/dpx, H/2 dL/dpy)|   (detector-position gradient in normalised
+ *                                                  device coordinates: W pixels span [-1, 1])
+ *   d_vis[i]       += 1.
+ * Both arrays (n entries) are added to, never cleared; zero them when a window starts.  Both
+ * NULL = gs_project_backward; one of them NULL = GS_ERR_ARG. */
+int gs_project_backward_stats(const float* d_mean_rho, const float* d_scale,
+                              const float* d_quat, int n, const gs_view* d_views, int n_views,
+                              int W, int H, const gs_opts* opts, const float* d_dimg,
+                              float* d_g_mean_rho, float* d_g_scale, float* d_g_quat,
+                              float* d_grad_stat, int32_t* d_vis, int accumulate, int reuse,
+                              void* d_ws, size_t ws_bytes, void* stream);
 
 /* Counts the (pixel, Gaussian) evaluations inside the cut of the current parameters (the
  * algorithmic work of one forward) into the status block's `evals` field; uses and rebuilds
@@ -205,6 +222,13 @@ int gs_project_batch_backward(const float* d_mean_rho, const float* d_scale,
                               const float* d_dimg, float* d_g_mean_rho, float* d_g_scale,
                               float* d_g_quat, int accumulate, int reuse, void* d_ws,
                               size_t ws_bytes, void* stream);
+int gs_project_batch_backward_stats(const float* d_mean_rho, const float* d_scale,
+                                    const float* d_quat, const gs_view* d_views,
+                                    const gs_instance* h_inst, int n_inst, const gs_opts* opts,
+                                    const float* d_dimg, float* d_g_mean_rho,
+                                    float* d_g_scale, float* d_g_quat, float* d_grad_stat,
+                                    int32_t* d_vis, int accumulate, int reuse, void* d_ws,
+                                    size_t ws_bytes, void* stream);
 int gs_project_batch_count_evals(const float* d_mean_rho, const float* d_scale,
                                  const float* d_quat, const gs_view* d_views,
                                  const gs_instance* h_inst, int n_inst, const gs_opts* opts,
@@ -372,6 +396,59 @@ int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, f
                  float* d_v, const float* d_g_mean_rho, const float* d_g_scale,
                  const float* d_g_quat, float* d_mean_rho, float* d_scale, float* d_quat, int n,
                  int* d_step, const gs_adam_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Adaptive density control: prune, clone and split (the optimisation loop of Sec. 3.4 names
+ * the three operations; the rules are those of the 3D Gaussian splatting lineage the paper
+ * builds on, restated for additive X-ray rendering).
+ *
+ * Per Gaussian, with mean statistic g = grad_scale * grad_stat / vis (0 if vis = 0), rho its
+ * density and s_max its largest scale:
+ *   prune   when rho < min_density or s_max > max_scale;
+ *   else densify when vis > 0 and g >= grad_threshold:
+ *     split when s_max > split_scale: two children at p + R(q) diag(s) z_k (z_k = the
+ *           standard normal draws d_normals[6i + 3k .. 6i + 3k + 2]), log-scales
+ *           max(log s - log split_factor, min_log_scale), density rho split_factor^3 / 2
+ *           (the pair keeps the parent's integrated density rho (2 pi)^(3/2) sx sy sz), zero
+ *           Adam moments;
+ *     clone otherwise: two copies with density rho / 2 (together they render as the parent);
+ *           the first keeps the Adam moments, the second starts from zero moments;
+ *   else keep.
+ * Budget: when the densify candidates do not all fit under max_gaussians (counting the
+ * Gaussians that stay), only the max_gaussians - (n - pruned) candidates with the highest
+ * grad_stat / vis are densified (ties: lower index first; none if that number is <= 0).
+ * ------------------------------------------------------------------------------------- */
+typedef struct gs_densify_opts {
+  float grad_threshold;  /* densify when the mean statistic reaches this */
+  float grad_scale;      /* views per step: the statistic of the all-views mean loss times
+                            this is the per-view loss's */
+  float split_scale;     /* largest scale above which a densified Gaussian is split */
+  float split_factor;    /* a split child's scales are the parent's / split_factor (> 1) */
+  float min_density;     /* prune below this density */
+  float max_scale;       /* prune above this largest scale */
+  float min_log_scale;   /* lower clamp of the children's raw log-scales */
+  int32_t max_gaussians; /* budget of Gaussians after densification (>= 0) */
+} gs_densify_opts;
+
+/* Workspace bytes of gs_densify for n Gaussians. */
+size_t gs_densify_workspace_size(int n);
+
+/* Applies the rules to n Gaussians in raw (optimiser) form as gs_adam_step keeps them:
+ * d_raw_mean_rho = (x, y, z, softplus^-1(rho)), d_raw_scale = (log sx, log sy, log sz, 0),
+ * d_raw_quat = (w, x, y, z), d_m / d_v their Adam moments (3 float4 per Gaussian), with the
+ * statistics of gs_project_backward_stats and d_normals (6n floats).  Writes the surviving
+ * Gaussians and the children in Gaussian order (a densified Gaussian's two children next to
+ * each other) to the d_out_* arrays, which hold out_capacity Gaussians (moments: 3 float4
+ * each) and must not overlap the inputs.  Asynchronous; the result is the status block of
+ * d_ws (gs_read_status): pairs = number of output Gaussians, code = GS_ERR_CAPACITY if that
+ * exceeds out_capacity (then nothing is written), reserved[0..3] = pruned, cloned, split and
+ * candidate counts.  out_capacity = min(2n, max(n, max_gaussians)) always suffices. */
+int gs_densify(const float* d_raw_mean_rho, const float* d_raw_scale, const float* d_raw_quat,
+               const float* d_m, const float* d_v, const float* d_grad_stat,
+               const int32_t* d_vis, const float* d_normals, int n, const gs_densify_opts* opts,
+               float* d_out_raw_mean_rho, float* d_out_raw_scale, float* d_out_raw_quat,
+               float* d_out_m, float* d_out_v, int out_capacity, void* d_ws, size_t ws_bytes,
+               void* stream);
 
 /* *d_step += 1 on the device (step counter of gs_adam_flat users). */
 int gs_step_incr(int* d_step, void* stream);

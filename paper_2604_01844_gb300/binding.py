@@ -67,11 +67,19 @@ class GsVoxelInstance(ctypes.Structure):
                 ("roi_dim", ctypes.c_int32 * 3)]
 
 
+class GsDensifyOpts(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("grad_scale", ctypes.c_float),
+                ("split_scale", ctypes.c_float), ("split_factor", ctypes.c_float),
+                ("min_density", ctypes.c_float), ("max_scale", ctypes.c_float),
+                ("min_log_scale", ctypes.c_float), ("max_gaussians", ctypes.c_int32)]
+
+
 MAX_INSTANCES = 32
 
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
 assert ctypes.sizeof(GsInstance) == 16 and ctypes.sizeof(GsVoxelInstance) == 64
 assert ctypes.sizeof(GsAdamOpts) == 48
+assert ctypes.sizeof(GsDensifyOpts) == 32
 assert ctypes.sizeof(GsStatus) == 256
 
 _lib = None
@@ -95,6 +103,8 @@ SIGNATURES = {
     "gs_project": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _P, _SZ, _P]),
     "gs_project_backward": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _P, _P, _P, _I, _I,
                                  _P, _SZ, _P]),
+    "gs_project_backward_stats": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _P, _P, _P,
+                                       _P, _P, _I, _I, _P, _SZ, _P]),
     "gs_project_count_evals": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _SZ, _P]),
     "gs_project_batch_workspace_size": (_SZ, [_INST, _I, _OPTS, _I64]),
     "gs_project_batch_count_pairs": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _SZ, _P,
@@ -102,6 +112,8 @@ SIGNATURES = {
     "gs_project_batch": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _P, _SZ, _P]),
     "gs_project_batch_backward": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _P, _P, _P, _I,
                                        _I, _P, _SZ, _P]),
+    "gs_project_batch_backward_stats": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _P, _P, _P,
+                                             _P, _P, _I, _I, _P, _SZ, _P]),
     "gs_project_batch_count_evals": (_I, [_P, _P, _P, _P, _INST, _I, _OPTS, _P, _SZ, _P]),
     "gs_voxelize_workspace_size": (_SZ, [_I, _GRID, _I3, _I3, _OPTS, _I64]),
     "gs_voxelize_count_pairs": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P,
@@ -131,6 +143,9 @@ SIGNATURES = {
                                     _I, _P]),
     "gs_adam_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P,
                           ctypes.c_void_p, _P]),
+    "gs_densify_workspace_size": (_SZ, [_I]),
+    "gs_densify": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(GsDensifyOpts), _P, _P,
+                        _P, _P, _P, _I, _P, _SZ, _P]),
     "gs_activate": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
     "gs_phantom_project": (_I, [_P, _I, _P, _I, _I, _I, _P, _P]),
     "gs_phantom_voxelize": (_I, [_P, _I, _GRID, _P, _P]),

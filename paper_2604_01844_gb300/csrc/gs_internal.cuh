@@ -151,6 +151,9 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
   return v;
 }
 
+// Density activation of the optimiser's raw parameter: softplus, linear above 20.
+__device__ __forceinline__ float softplus(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
 // Rotation matrix of the unit quaternion (w, x, y, z).
 __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float R[3][3]) {
   R[0][0] = 1.f - 2.f * (y * y + z * z);

@@ -537,7 +537,7 @@ constexpr size_t ssim3d_xy_smem() {
 // ------------------------------------------------------------------------------------------
 // Adam with activations: mean raw, density softplus(raw), scale exp(raw), quaternion raw.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float softplusf(float x) { return gsd::softplus(x); }
 __device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + expf(-x)); }
 
 __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float lr, float b1,

@@ -704,7 +704,9 @@ __global__ void __launch_bounds__(kThreads)
                     const float4* __restrict__ scale, const float4* __restrict__ quat,
                     int total_n, const ViewFrame* __restrict__ frames,
                     const float4* __restrict__ fpgrad, float4* __restrict__ g_mr,
-                    float4* __restrict__ g_sc, float4* __restrict__ g_q, int accumulate) {
+                    float4* __restrict__ g_sc, float4* __restrict__ g_q, int accumulate,
+                    const uint32_t* __restrict__ counts, float* __restrict__ stat,
+                    int* __restrict__ vis) {
   const int gi = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (gi >= total_n) return;
@@ -714,8 +716,13 @@ __global__ void __launch_bounds__(kThreads)
   float acc[11];
 #pragma unroll
   for (int k = 0; k < 11; ++k) acc[k] = 0.f;
+  // adaptive density control statistics: NDC detector-position gradient norms and the
+  // number of views with a listed tile
+  float st_acc = 0.f;
+  int vis_acc = 0;
   for (int v = lane; v < I.nv; v += 32) {
     const size_t rec = (size_t)(I.item_off + (int64_t)v * I.n + il);
+    if (stat && counts[rec] > 0u) ++vis_acc;
     const float4 m0 = fpgrad[2 * rec], m1 = fpgrad[2 * rec + 1];
     if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f)
       continue;
@@ -725,6 +732,13 @@ __global__ void __launch_bounds__(kThreads)
     if (!footprint(mr, sc, qt, f, I.W, I.H, b.cut2, b.eps, b.znear, o, x0, y0, x1, y1)) continue;
     float gp[3], grho, gs3[3], gq[4];
     chain_one(o, f, m0, m1, gp, grho, gs3, gq);
+    if (stat) {
+      // dI/dpx = A e (ca dx + cb dy) summed against dL/dI: the moments' first-order terms
+      const float dpx = o.A * (o.ca * m0.y + o.cb * m0.z);
+      const float dpy = o.A * (o.cb * m0.y + o.cc * m0.z);
+      const float nx = 0.5f * (float)I.W * dpx, ny = 0.5f * (float)I.H * dpy;
+      st_acc += sqrtf(nx * nx + ny * ny);
+    }
     acc[0] += gp[0]; acc[1] += gp[1]; acc[2] += gp[2]; acc[3] += grho;
     acc[4] += gs3[0]; acc[5] += gs3[1]; acc[6] += gs3[2];
     acc[7] += gq[0]; acc[8] += gq[1]; acc[9] += gq[2]; acc[10] += gq[3];
@@ -744,6 +758,14 @@ __global__ void __launch_bounds__(kThreads)
     g_mr[gi] = a;
     g_sc[gi] = bb;
     g_q[gi] = c;
+  }
+  if (stat) {
+    st_acc = gsd::warp_sum(st_acc);
+    vis_acc = gsd::warp_sum(vis_acc);
+    if (lane == 0) {
+      stat[gi] += st_acc;
+      vis[gi] += vis_acc;
+    }
   }
 }
 
@@ -944,12 +966,14 @@ int gs_project_batch_count_evals(const float* d_mean_rho, const float* d_scale,
   return dispatch_fwd(p, L, v, nullptr, true, s);
 }
 
-int gs_project_batch_backward(const float* d_mean_rho, const float* d_scale,
-                              const float* d_quat, const gs_view* d_views,
-                              const gs_instance* inst, int n_inst, const gs_opts* opts,
-                              const float* d_dimg, float* d_g_mean_rho, float* d_g_scale,
-                              float* d_g_quat, int accumulate, int reuse, void* d_ws,
-                              size_t ws_bytes, void* stream) {
+int gs_project_batch_backward_stats(const float* d_mean_rho, const float* d_scale,
+                                    const float* d_quat, const gs_view* d_views,
+                                    const gs_instance* inst, int n_inst, const gs_opts* opts,
+                                    const float* d_dimg, float* d_g_mean_rho,
+                                    float* d_g_scale, float* d_g_quat, float* d_grad_stat,
+                                    int32_t* d_vis, int accumulate, int reuse, void* d_ws,
+                                    size_t ws_bytes, void* stream) {
+  if ((d_grad_stat == nullptr) != (d_vis == nullptr)) return GS_ERR_ARG;
   Plan p;
   Layout L;
   GS_TRY(prepare(inst, n_inst, opts, d_mean_rho, d_scale, d_quat, d_views, d_ws, ws_bytes, p,
@@ -977,7 +1001,20 @@ int gs_project_batch_backward(const float* d_mean_rho, const float* d_scale,
   return launch("project_chain", k_project_chain, dim3(blocks), dim3(kThreads), 0, s, p.b,
                 (const float4*)d_mean_rho, (const float4*)d_scale, (const float4*)d_quat,
                 p.total_n, (const ViewFrame*)L.frames, (const float4*)L.fpgrad,
-                (float4*)d_g_mean_rho, (float4*)d_g_scale, (float4*)d_g_quat, accumulate);
+                (float4*)d_g_mean_rho, (float4*)d_g_scale, (float4*)d_g_quat, accumulate,
+                (const uint32_t*)L.counts, d_grad_stat, (int*)d_vis);
+}
+
+int gs_project_batch_backward(const float* d_mean_rho, const float* d_scale,
+                              const float* d_quat, const gs_view* d_views,
+                              const gs_instance* inst, int n_inst, const gs_opts* opts,
+                              const float* d_dimg, float* d_g_mean_rho, float* d_g_scale,
+                              float* d_g_quat, int accumulate, int reuse, void* d_ws,
+                              size_t ws_bytes, void* stream) {
+  return gs_project_batch_backward_stats(d_mean_rho, d_scale, d_quat, d_views, inst, n_inst,
+                                         opts, d_dimg, d_g_mean_rho, d_g_scale, d_g_quat,
+                                         nullptr, nullptr, accumulate, reuse, d_ws, ws_bytes,
+                                         stream);
 }
 
 // ---- single instance = batch of one ------------------------------------------------------
@@ -1022,6 +1059,19 @@ int gs_project_backward(const float* d_mean_rho, const float* d_scale, const flo
   return gs_project_batch_backward(d_mean_rho, d_scale, d_quat, d_views, &i, 1, opts, d_dimg,
                                    d_g_mean_rho, d_g_scale, d_g_quat, accumulate, reuse, d_ws,
                                    ws_bytes, stream);
+}
+
+int gs_project_backward_stats(const float* d_mean_rho, const float* d_scale,
+                              const float* d_quat, int n, const gs_view* d_views, int n_views,
+                              int W, int H, const gs_opts* opts, const float* d_dimg,
+                              float* d_g_mean_rho, float* d_g_scale, float* d_g_quat,
+                              float* d_grad_stat, int32_t* d_vis, int accumulate, int reuse,
+                              void* d_ws, size_t ws_bytes, void* stream) {
+  const gs_instance i = one(n, n_views, W, H);
+  return gs_project_batch_backward_stats(d_mean_rho, d_scale, d_quat, d_views, &i, 1, opts,
+                                         d_dimg, d_g_mean_rho, d_g_scale, d_g_quat,
+                                         d_grad_stat, d_vis, accumulate, reuse, d_ws, ws_bytes,
+                                         stream);
 }
 
 }  // extern "C"

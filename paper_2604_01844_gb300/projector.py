@@ -147,7 +147,10 @@ class Projector:
         return out
 
     def backward(self, mean_rho, scale, quat, dimg, grads=None, accumulate: bool = False,
-                 reuse: bool | None = None):
+                 reuse: bool | None = None, stats=None):
+        """dL/d(mean_rho, scale, quat) from dL/dimg.  stats = (grad_stat float32 (n,),
+        vis int32 (n,)) additionally accumulates the adaptive density control statistics
+        (gs_project_backward_stats)."""
         mean_rho, scale, quat = _f4(mean_rho, "mean_rho"), _f4(scale, "scale"), _f4(quat, "quat")
         dimg = dimg.contiguous()
         n = mean_rho.shape[0]
@@ -161,14 +164,25 @@ class Projector:
         if self.chunks is not None:
             for k, (v0, v1, sub) in enumerate(self.chunks):
                 sub.backward(mean_rho, scale, quat, dimg[v0:v1], grads=grads,
-                             accumulate=accumulate or k > 0, reuse=reuse)
+                             accumulate=accumulate or k > 0, reuse=reuse, stats=stats)
             return grads
         g_mr, g_sc, g_q = grads
-        B.check(B.lib().gs_project_backward(
+        if stats is None:
+            B.check(B.lib().gs_project_backward(
+                B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
+                self.W, self.H, ctypes.byref(self.opts), B.ptr(dimg), B.ptr(g_mr), B.ptr(g_sc),
+                B.ptr(g_q), 1 if accumulate else 0, 1 if reuse else 0, B.ptr(self.ws),
+                self.ws.numel(), B.stream_handle()), "gs_project_backward")
+            return g_mr, g_sc, g_q
+        stat, vis = stats
+        if stat.dtype != torch.float32 or vis.dtype != torch.int32 or stat.numel() != n or \
+                vis.numel() != n:
+            raise ValueError("stats: float32 and int32 arrays of n entries")
+        B.check(B.lib().gs_project_backward_stats(
             B.ptr(mean_rho), B.ptr(scale), B.ptr(quat), n, B.ptr(self.views), self.n_views,
             self.W, self.H, ctypes.byref(self.opts), B.ptr(dimg), B.ptr(g_mr), B.ptr(g_sc),
-            B.ptr(g_q), 1 if accumulate else 0, 1 if reuse else 0, B.ptr(self.ws),
-            self.ws.numel(), B.stream_handle()), "gs_project_backward")
+            B.ptr(g_q), B.ptr(stat), B.ptr(vis), 1 if accumulate else 0, 1 if reuse else 0,
+            B.ptr(self.ws), self.ws.numel(), B.stream_handle()), "gs_project_backward_stats")
         return g_mr, g_sc, g_q
 
     def count_evals(self, mean_rho, scale, quat) -> int:

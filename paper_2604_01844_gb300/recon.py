@@ -83,6 +83,19 @@ class Reconstruction:
         o.beta1, o.beta2, o.eps = cfg.beta1, cfg.beta2, cfg.eps
         o.min_log_scale, o.max_log_scale = cfg.min_log_scale, cfg.max_log_scale
         self.adam_opts = o
+        self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set
+        self.activate()
+        self.plan()
+
+    def replace_parameters(self, raw, m, v):
+        """Swaps in a new Gaussian set (raw parameters, Adam moments; e.g. after adaptive
+        density control), re-activates it and re-plans the workspaces (synchronous).  The Adam
+        step count is kept."""
+        self.n = int(raw[0].shape[0])
+        self.raw = [t.contiguous() for t in raw]
+        self.act = [torch.empty_like(t) for t in self.raw]
+        self.grads = [torch.zeros_like(t) for t in self.raw]
+        self.m, self.v = m.contiguous(), v.contiguous()
         self.activate()
         self.plan()
 
@@ -112,7 +125,7 @@ class Reconstruction:
                                      B.ptr(self.loss), B.ptr(self.dimg), 1, B.ptr(self.ssim_ws),
                                      self.ssim_ws.numel(), s), "gs_ssim2d_loss")
         self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=False,
-                                reuse=not cfg.recompute_lists)
+                                reuse=not cfg.recompute_lists, stats=self.density_stats)
         if cfg.alpha_tv > 0:
             self.voxelizer.forward(*self.act, out=self.vol)
             dz, dy, dx = self.vol.shape

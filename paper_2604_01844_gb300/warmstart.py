@@ -18,7 +18,7 @@ import torch
 
 from . import binding as B
 from .fit import VolumeFit, fit_opts
-from .recon import psnr_of
+from .evaluate import VolumeScore, trajectory  # noqa: F401  (re-exported)
 
 
 def fit_prior(prior_vol: torch.Tensor, prior_grid, n: int, iters: int, uniforms: torch.Tensor,
@@ -34,69 +34,6 @@ def fit_prior(prior_vol: torch.Tensor, prior_grid, n: int, iters: int, uniforms:
     fit = VolumeFit(prior_grid, n, max_pairs=max_pairs, device=prior_vol.device)
     params = fit.run(prior_vol, iters, opts, uniforms.contiguous())
     return params, fit
-
-
-class VolumeScore:
-    """PSNR and 3D SSIM of a volume against a fixed ground truth, from the library's FP64 SSE
-    and its value-only 3D SSIM (both synchronise on the read-back)."""
-
-    def __init__(self, gt: torch.Tensor, peak: float | None = None):
-        self.gt = gt.contiguous()
-        self.peak = float(peak if peak is not None else float(gt.max()))
-        self.sse = torch.zeros(1, dtype=torch.float64, device=gt.device)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=gt.device)
-        self.ws = torch.empty(B.lib().gs_ssim3d_workspace_size(gt.numel()), dtype=torch.uint8,
-                              device=gt.device)
-
-    def psnr(self, vol: torch.Tensor) -> float:
-        return psnr_of(vol, self.gt, self.peak, self.sse)
-
-    def ssim(self, vol: torch.Tensor) -> float:
-        L = B.lib()
-        s = B.stream_handle()
-        dz, dy, dx = self.gt.shape
-        B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
-        B.check(L.gs_ssim3d_loss(B.ptr(vol), B.ptr(self.gt), dx, dy, dz, self.peak, 1.0,
-                                 B.ptr(self.loss), None, 0, B.ptr(self.ws), self.ws.numel(), s),
-                "gs_ssim3d_loss")
-        return 1.0 - float(self.loss.item())
-
-
-def trajectory(rec, score: VolumeScore, iters: int, eval_every: int = 5, ssim: bool = True,
-               graph: bool = False):
-    """Runs `iters` steps of rec (a recon.Reconstruction; graph = True replays the step as one
-    CUDA graph) and scores its voxelized volume at iteration 0 and every eval_every
-    iterations.  Returns ([(iteration, GPU ms of the steps so far, PSNR, SSIM or None)],
-    re-plans): at each evaluation point a pair-capacity overflow of the steps since the last
-    one is detected, and the workspaces are re-planned (and the graph captured again).  The
-    scoring itself is not timed."""
-    from .recon import GraphStep
-
-    step = GraphStep(rec, warmup=0) if graph else rec.step
-    vol = rec.voxelizer.forward(*rec.act)
-    out = [(0, 0.0, score.psnr(vol), score.ssim(vol) if ssim else None)]
-    ms = 0.0
-    it = 0
-    replans = 0
-    while it < iters:
-        k = min(eval_every, iters - it)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(k):
-            step()
-        e1.record()
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        it += k
-        if rec.projector.status().code != B.GS_OK or rec.voxelizer.status().code != B.GS_OK:
-            rec.plan()
-            replans += 1
-            if graph:
-                step = GraphStep(rec, warmup=0)
-        vol = rec.voxelizer.forward(*rec.act)
-        out.append((it, ms, score.psnr(vol), score.ssim(vol) if ssim else None))
-    return out, replans
 
 
 def tau_iter(cold, warm, n_iter: int, col: int):
