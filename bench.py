@@ -295,6 +295,7 @@ def run_ours(args, ws, rank, local):
         out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
         out["scale_up"] = scale_up(device)
         out["warm_start"] = warm_start_study(device, side=args.warm_side, det=args.warm_det)
+        out["adaptive_control"] = adaptive_control(device)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -627,6 +628,84 @@ def warm_start_study(device, side=512, det=1024, n_views=50, n=100000, fit_iters
             "tau_iter_ssim": tau_iter(cold, warm, n_iter, 3),
             "note": "tau_iter = first evaluated warm iteration reaching the cold start's best "
                     "within n_iter, / n_iter; trajectories evaluated every eval_every iterations"}
+
+
+def adaptive_control(device, n0=25000, budget=50000, iters=400, eval_every=50,
+                     grad_threshold=7e-5):
+    """Adaptive density control (prune / clone / split) on the 40-ellipsoid phantom, 75 cone
+    views of 512^2, 256^3: n0 Gaussians from the FDK-gradient initialiser, densified every 100
+    iterations from iteration 100 to 300 up to `budget`, against the same start kept at n0.
+    Reports both PSNR trajectories, the events' counts and the gs_densify time at the budget."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300 import binding as B
+    from paper_2604_01844_gb300.density import DensifyConfig, DensityControl
+    from paper_2604_01844_gb300.evaluate import VolumeScore, trajectory
+    from paper_2604_01844_gb300.recon import (PhantomProblem, ReconConfig, Reconstruction,
+                                               fdk_volume, gradient_init)
+
+    views = synth.cone_views(75, 512, 512)
+    grid = synth.cube_grid(256)
+    prob = PhantomProblem(synth.ellipsoid_phantom(1, 40), views, 512, 512, grid, device=device)
+    fdk = fdk_volume(prob, grid)
+    score = VolumeScore(prob.gt, prob.peak)
+    u = np.random.default_rng(7).random((n0, 4)).astype(np.float32)
+    start = [t.cpu().numpy() for t in gradient_init(fdk, grid, n0, u)]
+    cfg = DensifyConfig(start=100, interval=100, stop=301, max_gaussians=budget,
+                        grad_threshold=grad_threshold)
+    out = {}
+    for name, dens in (("fixed", None), ("densified", cfg)):
+        rec = Reconstruction(views, 512, 512, prob.proj, grid, *start,
+                             cfg=ReconConfig(**LR_FAST), device=device)
+        ctrl = DensityControl(rec, dens) if dens else None
+        traj, _ = trajectory(rec, score, iters, eval_every, ssim=False, graph=True,
+                             control=ctrl)
+        out[name] = {"psnr_db_every_%d" % eval_every: [round(r[2], 2) for r in traj],
+                     "ms": round(traj[-1][1], 1), "gaussians_final": rec.n}
+        if ctrl:
+            out[name]["events"] = ctrl.history
+            # gs_densify alone on the final set (statistics of one more window), CUDA events
+            for _ in range(3):
+                rec.step()
+            n = rec.n
+            normals = torch.randn(n, 6, device=device)
+            o = ctrl.opts
+            cap = 2 * n
+            bufs = [torch.empty((cap, 4), device=device) for _ in range(3)]
+            om = torch.empty((3 * cap, 4), device=device)
+            ov = torch.empty_like(om)
+            ws = torch.empty(B.lib().gs_densify_workspace_size(n), dtype=torch.uint8,
+                             device=device)
+
+            def call():
+                B.check(B.lib().gs_densify(
+                    *[B.ptr(t) for t in rec.raw], B.ptr(rec.m), B.ptr(rec.v), B.ptr(ctrl.stat),
+                    B.ptr(ctrl.vis), B.ptr(normals), n, ctypes.byref(o),
+                    *[B.ptr(t) for t in bufs], B.ptr(om), B.ptr(ov), cap, B.ptr(ws), ws.numel(),
+                    B.stream_handle()), "gs_densify")
+            for _ in range(3):
+                call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                call()
+            e1.record()
+            e1.synchronize()
+            out[name]["densify_call_ms"] = round(e0.elapsed_time(e1) / 20, 4)
+        del rec, ctrl
+        torch.cuda.empty_cache()
+    out.update({"workload": f"40-ellipsoid phantom, 75 cone views x 512^2, 256^3; {n0} Gaussians "
+                            f"(FDK-gradient init), densified up to {budget}",
+                "rules": {"grad_threshold": grad_threshold, "split_scale": cfg.split_scale,
+                          "split_factor": cfg.split_factor, "min_density": cfg.min_density,
+                          "max_scale": cfg.max_scale, "schedule": "iterations 100, 200, 300"},
+                "note": "PSNR evaluated right after each densification event (iterations 100, "
+                        "200, 300) shows the event's immediate effect"})
+    return out
 
 
 def scale_up(device, steps=5, warmup=3):

@@ -410,9 +410,10 @@ int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, f
  *           standard normal draws d_normals[6i + 3k .. 6i + 3k + 2]), log-scales
  *           max(log s - log split_factor, min_log_scale), density rho split_factor^3 / 2
  *           (the pair keeps the parent's integrated density rho (2 pi)^(3/2) sx sy sz), zero
- *           Adam moments;
+ *           Adam moments (the parent's with inherit_moments = 1);
  *     clone otherwise: two copies with density rho / 2 (together they render as the parent);
- *           the first keeps the Adam moments, the second starts from zero moments;
+ *           the first keeps the Adam moments, the second starts from zero moments (from the
+ *           parent's with inherit_moments = 1);
  *   else keep.
  * Budget: when the densify candidates do not all fit under max_gaussians (counting the
  * Gaussians that stay), only the max_gaussians - (n - pruned) candidates with the highest
@@ -428,6 +429,9 @@ typedef struct gs_densify_opts {
   float max_scale;       /* prune above this largest scale */
   float min_log_scale;   /* lower clamp of the children's raw log-scales */
   int32_t max_gaussians; /* budget of Gaussians after densification (>= 0) */
+  int32_t inherit_moments; /* 1: every child starts from its parent's Adam moments instead of
+                              the zero moments described above */
+  int32_t pad[3];
 } gs_densify_opts;
 
 /* Workspace bytes of gs_densify for n Gaussians. */

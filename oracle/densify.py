@@ -21,6 +21,8 @@ builds on (Kerbl et al. 2023, via R2-Gaussian), restated for additive X-ray rend
   s / split_factor (log-scale clamped below at min_log_scale), and the density that conserves
   the integrated density rho (2 pi)^(3/2) s_x s_y s_z of the parent:
   rho' = rho split_factor^3 / 2.  Zero Adam moments.
+* Option inherit_moments: every child (both clones, both split children) starts from its
+  parent's Adam moments instead.
 * Output order: Gaussian order, a densified Gaussian's two children consecutive.
 
 Decisions (comparisons with the thresholds, the budget ranking) are taken in FP32, the
@@ -111,6 +113,7 @@ def densify(raw_mr, raw_sc, raw_q, m, v, stat, vis, normals, opts):
     Returns (out_raw_mr, out_raw_sc, out_raw_q, out_m, out_v, act, candidates)."""
     act, _, cands = classify(raw_mr, raw_sc, stat, vis, opts)
     phi = float(opts["split_factor"])
+    inherit = bool(opts.get("inherit_moments", 0))
     outs = [[] for _ in range(5)]
 
     def put(a, b, c, mm, vv):
@@ -130,7 +133,7 @@ def densify(raw_mr, raw_sc, raw_q, m, v, stat, vis, normals, opts):
             half = a.copy()
             half[3] = inverse_softplus(0.5 * rho)
             put(half, b, c, m[i], v[i])
-            put(half, b, c, zero, zero)
+            put(half, b, c, *((m[i], v[i]) if inherit else (zero, zero)))
             continue
         qn = np.asarray(c, dtype=np.float64)
         qn = qn / np.linalg.norm(qn)
@@ -145,7 +148,7 @@ def densify(raw_mr, raw_sc, raw_q, m, v, stat, vis, normals, opts):
             child = a.copy()
             child[:3] = a[:3] + R @ (s * normals[i, 3 * k:3 * k + 3])
             child[3] = inverse_softplus(rho * phi ** 3 / 2.0)
-            put(child, child_sc, c, zero, zero)
+            put(child, child_sc, c, *((m[i], v[i]) if inherit else (zero, zero)))
     shapes = [(0, 4), (0, 4), (0, 4), (0, 3, 4), (0, 3, 4)]
     res = [np.stack(o) if o else np.zeros(sh) for o, sh in zip(outs, shapes)]
     return (*res, act, cands)

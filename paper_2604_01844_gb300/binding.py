@@ -71,7 +71,8 @@ class GsDensifyOpts(ctypes.Structure):
     _fields_ = [("grad_threshold", ctypes.c_float), ("grad_scale", ctypes.c_float),
                 ("split_scale", ctypes.c_float), ("split_factor", ctypes.c_float),
                 ("min_density", ctypes.c_float), ("max_scale", ctypes.c_float),
-                ("min_log_scale", ctypes.c_float), ("max_gaussians", ctypes.c_int32)]
+                ("min_log_scale", ctypes.c_float), ("max_gaussians", ctypes.c_int32),
+                ("inherit_moments", ctypes.c_int32), ("pad", ctypes.c_int32 * 3)]
 
 
 MAX_INSTANCES = 32
@@ -79,7 +80,7 @@ MAX_INSTANCES = 32
 assert ctypes.sizeof(GsGrid) == 36 and ctypes.sizeof(GsOpts) == 32
 assert ctypes.sizeof(GsInstance) == 16 and ctypes.sizeof(GsVoxelInstance) == 64
 assert ctypes.sizeof(GsAdamOpts) == 48
-assert ctypes.sizeof(GsDensifyOpts) == 32
+assert ctypes.sizeof(GsDensifyOpts) == 48
 assert ctypes.sizeof(GsStatus) == 256
 
 _lib = None

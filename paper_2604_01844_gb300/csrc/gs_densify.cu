@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kDT)
     out_q[j] = pq;
     out_q[j + 1] = pq;
     put(out_m, out_v, j, m, v, i, true);
-    put(out_m, out_v, j + 1, m, v, i, false);
+    put(out_m, out_v, j + 1, m, v, i, o.inherit_moments != 0);
     return;
   }
   // split: children at p + R diag(s) z_k, scales / phi, density conserving the integral
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kDT)
     out_mr[j + k] = cm;
     out_sc[j + k] = csc;
     out_q[j + k] = pq;
-    put(out_m, out_v, j + k, m, v, i, false);
+    put(out_m, out_v, j + k, m, v, i, o.inherit_moments != 0);
   }
 }
 

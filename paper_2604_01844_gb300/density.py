@@ -31,6 +31,7 @@ class DensifyConfig:
     stop: int = 10 ** 9            # no densification at or after this iteration
     interval: int = 100            # iterations per statistics window
     seed: int = 0                  # seed of the split children's normal draws
+    inherit_moments: bool = False  # children start from the parent's Adam moments
 
 
 def opts_struct(cfg: DensifyConfig, views_per_step: int, min_log_scale: float) -> B.GsDensifyOpts:
@@ -39,6 +40,7 @@ def opts_struct(cfg: DensifyConfig, views_per_step: int, min_log_scale: float) -
     o.split_scale, o.split_factor = cfg.split_scale, cfg.split_factor
     o.min_density, o.max_scale = cfg.min_density, cfg.max_scale
     o.min_log_scale, o.max_gaussians = min_log_scale, int(cfg.max_gaussians)
+    o.inherit_moments = 1 if cfg.inherit_moments else 0
     return o
 
 

@@ -146,11 +146,12 @@ def _compare(got, k, want):
                                atol=1e-9)
 
 
-@pytest.mark.parametrize("budget", [None, "binding", "zero"])
-def test_densify_matches_oracle(gsct, budget):
+@pytest.mark.parametrize("budget,inherit", [(None, 0), ("binding", 0), ("zero", 0),
+                                             (None, 1), ("binding", 1)])
+def test_densify_matches_oracle(gsct, budget, inherit):
     n = 3000
     state = _random_state(50, n)
-    o = dict(OPTS)
+    o = dict(OPTS, inherit_moments=inherit)
     act0, _, cands0 = OD.classify(state[0], state[1], state[5], state[6], o)
     kept = n - int((act0 == OD.PRUNE).sum())
     if budget == "binding":

@@ -167,3 +167,25 @@ def test_everything_pruned_and_empty():
     e = D.densify(raw_mr[:0], raw_sc[:0], raw_q[:0], np.zeros((0, 3, 4)), np.zeros((0, 3, 4)),
                   np.zeros(0, np.float32), np.zeros(0), np.zeros((0, 6)), OPTS)
     assert e[0].shape == (0, 4)
+
+
+def test_inherit_moments_copies_the_parent_moments_to_every_child():
+    n = 30
+    raw_mr, raw_sc, raw_q = _raw(n, 13)
+    m = np.random.default_rng(5).random((n, 3, 4))
+    v = np.random.default_rng(6).random((n, 3, 4))
+    normals = np.random.default_rng(7).standard_normal((n, 6))
+    for split_scale, kind in ((0.0, D.SPLIT), (10.0, D.CLONE)):
+        o = dict(OPTS, split_scale=split_scale, max_scale=10.0, min_density=0.0,
+                 inherit_moments=1)
+        out = D.densify(raw_mr, raw_sc, raw_q, m, v, np.ones(n, np.float32), np.ones(n),
+                        normals, o)
+        assert np.all(out[5] == kind)
+        for k in (0, 1):
+            np.testing.assert_array_equal(out[3][k::2], m)
+            np.testing.assert_array_equal(out[4][k::2], v)
+        # the parameters do not depend on the moment rule
+        base = D.densify(raw_mr, raw_sc, raw_q, m, v, np.ones(n, np.float32), np.ones(n),
+                         normals, dict(o, inherit_moments=0))
+        for a, b in zip(out[:3], base[:3]):
+            np.testing.assert_array_equal(a, b)
