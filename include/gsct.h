@@ -272,6 +272,42 @@ int gs_voxelize_count_evals(const float* d_mean_rho, const float* d_scale, const
                             size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * FP16 Gaussian codec and on-demand voxelization (the paper's volume fitting and compression
+ * study: the 11 parameters of a Gaussian stored as IEEE binary16, 22 bytes per Gaussian,
+ * voxelized when a volume is needed).
+ *
+ * Codec layout: 11 planes of n binary16 values, plane k = parameter k of every Gaussian in the
+ * order x, y, z, sx, sy, sz, qw, qx, qy, qz, rho (22 n bytes, 2-byte aligned).  Encoding
+ * rounds to nearest, ties to even (values beyond +-65504 become +-inf); decoding is exact.
+ * ------------------------------------------------------------------------------------- */
+#define GS_CODEC_RECORD_BYTES 22
+
+/* d_out (22 n bytes) = the codec of the activated parameters (scale's 4th component is not
+ * stored). */
+int gs_encode_fp16(const float* d_mean_rho, const float* d_scale, const float* d_quat, int n,
+                   void* d_out, void* stream);
+/* Activated parameters from a codec (scale's 4th component set to 0). */
+int gs_decode_fp16(const void* d_in, int n, float* d_mean_rho, float* d_scale, float* d_quat,
+                   void* stream);
+
+/* Workspace of gs_voxelize_fp16: the voxelizer's (for max_pairs pairs) plus room for the
+ * decoded parameters. */
+size_t gs_voxelize_fp16_workspace_size(int n, const gs_grid* grid, const int32_t roi_lo[3],
+                                       const int32_t roi_dim[3], const gs_opts* opts,
+                                       int64_t max_pairs);
+/* gs_voxelize of the Gaussians of a codec: decodes them into the end of the workspace, then
+ * voxelizes; the pair capacity is what the rest of the workspace holds.  The status block at
+ * the start of d_ws is the voxelizer's. */
+int gs_voxelize_fp16(const void* d_codec, int n, const gs_grid* grid, const int32_t roi_lo[3],
+                     const int32_t roi_dim[3], const gs_opts* opts, float* d_vol, void* d_ws,
+                     size_t ws_bytes, void* stream);
+/* gs_voxelize_count_pairs of the Gaussians of a codec (SYNCHRONOUS). */
+int gs_voxelize_fp16_count_pairs(const void* d_codec, int n, const gs_grid* grid,
+                                 const int32_t roi_lo[3], const int32_t roi_dim[3],
+                                 const gs_opts* opts, void* d_ws, size_t ws_bytes, void* stream,
+                                 int64_t* h_pairs);
+
+/* ---------------------------------------------------------------------------------------
  * Batched voxelizer: up to GS_MAX_INSTANCES independent volumes (each with its own Gaussians,
  * grid and region of interest) voxelized with one kernel launch per pass.  The single-volume
  * calls above are this with one instance.  Not described in the paper (one volume at a time);

@@ -23,8 +23,9 @@ def planes_of(mean_rho, scale, quat) -> np.ndarray:
 
 
 def encode(mean_rho, scale, quat) -> np.ndarray:
-    """(11, n) uint16 binary16 bit patterns."""
-    return planes_of(mean_rho, scale, quat).astype(np.float16).view(np.uint16)
+    """(11, n) uint16 binary16 bit patterns (values beyond the binary16 range become inf)."""
+    with np.errstate(over="ignore"):
+        return planes_of(mean_rho, scale, quat).astype(np.float16).view(np.uint16)
 
 
 def decode(bits: np.ndarray):

@@ -123,6 +123,12 @@ SIGNATURES = {
     "gs_voxelize_backward": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _P, _P, _P, _I,
                                   _I, _P, _SZ, _P]),
     "gs_voxelize_count_evals": (_I, [_P, _P, _P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P]),
+    "gs_encode_fp16": (_I, [_P, _P, _P, _I, _P, _P]),
+    "gs_decode_fp16": (_I, [_P, _I, _P, _P, _P, _P]),
+    "gs_voxelize_fp16_workspace_size": (_SZ, [_I, _GRID, _I3, _I3, _OPTS, _I64]),
+    "gs_voxelize_fp16": (_I, [_P, _I, _GRID, _I3, _I3, _OPTS, _P, _P, _SZ, _P]),
+    "gs_voxelize_fp16_count_pairs": (_I, [_P, _I, _GRID, _I3, _I3, _OPTS, _P, _SZ, _P,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "gs_voxelize_batch_workspace_size": (_SZ, [_VINST, _I, _OPTS, _I64]),
     "gs_voxelize_batch_count_pairs": (_I, [_P, _P, _P, _VINST, _I, _OPTS, _P, _SZ, _P,
                                            ctypes.POINTER(ctypes.c_int64)]),
