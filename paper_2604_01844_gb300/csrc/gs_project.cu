@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT)
                  const gs_status* st) {
   using S = BwdBlocks<T>;
   constexpr int BW = S::BW;
-  __shared__ float s_g[T][T + 1];
+  __shared__ __align__(16) float s_g[T][T];
   __shared__ float4 s_geo[S::NT];
   __shared__ float4 s_con[S::NT];
   __shared__ uint32_t s_rec[S::NT];
@@ -644,33 +644,40 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT)
         const float4 g = s_geo[j];
         const float4 c = s_con[j];
         const float cut = active ? g.w : 1.f;  // e <= 0 < 1: an idle lane never passes
-        float dx[BW];
+        // pixel pairs (q, q + 1) of a row in packed FP32x2 arithmetic: each component rounds
+        // like the scalar fmaf / add / mul, so e and the cut are exactly the forward's
+        float2 dx[BW / 2];
 #pragma unroll
-        for (int q = 0; q < BW; ++q) dx[q] = (float)(tx0 + bxl + q) - g.x;
+        for (int p = 0; p < BW / 2; ++p)
+          dx[p] = make_float2((float)(tx0 + bxl + 2 * p) - g.x, (float)(tx0 + bxl + 2 * p + 1) - g.x);
+        const float2 ca = make_float2(c.x, c.x);
         float s0 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
         for (int ry = 0; ry < 4; ++ry) {
           const float dy = (float)(ty0 + byl + ry) - g.y;
           const float B = row_b(c, dy), cdy2 = row_c(c, dy);
-          const float* grow = &s_g[byl + ry][bxl];
-          float r0 = 0.f, rx = 0.f, rxx = 0.f;
+          const float2 B2 = make_float2(B, B), C2 = make_float2(cdy2, cdy2);
+          const float4* grow = reinterpret_cast<const float4*>(&s_g[byl + ry][bxl]);
+          float2 r0 = make_float2(0.f, 0.f), rx = r0, rxx = r0;
 #pragma unroll
-          for (int q = 0; q < BW; ++q) {
-            const float e = expo(c, dx[q], B, cdy2);
-            if (e > cut) {
-              const float G = grow[q] * ex2(e);
-              const float Gx = G * dx[q];
-              r0 += G;
-              rx += Gx;
-              rxx = fmaf(Gx, dx[q], rxx);
-            }
+          for (int p = 0; p < BW / 2; ++p) {
+            const float2 e = __ffma2_rn(__ffma2_rn(ca, dx[p], B2), dx[p], C2);
+            const float4 g4 = grow[p >> 1];
+            const float2 gg = (p & 1) ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
+            const float2 val = make_float2(e.x > cut ? ex2(e.x) : 0.f, e.y > cut ? ex2(e.y) : 0.f);
+            const float2 G = __fmul2_rn(gg, val);
+            const float2 Gx = __fmul2_rn(G, dx[p]);
+            r0 = __fadd2_rn(r0, G);
+            rx = __fadd2_rn(rx, Gx);
+            rxx = __ffma2_rn(Gx, dx[p], rxx);
           }
-          s0 += r0;
-          sx += rx;
-          sxx += rxx;
-          sy = fmaf(dy, r0, sy);
-          sxy = fmaf(dy, rx, sxy);
-          syy = fmaf(dy * dy, r0, syy);
+          const float r0s = r0.x + r0.y, rxs = rx.x + rx.y;
+          s0 += r0s;
+          sx += rxs;
+          sxx += rxx.x + rxx.y;
+          sy = fmaf(dy, r0s, sy);
+          sxy = fmaf(dy, rxs, sxy);
+          syy = fmaf(dy * dy, r0s, syy);
         }
         if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
           atomicAdd(&s_acc[0][j], s0);
