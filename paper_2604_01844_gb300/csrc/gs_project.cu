@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(RasterShape<T>::NT, 2048 / RasterShape<T>::NT)
 // per record adds them to the record's moments (two float4 atomics).
 // ------------------------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(BwdBlocks<T>::NT)
+__global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBlocks<T>::NT)
     k_raster_bwd(const __grid_constant__ Batch b, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ vals, const float4* __restrict__ geo,
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
