@@ -289,14 +289,22 @@ def run_ours(args, ws, rank, local):
         "loss": loss,
     }
     if not args.no_extras:
-        out["time_to_psnr"] = time_to_psnr(device)
-        out["learned_init"] = learned_vs_plain(device)
-        out["batched"] = batched_learned_vs_plain(device)
-        out["fit_volume"] = fit_volume_rate(device, args.fit_side, args.fit_gaussians)
-        out["scale_up"] = scale_up(device)
-        out["warm_start"] = warm_start_study(device, side=args.warm_side, det=args.warm_det)
-        out["adaptive_control"] = adaptive_control(device)
-        out["compression"] = compression(device)
+        legs = {
+            "time_to_psnr": lambda: time_to_psnr(device),
+            "learned_init": lambda: learned_vs_plain(device),
+            "batched": lambda: batched_learned_vs_plain(device),
+            "fit_volume": lambda: fit_volume_rate(device, args.fit_side, args.fit_gaussians),
+            "scale_up": lambda: scale_up(device),
+            "warm_start": lambda: warm_start_study(device, side=args.warm_side,
+                                                   det=args.warm_det),
+            "adaptive_control": lambda: adaptive_control(device),
+            "compression": lambda: compression(device),
+        }
+        chosen = list(legs) if args.extras == "all" else args.extras.split(",")
+        for name in chosen:
+            if name not in legs:
+                raise SystemExit(f"unknown extra leg {name!r}; choose from {', '.join(legs)}")
+            out[name] = legs[name]()
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views, target_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -980,6 +988,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the time-to-PSNR and volume-fit measurements")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated study legs to run after the headline step "
+                         "(time_to_psnr, learned_init, batched, fit_volume, scale_up, "
+                         "warm_start, adaptive_control, compression) or 'all'")
     ap.add_argument("--fit-side", type=int, default=1024)
     ap.add_argument("--fit-gaussians", type=int, default=500000)
     ap.add_argument("--warm-side", type=int, default=512)
