@@ -113,237 +113,18 @@ __global__ void __launch_bounds__(kThreads)
 // ------------------------------------------------------------------------------------------
 constexpr int kR = 5;            // window radius (11 taps)
 
-__device__ __forceinline__ void window_weights(float* w) {
-  // normalised 11-tap Gaussian, sigma 1.5
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    float s = 0.f;
-    for (int k = 0; k < 2 * kR + 1; ++k) {
-      const float d = (float)(k - kR);
-      w[k] = expf(-d * d / (2.f * 1.5f * 1.5f));
-      s += w[k];
-    }
-    for (int k = 0; k < 2 * kR + 1; ++k) w[k] /= s;
-  }
-}
-
-// Both SSIM 2D kernels work on 32 x 32 output tiles with a 5-pixel halo staged in shared
-// memory and register blocking in the two separable passes: the horizontal pass gives each
-// thread 4 adjacent outputs of one row (14 staged inputs serve all 4), the vertical pass 4
-// adjacent outputs of one column (14 filtered rows serve all 4).
+// The SSIM kernels filter 32 x 32 output tiles (plus a 5-pixel halo staged in shared memory)
+// in two separable passes with register blocking: the horizontal pass gives each thread 4
+// adjacent outputs of one row (14 staged inputs serve all 4), the vertical pass 4 adjacent
+// outputs of one column.  Channels travel in pairs through packed FP32x2 arithmetic (one
+// instruction filters two channels; each component rounds like the scalar fmaf), with a
+// single channel for an odd count.
 constexpr int kT2 = 32;              // output tile side
 constexpr int kIn2 = kT2 + 2 * kR;   // 42
 constexpr int kG = 4;                // outputs per thread in each pass
 constexpr int kSsimThreads = 256;
 static_assert(kT2 * (kT2 / kG) == kSsimThreads, "vertical pass: one thread per 4-row group");
-
-// Stages the (kIn2 x kIn2) halo tile at (x0, y0) of NC channels (channel m at src[m] + m_off *
-// m, element (x, y) at + y * nx + x) into shared memory, zero outside [0, nx) x [0, ny).  All
-// of a thread's loads are issued before the first shared-memory store, so the tile costs one
-// memory round trip instead of one per row of threads.
 constexpr int kStageIters = (kIn2 * kIn2 + kSsimThreads - 1) / kSsimThreads;
-template <int NC>
-__device__ __forceinline__ void stage_halo(const float* const (&src)[NC], int x0, int y0,
-                                           int nx, int ny, float (*dst)[kIn2][kIn2 + 1]) {
-  float v[kStageIters][NC];
-#pragma unroll
-  for (int it = 0; it < kStageIters; ++it) {
-    const int p = threadIdx.x + it * kSsimThreads;
-    const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
-    const bool ok = p < kIn2 * kIn2 && x >= 0 && x < nx && y >= 0 && y < ny;
-    const size_t o = (size_t)y * nx + x;
-#pragma unroll
-    for (int m = 0; m < NC; ++m) v[it][m] = ok ? src[m][o] : 0.f;
-  }
-#pragma unroll
-  for (int it = 0; it < kStageIters; ++it) {
-    const int p = threadIdx.x + it * kSsimThreads;
-    if (p < kIn2 * kIn2) {
-      const int r = p / kIn2, c = p % kIn2;
-#pragma unroll
-      for (int m = 0; m < NC; ++m) dst[m][r][c] = v[it][m];
-    }
-  }
-}
-
-__device__ __forceinline__ void window_regs(const float* w, float wr[2 * kR + 1]) {
-#pragma unroll
-  for (int k = 0; k <= 2 * kR; ++k) wr[k] = w[k];
-}
-
-// Kernel 1: moments, SSIM, and the maps m1 = dS/dmu_x - 2 mu_x dS/dsxx - mu_y dS/dsxy,
-// m2 = dS/dsxx, m3 = dS/dsxy, all multiplied by -weight / N (the loss is weight * (1 - SSIM)).
-__global__ void __launch_bounds__(kSsimThreads)
-    k_ssim2d_fwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W, float C1,
-                 float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
-                 int64_t plane) {
-  __shared__ float w[2 * kR + 1];
-  __shared__ float sxy_[2][kIn2][kIn2 + 1];
-  __shared__ float hm[5][kIn2][kT2 + 1];
-  float (*sx)[kIn2 + 1] = sxy_[0];
-  float (*sy)[kIn2 + 1] = sxy_[1];
-  window_weights(w);
-  const int img = blockIdx.z;
-  const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
-  const float* Xi = X + (size_t)img * H * W;
-  const float* Yi = Y + (size_t)img * H * W;
-  const int tid = threadIdx.x;
-  {
-    const float* const src[2] = {Xi, Yi};
-    stage_halo<2>(src, x0, y0, W, H, sxy_);
-  }
-  __syncthreads();
-  float wr[2 * kR + 1];
-  window_regs(w, wr);
-  // horizontal pass: kIn2 rows x (kT2 / kG) groups of kG outputs
-  for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
-    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
-    float acc[5][kG];
-#pragma unroll
-    for (int m = 0; m < 5; ++m)
-#pragma unroll
-      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
-#pragma unroll
-    for (int i = 0; i < kG + 2 * kR; ++i) {
-      const float u = sx[r][c0 + i], v = sy[r][c0 + i];
-      const float uu = u * u, vv = v * v, uv = u * v;
-#pragma unroll
-      for (int j = 0; j < kG; ++j) {
-        const int k = i - j;
-        if (k < 0 || k > 2 * kR) continue;
-        acc[0][j] = fmaf(wr[k], u, acc[0][j]);
-        acc[1][j] = fmaf(wr[k], v, acc[1][j]);
-        acc[2][j] = fmaf(wr[k], uu, acc[2][j]);
-        acc[3][j] = fmaf(wr[k], vv, acc[3][j]);
-        acc[4][j] = fmaf(wr[k], uv, acc[4][j]);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m)
-#pragma unroll
-      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
-  }
-  __syncthreads();
-  // vertical pass: column tx, rows ty0 .. ty0 + kG - 1
-  const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
-  float mo[5][kG];
-#pragma unroll
-  for (int m = 0; m < 5; ++m)
-#pragma unroll
-    for (int j = 0; j < kG; ++j) mo[m][j] = 0.f;
-#pragma unroll
-  for (int i = 0; i < kG + 2 * kR; ++i) {
-    float h[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) h[m] = hm[m][ty0 + i][tx];
-#pragma unroll
-    for (int j = 0; j < kG; ++j) {
-      const int k = i - j;
-      if (k < 0 || k > 2 * kR) continue;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) mo[m][j] = fmaf(wr[k], h[m], mo[m][j]);
-    }
-  }
-  const int x = blockIdx.x * kT2 + tx;
-  float contrib = 0.f;
-#pragma unroll
-  for (int j = 0; j < kG; ++j) {
-    const int y = blockIdx.y * kT2 + ty0 + j;
-    const float mx = mo[0][j], my = mo[1][j];
-    const float sxx = mo[2][j] - mx * mx, syy = mo[3][j] - my * my, sxy = mo[4][j] - mx * my;
-    const float A = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
-    const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
-    const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
-    const float S = (A * Bn) * inv;
-    if (x < W && y < H) {
-      const float dmu = (2.f * my * Bn) * inv - S * (2.f * mx) * (D * inv);
-      const float dsxx = -S * (C * inv);
-      const float dsxy = 2.f * A * inv;
-      const size_t o = (size_t)img * H * W + (size_t)y * W + x;
-      maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
-      maps[plane + o] = gscale * dsxx;
-      maps[2 * plane + o] = gscale * dsxy;
-      contrib += 1.f - S;
-    }
-  }
-  if (loss) block_add(contrib * (-gscale), loss);
-}
-
-// Kernel 2: dL/dx = w * m1 + 2 x (w * m2) + y (w * m3).
-__global__ void __launch_bounds__(kSsimThreads)
-    k_ssim2d_bwd(const float* __restrict__ X, const float* __restrict__ Y, int H, int W,
-                 const float* __restrict__ maps, int64_t plane, float* __restrict__ grad,
-                 int accumulate) {
-  __shared__ float w[2 * kR + 1];
-  __shared__ float sm[3][kIn2][kIn2 + 1];
-  __shared__ float hm[3][kIn2][kT2 + 1];
-  window_weights(w);
-  const int img = blockIdx.z;
-  const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
-  const int tid = threadIdx.x;
-  const size_t base = (size_t)img * H * W;
-  {
-    const float* const src[3] = {maps + base, maps + plane + base, maps + 2 * plane + base};
-    stage_halo<3>(src, x0, y0, W, H, sm);
-  }
-  __syncthreads();
-  float wr[2 * kR + 1];
-  window_regs(w, wr);
-  for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
-    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
-    float acc[3][kG];
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
-#pragma unroll
-    for (int i = 0; i < kG + 2 * kR; ++i) {
-      float u[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) u[m] = sm[m][r][c0 + i];
-#pragma unroll
-      for (int j = 0; j < kG; ++j) {
-        const int k = i - j;
-        if (k < 0 || k > 2 * kR) continue;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) acc[m][j] = fmaf(wr[k], u[m], acc[m][j]);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
-  }
-  __syncthreads();
-  const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
-  float f[3][kG];
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int j = 0; j < kG; ++j) f[m][j] = 0.f;
-#pragma unroll
-  for (int i = 0; i < kG + 2 * kR; ++i) {
-    float h[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) h[m] = hm[m][ty0 + i][tx];
-#pragma unroll
-    for (int j = 0; j < kG; ++j) {
-      const int k = i - j;
-      if (k < 0 || k > 2 * kR) continue;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) f[m][j] = fmaf(wr[k], h[m], f[m][j]);
-    }
-  }
-  const int x = blockIdx.x * kT2 + tx;
-  if (x >= W) return;
-#pragma unroll
-  for (int j = 0; j < kG; ++j) {
-    const int y = blockIdx.y * kT2 + ty0 + j;
-    if (y >= H) continue;
-    const size_t o = base + (size_t)y * W + x;
-    const float g = f[0][j] + 2.f * X[o] * f[1][j] + Y[o] * f[2][j];
-    grad[o] = accumulate ? grad[o] + g : g;
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // SSIM 3D, separable in two passes over the volume:
@@ -375,24 +156,41 @@ Win host_window() {
   return W;
 }
 
-template <int NIN>  // 2: (X, Y) -> 5 moments; 3: maps -> 3 filtered maps
+// Intermediate buffers of the SSIM kernels hold their channels in pairs: a buffer of NP pairs
+// and NS singles over n elements is NP float2 arrays of n followed by NS float arrays of n
+// (maps: (m1, m2) + m3; z-filtered forward moments: (mu_x, mu_y), (xx, yy) + xy).
+__device__ __forceinline__ float2 pair_at(const float* base, int64_t n, int m, int64_t o) {
+  return reinterpret_cast<const float2*>(base)[m * n + o];
+}
+
+template <int NIN>  // 2: (X, Y) -> 5 moments; 3: maps (pair layout) -> 3 filtered maps
 __global__ void __launch_bounds__(kThreads)
     k_ssim3d_z(const __grid_constant__ Win W, const float* __restrict__ A0,
-               const float* __restrict__ A1, const float* __restrict__ A2, int nx, int ny, int nz,
-               int64_t plane, float* __restrict__ out) {
+               const float* __restrict__ A1, int nx, int ny, int nz, int64_t plane,
+               float* __restrict__ out) {
   constexpr int NOUT = NIN == 2 ? 5 : 3;
   const int64_t sxy = (int64_t)nx * ny;
   const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (col >= sxy) return;
-  const float* in[3] = {A0, A1, A2};
+  // element o of input i: X / Y, or the maps' pair (i = 0, 1) and single (i = 2)
+  auto load = [&](int64_t o, float (&v)[NIN]) {
+    if (NIN == 2) {
+      v[0] = A0[o];
+      v[1] = A1[o];
+    } else {
+      const float2 p = pair_at(A0, plane, 0, o);
+      v[0] = p.x;
+      v[1] = p.y;
+      v[NIN - 1] = A0[2 * plane + o];
+    }
+  };
   float ring[2 * kR + 1][NIN];
 #pragma unroll
   for (int k = 0; k <= 2 * kR; ++k)
 #pragma unroll
     for (int i = 0; i < NIN; ++i) ring[k][i] = 0.f;
   float nxt[NIN];
-#pragma unroll
-  for (int i = 0; i < NIN; ++i) nxt[i] = in[i][col];
+  load(col, nxt);
   // plane zi enters ring slot zi % 11; output z = zi - kR is complete once plane zi is in
   for (int zb = 0; zb < nz + kR; zb += 2 * kR + 1) {
 #pragma unroll
@@ -401,8 +199,24 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int i = 0; i < NIN; ++i) ring[k][i] = nxt[i];
       const int zn = zi + 1;
+      if (zn < nz) {
+        load((int64_t)zn * sxy + col, nxt);
+      } else {
 #pragma unroll
-      for (int i = 0; i < NIN; ++i) nxt[i] = zn < nz ? in[i][(int64_t)zn * sxy + col] : 0.f;
+        for (int i = 0; i < NIN; ++i) nxt[i] = 0.f;
+      }
+      // the column's element 4 planes ahead is requested into L2 now, so that the load of the
+      // next plane rarely waits for DRAM
+      if (zi + 4 < nz) {
+        const int64_t o4 = (int64_t)(zi + 4) * sxy + col;
+        if (NIN == 2) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A0 + o4));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A1 + o4));
+        } else {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A0 + 2 * o4));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A0 + 2 * plane + o4));
+        }
+      }
       const int z = zi - kR;
       if (z < 0 || z >= nz) continue;
       float acc[NOUT];
@@ -425,113 +239,213 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       const int64_t o = (int64_t)z * sxy + col;
-#pragma unroll
-      for (int m = 0; m < NOUT; ++m) out[m * plane + o] = acc[m];
+      float2* out2 = reinterpret_cast<float2*>(out);
+      out2[o] = make_float2(acc[0], acc[1]);
+      if (NOUT == 5) out2[plane + o] = make_float2(acc[2], acc[3]);
+      out[2 * (NOUT / 2) * plane + o] = acc[NOUT - 1];
     }
   }
 }
 
-// xy pass and completion.  MODE 0: five z-filtered moments -> SSIM -> maps and loss;
-// MODE 1: three z-filtered maps -> dL/dx = f1 + 2 x f2 + y f3.
+// xy filtering and completion of a tile of one slice (an image of a 2D batch or a z-plane of a
+// volume; slice = blockIdx.z, nx x ny elements, channels cstride elements apart).
+//   MODE 0  2D forward: X, Y -> moments (x, y), (x^2, y^2) and x y -> SSIM, maps, loss
+//   MODE 1  3D forward: the five z-filtered moments -> SSIM, maps, loss
+//   MODE 2  backward (2D, or 3D after the z pass): maps m1, m2, m3 (filtered in z for 3D)
+//           -> dL/dx = w * m1 + 2 x (w * m2) + y (w * m3)
+// The maps are m1 = dS/dmu_x - 2 mu_x dS/dsxx - mu_y dS/dsxy, m2 = dS/dsxx, m3 = dS/dsxy, each
+// times -weight / N (the loss is weight * (1 - mean SSIM)), stored in the pair layout.
+template <int MODE>
+struct XyShape {
+  static constexpr int NPI = MODE == 1 ? 2 : 1;  // staged channel pairs
+  static constexpr int NSI = MODE == 0 ? 0 : 1;  // staged single channels
+  static constexpr int NPO = MODE == 2 ? 1 : 2;  // filtered pairs
+  static constexpr int NSO = 1;                  // filtered singles
+  // shared memory: rows of odd stride (in elements), so that a warp reading 32 consecutive
+  // rows of one column hits distinct banks
+  static constexpr size_t in2 = (size_t)NPI * kIn2 * (kIn2 + 1) * sizeof(float2);
+  static constexpr size_t in1 = (size_t)NSI * kIn2 * (kIn2 + 1) * sizeof(float);
+  static constexpr size_t h2 = (size_t)NPO * kIn2 * (kT2 + 1) * sizeof(float2);
+  static constexpr size_t h1 = (size_t)NSO * kIn2 * (kT2 + 1) * sizeof(float);
+  static constexpr size_t smem = in2 + in1 + h2 + h1;
+};
+
 template <int MODE>
 __global__ void __launch_bounds__(kSsimThreads)
-    k_ssim3d_xy(const __grid_constant__ Win W, const float* __restrict__ in, int nx, int ny,
-                int64_t plane, float C1, float C2, float gscale, float* __restrict__ loss,
-                float* __restrict__ maps, const float* __restrict__ X,
-                const float* __restrict__ Y, float* __restrict__ grad, int accumulate) {
-  constexpr int NM = MODE == 0 ? 5 : 3;
-  extern __shared__ float dyn[];
-  float (*sin_)[kIn2][kIn2 + 1] = reinterpret_cast<float (*)[kIn2][kIn2 + 1]>(dyn);
-  float (*hm)[kIn2][kT2 + 1] =
-      reinterpret_cast<float (*)[kIn2][kT2 + 1]>(dyn + NM * kIn2 * (kIn2 + 1));
-  const int z = blockIdx.z;
+    k_ssim_xy(const __grid_constant__ Win W, const float* __restrict__ A,
+              const float* __restrict__ Bsrc, int64_t cstride, int nx, int ny, float C1,
+              float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
+              const float* __restrict__ X, const float* __restrict__ Y,
+              float* __restrict__ grad, int accumulate) {
+  using S = XyShape<MODE>;
+  constexpr int NPI = S::NPI, NSI = S::NSI, NPO = S::NPO, NSO = S::NSO;
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  float2 (*in2)[kIn2][kIn2 + 1] = reinterpret_cast<float2 (*)[kIn2][kIn2 + 1]>(dyn_raw);
+  float (*in1)[kIn2][kIn2 + 1] = reinterpret_cast<float (*)[kIn2][kIn2 + 1]>(dyn_raw + S::in2);
+  float2 (*h2)[kIn2][kT2 + 1] =
+      reinterpret_cast<float2 (*)[kIn2][kT2 + 1]>(dyn_raw + S::in2 + S::in1);
+  float (*h1)[kIn2][kT2 + 1] =
+      reinterpret_cast<float (*)[kIn2][kT2 + 1]>(dyn_raw + S::in2 + S::in1 + S::h2);
   const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
-  const size_t sxy = (size_t)nx * ny, zo = (size_t)z * sxy;
+  const size_t slice = (size_t)blockIdx.z * nx * ny;
   const int tid = threadIdx.x;
+  // ---- stage the halo tile (zero outside the slice); every load before the first store
   {
-    const float* src[NM];
+    constexpr int NC = 2 * NPI + NSI;
+    float v[kStageIters][NC];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) src[m] = in + m * plane + zo;
-    stage_halo<NM>(src, x0, y0, nx, ny, sin_);
+    for (int it = 0; it < kStageIters; ++it) {
+      const int p = tid + it * kSsimThreads;
+      const int r = p / kIn2, c = p % kIn2, y = y0 + r, x = x0 + c;
+      const bool ok = p < kIn2 * kIn2 && x >= 0 && x < nx && y >= 0 && y < ny;
+      const size_t o = slice + (size_t)y * nx + x;
+      if (MODE == 0) {
+        v[it][0] = ok ? A[o] : 0.f;
+        v[it][1] = ok ? Bsrc[o] : 0.f;
+      } else {
+        // pair layout: NPI float2 planes, then the single
+#pragma unroll
+        for (int m = 0; m < NPI; ++m) {
+          const float2 q = ok ? pair_at(A, cstride, m, o) : make_float2(0.f, 0.f);
+          v[it][2 * m] = q.x;
+          v[it][2 * m + 1] = q.y;
+        }
+        v[it][2 * NPI] = ok ? A[2 * NPI * cstride + o] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kStageIters; ++it) {
+      const int p = tid + it * kSsimThreads;
+      if (p < kIn2 * kIn2) {
+        const int r = p / kIn2, c = p % kIn2;
+#pragma unroll
+        for (int m = 0; m < NPI; ++m) in2[m][r][c] = make_float2(v[it][2 * m], v[it][2 * m + 1]);
+#pragma unroll
+        for (int m = 0; m < NSI; ++m) in1[m][r][c] = v[it][2 * NPI + m];
+      }
+    }
   }
+  float2 w2[2 * kR + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k) w2[k] = make_float2(W.w[k], W.w[k]);
   __syncthreads();
+  // ---- horizontal pass: item p = (row r, columns c0 .. c0 + 3); lanes take consecutive rows
   for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
-    const int r = p / (kT2 / kG), c0 = (p % (kT2 / kG)) * kG;
-    float acc[NM][kG];
+    const int r = p % kIn2, c0 = (p / kIn2) * kG;
+    float2 a2[NPO][kG];
+    float a1[NSO][kG];
 #pragma unroll
-    for (int m = 0; m < NM; ++m)
+    for (int j = 0; j < kG; ++j) {
 #pragma unroll
-      for (int j = 0; j < kG; ++j) acc[m][j] = 0.f;
+      for (int m = 0; m < NPO; ++m) a2[m][j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < NSO; ++m) a1[m][j] = 0.f;
+    }
 #pragma unroll
     for (int i = 0; i < kG + 2 * kR; ++i) {
-      float u[NM];
+      float2 u2[NPO];
+      float u1[NSO];
+      if (MODE == 0) {
+        const float2 xy = in2[0][r][c0 + i];
+        u2[0] = xy;
+        u2[NPO - 1] = __fmul2_rn(xy, xy);
+        u1[0] = xy.x * xy.y;
+      } else {
 #pragma unroll
-      for (int m = 0; m < NM; ++m) u[m] = sin_[m][r][c0 + i];
+        for (int m = 0; m < NPO; ++m) u2[m] = in2[m][r][c0 + i];
+#pragma unroll
+        for (int m = 0; m < NSO; ++m) u1[m] = in1[m][r][c0 + i];
+      }
 #pragma unroll
       for (int j = 0; j < kG; ++j) {
         const int k = i - j;
         if (k < 0 || k > 2 * kR) continue;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m][j] = fmaf(W.w[k], u[m], acc[m][j]);
+        for (int m = 0; m < NPO; ++m) a2[m][j] = __ffma2_rn(w2[k], u2[m], a2[m][j]);
+#pragma unroll
+        for (int m = 0; m < NSO; ++m) a1[m][j] = fmaf(w2[k].x, u1[m], a1[m][j]);
       }
     }
 #pragma unroll
-    for (int m = 0; m < NM; ++m)
+    for (int j = 0; j < kG; ++j) {
 #pragma unroll
-      for (int j = 0; j < kG; ++j) hm[m][r][c0 + j] = acc[m][j];
+      for (int m = 0; m < NPO; ++m) h2[m][r][c0 + j] = a2[m][j];
+#pragma unroll
+      for (int m = 0; m < NSO; ++m) h1[m][r][c0 + j] = a1[m][j];
+    }
   }
   __syncthreads();
+  // ---- vertical pass: column tx, rows ty0 .. ty0 + 3
   const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
-  float f[NM][kG];
+  float2 f2[NPO][kG];
+  float f1[NSO][kG];
 #pragma unroll
-  for (int m = 0; m < NM; ++m)
+  for (int j = 0; j < kG; ++j) {
 #pragma unroll
-    for (int j = 0; j < kG; ++j) f[m][j] = 0.f;
+    for (int m = 0; m < NPO; ++m) f2[m][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < NSO; ++m) f1[m][j] = 0.f;
+  }
 #pragma unroll
   for (int i = 0; i < kG + 2 * kR; ++i) {
-    float h[NM];
+    float2 u2[NPO];
+    float u1[NSO];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) h[m] = hm[m][ty0 + i][tx];
+    for (int m = 0; m < NPO; ++m) u2[m] = h2[m][ty0 + i][tx];
+#pragma unroll
+    for (int m = 0; m < NSO; ++m) u1[m] = h1[m][ty0 + i][tx];
 #pragma unroll
     for (int j = 0; j < kG; ++j) {
       const int k = i - j;
       if (k < 0 || k > 2 * kR) continue;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) f[m][j] = fmaf(W.w[k], h[m], f[m][j]);
+      for (int m = 0; m < NPO; ++m) f2[m][j] = __ffma2_rn(w2[k], u2[m], f2[m][j]);
+#pragma unroll
+      for (int m = 0; m < NSO; ++m) f1[m][j] = fmaf(w2[k].x, u1[m], f1[m][j]);
     }
   }
+  // ---- completion
   const int x = blockIdx.x * kT2 + tx;
   float contrib = 0.f;
 #pragma unroll
   for (int j = 0; j < kG; ++j) {
     const int y = blockIdx.y * kT2 + ty0 + j;
     if (x >= nx || y >= ny) continue;
-    const size_t o = zo + (size_t)y * nx + x;
-    if (MODE == 0) {
-      const float mx = f[0][j], my = f[1][j];
-      const float sxx = f[2][j] - mx * mx, syy = f[3][j] - my * my, sxy2 = f[4][j] - mx * my;
-      const float A = 2.f * mx * my + C1, Bn = 2.f * sxy2 + C2;
+    const size_t o = slice + (size_t)y * nx + x;
+    if (MODE == 2) {
+      const float g = f2[0][j].x + 2.f * X[o] * f2[0][j].y + Y[o] * f1[0][j];
+      grad[o] = accumulate ? grad[o] + g : g;
+    } else {
+      const float mx = f2[0][j].x, my = f2[0][j].y;
+      const float sxx = f2[NPO - 1][j].x - mx * mx, syy = f2[NPO - 1][j].y - my * my;
+      const float sxy = f1[0][j] - mx * my;
+      const float Am = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
       const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
       const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
-      const float S = (A * Bn) * inv;
-      const float dmu = (2.f * my * Bn) * inv - S * (2.f * mx) * (D * inv);
-      const float dsxx = -S * (C * inv);
-      const float dsxy = 2.f * A * inv;
-      maps[o] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
-      maps[plane + o] = gscale * dsxx;
-      maps[2 * plane + o] = gscale * dsxy;
-      contrib += 1.f - S;
-    } else {
-      const float g = f[0][j] + 2.f * X[o] * f[1][j] + Y[o] * f[2][j];
-      grad[o] = accumulate ? grad[o] + g : g;
+      const float Sv = (Am * Bn) * inv;
+      const float dmu = (2.f * my * Bn) * inv - Sv * (2.f * mx) * (D * inv);
+      const float dsxx = -Sv * (C * inv);
+      const float dsxy = 2.f * Am * inv;
+      reinterpret_cast<float2*>(maps)[o] =
+          make_float2(gscale * (dmu - 2.f * mx * dsxx - my * dsxy), gscale * dsxx);
+      maps[2 * cstride + o] = gscale * dsxy;
+      contrib += 1.f - Sv;
     }
   }
-  if (MODE == 0 && loss) block_add(contrib * (-gscale), loss);
+  if (MODE != 2 && loss) block_add(contrib * (-gscale), loss);
 }
 
-template <int MODE>
-constexpr size_t ssim3d_xy_smem() {
-  return sizeof(float) * (size_t)(MODE == 0 ? 5 : 3) * kIn2 * ((kIn2 + 1) + (kT2 + 1));
+// Sets the dynamic shared-memory limit of the xy kernels that need more than 48 KB (host-side
+// state of the current device; set on every call).
+int ssim_xy_attributes() {
+  const cudaError_t e = cudaFuncSetAttribute(k_ssim_xy<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)XyShape<1>::smem);
+  if (e != cudaSuccess) {
+    set_last_error("ssim_xy attributes", e);
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -626,6 +540,24 @@ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 }  // namespace
 }  // namespace gs
 
+namespace gs {
+namespace {
+// The two 2D SSIM launches: moments, SSIM and maps; then the gradient from the maps.
+int ssim2d(const float* d_x, const float* d_y, int H, int W, dim3 grid, float C1, float C2,
+           float gscale, float* d_loss, float* maps, int64_t plane, float* d_grad,
+           int accumulate, cudaStream_t s) {
+  const Win Wn = host_window();
+  const dim3 block(kSsimThreads);
+  GS_TRY(launch("ssim2d_fwd", k_ssim_xy<0>, grid, block, XyShape<0>::smem, s, Wn, d_x, d_y,
+                plane, W, H, C1, C2, gscale, d_loss, maps, (const float*)nullptr,
+                (const float*)nullptr, (float*)nullptr, 0));
+  return launch("ssim2d_bwd", k_ssim_xy<2>, grid, block, XyShape<2>::smem, s, Wn,
+                (const float*)maps, (const float*)nullptr, plane, W, H, C1, C2, gscale,
+                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate);
+}
+}  // namespace
+}  // namespace gs
+
 using namespace gs;
 
 extern "C" {
@@ -676,12 +608,10 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
-  dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img), block(kSsimThreads);
+  const dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img);
   float* maps = (float*)d_ws;
-  GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
-                d_loss, maps, plane));
-  return launch("ssim2d_bwd", k_ssim2d_bwd, grid, block, 0, s, d_x, d_y, H, W,
-                (const float*)maps, plane, d_grad, accumulate);
+  return ssim2d(d_x, d_y, H, W, grid, C1, C2, gscale, d_loss, maps, plane, d_grad, accumulate,
+                s);
 }
 
 }  // extern "C"
@@ -740,12 +670,10 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
-  dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img), block(kSsimThreads);
+  const dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img);
   // kernel 1 writes every map entry kernel 2 reads, so the array needs no clearing between calls
-  GS_TRY(launch("ssim2d_fwd", k_ssim2d_fwd, grid, block, 0, s, d_x, d_y, H, W, C1, C2, gscale,
-                d_loss, maps, plane));
-  return launch("ssim2d_bwd", k_ssim2d_bwd, grid, block, 0, s, d_x, d_y, H, W,
-                (const float*)maps, plane, d_grad, accumulate);
+  return ssim2d(d_x, d_y, H, W, grid, C1, C2, gscale, d_loss, maps, plane, d_grad, accumulate,
+                s);
 }
 
 size_t gs_ssim3d_workspace_size(int64_t n_voxels) {
@@ -761,40 +689,31 @@ int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, f
   if (!d_grad && !d_loss) return GS_ERR_ARG;
   const int64_t plane = (int64_t)nx * ny * nz;
   if (ws_bytes < gs_ssim3d_workspace_size(plane)) return GS_ERR_CAPACITY;
-  // the forward's xy kernel needs more than the default 48 KB of dynamic shared memory; the
-  // attribute is host-side state of the current device, set on every call
-  cudaError_t attr_err = cudaFuncSetAttribute(
-      k_ssim3d_xy<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssim3d_xy_smem<0>());
-  if (attr_err == cudaSuccess)
-    attr_err = cudaFuncSetAttribute(k_ssim3d_xy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ssim3d_xy_smem<1>());
-  if (attr_err != cudaSuccess) {
-    set_last_error("ssim3d_xy attributes", attr_err);
-    return GS_ERR_CUDA;
-  }
+  // the forward's xy kernel needs more than the default 48 KB of dynamic shared memory
+  GS_TRY(ssim_xy_attributes());
   cudaStream_t s = (cudaStream_t)stream;
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
   const float gscale = -weight / (float)plane;
   const Win W = host_window();
-  float* maps = (float*)d_ws;         // 3 volumes, kept from the forward for the backward
-  float* tmp = maps + 3 * plane;      // 5 volumes of z-filtered channels
+  // maps (pair layout, 3 volumes), kept from the forward for the backward; then the 5 volumes
+  // of z-filtered channels (pair layout), 16-byte aligned (the workspace's 256-byte slack)
+  float* maps = (float*)d_ws;
+  float* tmp = (float*)(((uintptr_t)(maps + 3 * plane) + 15) & ~(uintptr_t)15);
   const dim3 gxy((nx + kT2 - 1) / kT2, (ny + kT2 - 1) / kT2, nz), bxy(kSsimThreads);
   const int64_t cols = (int64_t)nx * ny;
   const dim3 gz((unsigned)((cols + kThreads - 1) / kThreads)), bz(kThreads);
-  const float* nul = nullptr;
-  GS_TRY(launch("ssim3d_z_fwd", k_ssim3d_z<2>, gz, bz, 0, s, W, d_x, d_y, nul, nx, ny, nz, plane,
+  GS_TRY(launch("ssim3d_z_fwd", k_ssim3d_z<2>, gz, bz, 0, s, W, d_x, d_y, nx, ny, nz, plane,
                 tmp));
-  GS_TRY(launch("ssim3d_xy_fwd", k_ssim3d_xy<0>, gxy, bxy, ssim3d_xy_smem<0>(), s, W,
-                (const float*)tmp, nx, ny, plane, C1, C2, gscale, d_loss, maps, nul, nul,
-                (float*)nullptr, 0));
+  GS_TRY(launch("ssim3d_xy_fwd", k_ssim_xy<1>, gxy, bxy, XyShape<1>::smem, s, W,
+                (const float*)tmp, (const float*)nullptr, plane, nx, ny, C1, C2, gscale, d_loss,
+                maps, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, 0));
   if (!d_grad) return GS_OK;  // value only
   GS_TRY(launch("ssim3d_z_bwd", k_ssim3d_z<3>, gz, bz, 0, s, W, (const float*)maps,
-                (const float*)(maps + plane), (const float*)(maps + 2 * plane), nx, ny, nz,
-                plane, tmp));
-  return launch("ssim3d_xy_bwd", k_ssim3d_xy<1>, gxy, bxy, ssim3d_xy_smem<1>(), s, W,
-                (const float*)tmp, nx, ny, plane, C1, C2, gscale, (float*)nullptr,
-                (float*)nullptr, d_x, d_y, d_grad, accumulate);
+                (const float*)nullptr, nx, ny, nz, plane, tmp));
+  return launch("ssim3d_xy_bwd", k_ssim_xy<2>, gxy, bxy, XyShape<2>::smem, s, W,
+                (const float*)tmp, (const float*)nullptr, plane, nx, ny, C1, C2, gscale,
+                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate);
 }
 
 int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, float* d_m,
