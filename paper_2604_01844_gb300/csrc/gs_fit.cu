@@ -158,10 +158,13 @@ int gs_fit_volume(const float* d_vol_gt, const gs_grid* grid, int n, int iters,
     GS_CUDA(cudaMemsetAsync(L.loss, 0, sizeof(float), s));
     GS_TRY(gs_voxelize(d_mean_rho, d_scale, d_quat, n, grid, lo, grid->dims, &o, L.vol, L.vox_ws,
                        L.vox_bytes, stream));
-    GS_TRY(gs_l1_loss(L.vol, d_vol_gt, nvox, 1.f, L.loss, L.dvol, 0, stream));
-    if (fo->alpha_ssim > 0.f)
-      GS_TRY(gs_ssim3d_loss(L.vol, d_vol_gt, nx, ny, nz, data_range, fo->alpha_ssim, L.loss,
-                            L.dvol, 1, L.maps, maps_bytes, stream));
+    if (fo->alpha_ssim > 0.f) {
+      // L1 + alpha SSIM3D in the SSIM passes (no separate L1 pass over the volume)
+      GS_TRY(ssim3d(L.vol, d_vol_gt, nx, ny, nz, data_range, fo->alpha_ssim, 1.f, L.loss,
+                    L.dvol, 0, L.maps, maps_bytes, stream));
+    } else {
+      GS_TRY(gs_l1_loss(L.vol, d_vol_gt, nvox, 1.f, L.loss, L.dvol, 0, stream));
+    }
     GS_TRY(gs_voxelize_backward(d_mean_rho, d_scale, d_quat, n, grid, lo, grid->dims, &o, L.dvol,
                                 (float*)g_mr, (float*)g_sc, (float*)g_q, 0, 1, L.vox_ws,
                                 L.vox_bytes, stream));

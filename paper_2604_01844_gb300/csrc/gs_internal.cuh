@@ -109,6 +109,12 @@ int build_ranges(const uint32_t* keys, uint2* ranges, int64_t n_keys, gs_status*
 
 int bits_for(int64_t n_keys);
 
+// gs_ssim3d_loss plus, with l1_weight != 0, the L1 term l1_weight * mean |x - y| fused into the
+// same passes (loss and gradient), as the volume fit's L1 + alpha SSIM loss (Eq. 6) uses it.
+int ssim3d(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
+           float weight, float l1_weight, float* d_loss, float* d_grad, int accumulate,
+           void* d_ws, size_t ws_bytes, void* stream);
+
 }  // namespace gs
 
 // ------------------------------------------------------------------------------------------

@@ -163,15 +163,18 @@ __device__ __forceinline__ float2 pair_at(const float* base, int64_t n, int m, i
   return reinterpret_cast<const float2*>(base)[m * n + o];
 }
 
+// With l1_scale != 0 the forward also adds l1_scale * sum |X - Y| over its columns to *loss
+// (the L1 term of a fused L1 + SSIM loss).
 template <int NIN>  // 2: (X, Y) -> 5 moments; 3: maps (pair layout) -> 3 filtered maps
 __global__ void __launch_bounds__(kThreads)
     k_ssim3d_z(const __grid_constant__ Win W, const float* __restrict__ A0,
                const float* __restrict__ A1, int nx, int ny, int nz, int64_t plane,
-               float* __restrict__ out) {
+               float* __restrict__ out, float l1_scale, float* __restrict__ loss) {
   constexpr int NOUT = NIN == 2 ? 5 : 3;
   const int64_t sxy = (int64_t)nx * ny;
   const int64_t col = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (col >= sxy) return;
+  float l1 = 0.f;
+  if (col < sxy) {
   // element o of input i: X / Y, or the maps' pair (i = 0, 1) and single (i = 2)
   auto load = [&](int64_t o, float (&v)[NIN]) {
     if (NIN == 2) {
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(kThreads)
       const int zi = zb + k;
 #pragma unroll
       for (int i = 0; i < NIN; ++i) ring[k][i] = nxt[i];
+      if (NIN == 2 && l1_scale != 0.f) l1 += fabsf(nxt[0] - nxt[1]);  // 0 beyond the volume
       const int zn = zi + 1;
       if (zn < nz) {
         load((int64_t)zn * sxy + col, nxt);
@@ -245,6 +249,8 @@ __global__ void __launch_bounds__(kThreads)
       out[2 * (NOUT / 2) * plane + o] = acc[NOUT - 1];
     }
   }
+  }
+  if (NIN == 2 && l1_scale != 0.f && loss) block_add(l1 * l1_scale, loss);
 }
 
 // xy filtering and completion of a tile of one slice (an image of a 2D batch or a z-plane of a
@@ -252,7 +258,8 @@ __global__ void __launch_bounds__(kThreads)
 //   MODE 0  2D forward: X, Y -> moments (x, y), (x^2, y^2) and x y -> SSIM, maps, loss
 //   MODE 1  3D forward: the five z-filtered moments -> SSIM, maps, loss
 //   MODE 2  backward (2D, or 3D after the z pass): maps m1, m2, m3 (filtered in z for 3D)
-//           -> dL/dx = w * m1 + 2 x (w * m2) + y (w * m3)
+//           -> dL/dx = w * m1 + 2 x (w * m2) + y (w * m3) (+ l1g sign(x - y) when fused
+//           with an L1 term)
 // The maps are m1 = dS/dmu_x - 2 mu_x dS/dsxx - mu_y dS/dsxy, m2 = dS/dsxx, m3 = dS/dsxy, each
 // times -weight / N (the loss is weight * (1 - mean SSIM)), stored in the pair layout.
 template <int MODE>
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(kSsimThreads)
               const float* __restrict__ Bsrc, int64_t cstride, int nx, int ny, float C1,
               float C2, float gscale, float* __restrict__ loss, float* __restrict__ maps,
               const float* __restrict__ X, const float* __restrict__ Y,
-              float* __restrict__ grad, int accumulate) {
+              float* __restrict__ grad, int accumulate, float l1g) {
   using S = XyShape<MODE>;
   constexpr int NPI = S::NPI, NSI = S::NSI, NPO = S::NPO, NSO = S::NSO;
   extern __shared__ __align__(16) unsigned char dyn_raw[];
@@ -413,7 +420,9 @@ __global__ void __launch_bounds__(kSsimThreads)
     if (x >= nx || y >= ny) continue;
     const size_t o = slice + (size_t)y * nx + x;
     if (MODE == 2) {
-      const float g = f2[0][j].x + 2.f * X[o] * f2[0][j].y + Y[o] * f1[0][j];
+      const float xv = X[o], yv = Y[o];
+      float g = f2[0][j].x + 2.f * xv * f2[0][j].y + yv * f1[0][j];
+      if (l1g != 0.f) g = l1g * sgnf(xv - yv) + g;  // fused L1 term
       grad[o] = accumulate ? grad[o] + g : g;
     } else {
       const float mx = f2[0][j].x, my = f2[0][j].y;
@@ -550,10 +559,10 @@ int ssim2d(const float* d_x, const float* d_y, int H, int W, dim3 grid, float C1
   const dim3 block(kSsimThreads);
   GS_TRY(launch("ssim2d_fwd", k_ssim_xy<0>, grid, block, XyShape<0>::smem, s, Wn, d_x, d_y,
                 plane, W, H, C1, C2, gscale, d_loss, maps, (const float*)nullptr,
-                (const float*)nullptr, (float*)nullptr, 0));
+                (const float*)nullptr, (float*)nullptr, 0, 0.f));
   return launch("ssim2d_bwd", k_ssim_xy<2>, grid, block, XyShape<2>::smem, s, Wn,
                 (const float*)maps, (const float*)nullptr, plane, W, H, C1, C2, gscale,
-                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate);
+                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate, 0.f);
 }
 }  // namespace
 }  // namespace gs
@@ -683,6 +692,17 @@ size_t gs_ssim3d_workspace_size(int64_t n_voxels) {
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream) {
+  return gs::ssim3d(d_x, d_y, nx, ny, nz, data_range, weight, 0.f, d_loss, d_grad, accumulate,
+                    d_ws, ws_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace gs {
+
+int ssim3d(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
+           float weight, float l1_weight, float* d_loss, float* d_grad, int accumulate,
+           void* d_ws, size_t ws_bytes, void* stream) {
   if (!d_x || !d_y || !d_ws || nx < 1 || ny < 1 || nz < 1 || !(data_range > 0.f))
     return GS_ERR_ARG;
   if (nz > 65535) return GS_ERR_ARG;
@@ -703,18 +723,23 @@ int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, f
   const dim3 gxy((nx + kT2 - 1) / kT2, (ny + kT2 - 1) / kT2, nz), bxy(kSsimThreads);
   const int64_t cols = (int64_t)nx * ny;
   const dim3 gz((unsigned)((cols + kThreads - 1) / kThreads)), bz(kThreads);
+  const float l1s = l1_weight / (float)plane;
   GS_TRY(launch("ssim3d_z_fwd", k_ssim3d_z<2>, gz, bz, 0, s, W, d_x, d_y, nx, ny, nz, plane,
-                tmp));
+                tmp, l1s, d_loss));
   GS_TRY(launch("ssim3d_xy_fwd", k_ssim_xy<1>, gxy, bxy, XyShape<1>::smem, s, W,
                 (const float*)tmp, (const float*)nullptr, plane, nx, ny, C1, C2, gscale, d_loss,
-                maps, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, 0));
+                maps, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, 0, 0.f));
   if (!d_grad) return GS_OK;  // value only
   GS_TRY(launch("ssim3d_z_bwd", k_ssim3d_z<3>, gz, bz, 0, s, W, (const float*)maps,
-                (const float*)nullptr, nx, ny, nz, plane, tmp));
+                (const float*)nullptr, nx, ny, nz, plane, tmp, 0.f, (float*)nullptr));
   return launch("ssim3d_xy_bwd", k_ssim_xy<2>, gxy, bxy, XyShape<2>::smem, s, W,
                 (const float*)tmp, (const float*)nullptr, plane, nx, ny, C1, C2, gscale,
-                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate);
+                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate, l1s);
 }
+
+}  // namespace gs
+
+extern "C" {
 
 int gs_adam_step(float* d_raw_mean_rho, float* d_raw_scale, float* d_raw_quat, float* d_m,
                  float* d_v, const float* d_g_mean_rho, const float* d_g_scale,
