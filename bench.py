@@ -37,10 +37,46 @@ SMALL = dict(WORKLOAD, workload="recon step, 16 cone views x 512^2, 50k Gaussian
 METRIC = "Gaussian-pixel evals/s (fwd+bwd step) at 75x512^2"
 UNIT = "evals/s"
 
-# evaluations per SM clock at the ALU roofline of the evaluation kernels:
-# forward: one ex2 per evaluation on 16 SFU lanes/SM/clk; backward: ~16 FP32 ops per
-# evaluation on 128 FP32 lanes/SM/clk.
-EVALS_PER_SM_CLK = {"raster_fwd": 16.0, "raster_bwd": 8.0, "vox_fwd": 16.0, "vox_bwd": 8.0}
+# The evaluation kernels' work per in-cut evaluation: one ex2 on the special-function unit and
+# this many FP32 lane operations (raster_fwd: offset, two fma for the exponent, the
+# accumulating fma; raster_bwd: two fma, G = g e, G dx, three moment updates -- the y moments
+# are folded per row; vox_fwd: the z offset fma, two fma, the accumulating fma; vox_bwd: the
+# same offset and exponent, q = g e, q dz, three moment updates).  Their roofline is the
+# slower of the two units at the rates the probe kernels measure.
+FP32_OPS_PER_EVAL = {"raster_fwd": 4, "raster_bwd": 7, "vox_fwd": 4, "vox_bwd": 8}
+
+
+def alu_peaks(device, blocks_per_sm=8, iters=2048):
+    """Measured throughput of ex2.approx (SFU) and FP32 fma (ops/s) by the library's probe
+    kernels, timed with CUDA events after warm-up; also per SM per clock at f_mhz."""
+    import torch
+
+    from paper_2604_01844_gb300 import binding as B
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * blocks_per_sm
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=device)
+    out = {}
+    for kind, name in ((0, "ex2"), (1, "fma")):
+        for _ in range(3):
+            B.check(B.lib().gs_probe_rate(kind, blocks, iters, B.ptr(sink), B.stream_handle()),
+                    "gs_probe_rate")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.check(B.lib().gs_probe_rate(kind, blocks, iters, B.ptr(sink), B.stream_handle()),
+                "gs_probe_rate")
+        e1.record()
+        e1.synchronize()
+        out[name + "_per_s"] = blocks * 256 * 8 * iters / (e0.elapsed_time(e1) * 1e-3)
+    out["sms"] = sms
+    return out
+
+
+def eval_peak(kernel, peaks):
+    """Roofline of an evaluation kernel in evaluations/s and its binding unit."""
+    sfu = peaks["ex2_per_s"]
+    fp32 = peaks["fma_per_s"] / FP32_OPS_PER_EVAL[kernel]
+    return (sfu, "sfu") if sfu <= fp32 else (fp32, "fp32")
 
 
 def log(*a):
@@ -240,14 +276,21 @@ def run_ours(args, ws, rank, local):
     mp = measured_peaks() or {}
     f_mhz = (clk or {}).get("sm_mhz") or mp.get("sm_max_mhz", 2070.0)
     roof = None
-    if name in EVALS_PER_SM_CLK:
+    peaks = alu_peaks(device)
+    per_clk = {k: round(v / (sms * f_mhz * 1e6), 2) for k, v in peaks.items() if k != "sms"}
+    if name in FP32_OPS_PER_EVAL:
         units = evals_px if name.startswith("raster") else evals_vox
-        peak = sms * f_mhz * 1e6 * EVALS_PER_SM_CLK[name] / 1e9
+        peak_s, unit_name = eval_peak(name, peaks)
+        peak = peak_s / 1e9
         ach = units / (avg_ms * 1e-3) / 1e9
         roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2),
                 "unit": "Geval/s", "frac": round(ach / peak, 4), "traffic": read_traffic(name),
-                "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz (median sampled) x "
-                              f"{EVALS_PER_SM_CLK[name]:g} evals/SM/clk",
+                "peak_basis": f"measured by the probe kernels: ex2 {peaks['ex2_per_s'] / 1e9:.0f} "
+                              f"G/s ({per_clk['ex2_per_s']} per SM per clock at {f_mhz:.0f} MHz), "
+                              f"fp32 fma {peaks['fma_per_s'] / 1e9:.0f} G/s "
+                              f"({per_clk['fma_per_s']}); one ex2 and "
+                              f"{FP32_OPS_PER_EVAL[name]} FP32 operations per evaluation, "
+                              f"bound by the {unit_name}",
                 "avg_launch_ms": round(avg_ms, 4), "launches": nl}
     else:
         roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": mp.get("hbm_gbs"),
@@ -256,12 +299,12 @@ def run_ours(args, ws, rank, local):
 
     # the same ALU roofline for every evaluation kernel of the step
     kernel_roofs = {}
-    for kname, per_clk in EVALS_PER_SM_CLK.items():
+    for kname in FP32_OPS_PER_EVAL:
         if kname not in per_kernel:
             continue
         kl, kt = per_kernel[kname]
         units = evals_px if kname.startswith("raster") else evals_vox
-        kpeak = sms * f_mhz * 1e6 * per_clk / 1e9
+        kpeak = eval_peak(kname, peaks)[0] / 1e9
         kach = units / ((kt / max(kl, 1)) * 1e-3) / 1e9
         kernel_roofs[kname] = {"achieved": round(kach, 2), "peak": round(kpeak, 2),
                                "unit": "Geval/s", "frac": round(kach / kpeak, 4),
@@ -280,6 +323,9 @@ def run_ours(args, ws, rank, local):
                    "l2": "working set per step > 0.5 GB (images, SSIM maps, 256^3 volume) > L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof, "kernel_rooflines": kernel_roofs,
+        "alu_peaks": {"ex2_per_s": round(peaks["ex2_per_s"]), "fma_per_s": round(peaks["fma_per_s"]),
+                      "per_sm_per_clock": per_clk, "sm_mhz": f_mhz,
+                      "note": "probe kernels gs_probe_rate, 8 CTAs of 256 threads per SM"},
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in
                                 sorted(per_kernel.items(), key=lambda kv: -kv[1][1])},
         "e2e": {"value": R.job_rate(evals_px, ms_e2e, ws), "unit": UNIT, "ms_per_step": ms_e2e,

@@ -116,6 +116,13 @@ const char* gs_last_error(void);
 /* Asynchronous byte fill of a device buffer (e.g. zeroing a loss accumulator). */
 int gs_memset(void* d_ptr, int value, size_t bytes, void* stream);
 
+/* Throughput probe of the units the evaluation kernels are bound by (their roofline
+ * denominators): kind 0 = ex2.approx.ftz.f32 on the special-function unit, kind 1 = FP32 fma.
+ * Launches `blocks` CTAs of 256 threads, each thread running 8 independent chains of `iters`
+ * operations (blocks * 256 * 8 * iters in total); d_sink receives blocks * 256 floats.  Time it
+ * with events on `stream`.  GS_ERR_ARG for kind not 0/1 or non-positive sizes. */
+int gs_probe_rate(int kind, int blocks, int iters, float* d_sink, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * X-ray rasterizer (Sec. 3.2, 3.5; Eq. 3, Eq. 4)
  * ------------------------------------------------------------------------------------- */

@@ -98,6 +98,7 @@ SIGNATURES = {
     "gs_read_status": (_I, [_P, _P, ctypes.POINTER(GsStatus)]),
     "gs_last_error": (ctypes.c_char_p, []),
     "gs_memset": (_I, [_P, _I, _SZ, _P]),
+    "gs_probe_rate": (_I, [_I, _I, _I, _P, _P]),
     "gs_project_workspace_size": (_SZ, [_I, _I, _I, _I, _OPTS, _I64]),
     "gs_project_count_pairs": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _OPTS, _P, _SZ, _P,
                                     ctypes.POINTER(ctypes.c_int64)]),

@@ -77,7 +77,57 @@ int num_sms() {
 
 }  // namespace gs
 
+namespace gs {
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+// Throughput probes of the two units the evaluation kernels use: each thread runs 8
+// independent chains of `iters` operations (enough independent work per warp to keep the unit
+// busy), and writes the sum of its chains so that nothing is optimised away.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_ex2(float* __restrict__ sink, int iters) {
+  float a[kProbeChains];
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) a[j] = 0.25f + 0.01f * (float)((threadIdx.x + j) & 31);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) a[j] = gsd::ex2(-a[j]);  // stays in [1/2, 1)
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) t += a[j];
+  sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kProbeThreads) k_probe_fma(float* __restrict__ sink, int iters) {
+  float a[kProbeChains];
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) a[j] = 0.25f + 0.01f * (float)((threadIdx.x + j) & 31);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) a[j] = fmaf(a[j], 0.999f, 0.0005f);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) t += a[j];
+  sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = t;
+}
+
+}  // namespace
+}  // namespace gs
+
 extern "C" {
+
+int gs_probe_rate(int kind, int blocks, int iters, float* d_sink, void* stream) {
+  if ((kind != 0 && kind != 1) || blocks < 1 || iters < 1 || !d_sink) return GS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (kind == 0)
+    return gs::launch("probe_ex2", gs::k_probe_ex2, dim3(blocks), dim3(gs::kProbeThreads), 0, s,
+                      d_sink, iters);
+  return gs::launch("probe_fma", gs::k_probe_fma, dim3(blocks), dim3(gs::kProbeThreads), 0, s,
+                    d_sink, iters);
+}
 
 const char* gs_version(void) { return "gsct 0.1 (sm_103a)"; }
 
