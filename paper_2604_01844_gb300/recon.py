@@ -35,6 +35,7 @@ class ReconConfig:
     cut: float = 3.0
     tv_roi: tuple | None = None  # (lo, dim) of the TV region; None = whole grid
     recompute_lists: bool = False  # backward rebuilds the sorted lists instead of reusing them
+    overlap_tv: bool = True  # the TV branch runs on a second stream beside the projection
 
 
 def inverse_softplus(x: np.ndarray) -> np.ndarray:
@@ -109,12 +110,35 @@ class Reconstruction:
         self.projector.ensure_capacity(*self.act)
         self.voxelizer.ensure_capacity(*self.act)
 
+    def _tv_branch(self, accumulate: bool):
+        """Voxelize -> TV (fused value and gradient) -> voxelizer backward into self.grads."""
+        L = B.lib()
+        s = B.stream_handle()
+        self.voxelizer.forward(*self.act, out=self.vol)
+        dz, dy, dx = self.vol.shape
+        B.check(L.gs_tv3d_loss(B.ptr(self.vol), dx, dy, dz, self.cfg.alpha_tv, B.ptr(self.loss),
+                               B.ptr(self.dvol), 0, s), "gs_tv3d_loss")
+        self.voxelizer.backward(*self.act, self.dvol, grads=self.grads, accumulate=accumulate,
+                                reuse=True)
+
     def step(self):
-        """One full iteration; the loss lands in self.loss (device), no host synchronisation."""
+        """One full iteration; the loss lands in self.loss (device), no host synchronisation.
+
+        With cfg.overlap_tv the TV branch (it needs only the parameters) runs on a second
+        stream while the projection, its losses and its backward run on the current one; the
+        branch writes the gradients first and the projection's backward adds to them."""
         L = B.lib()
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
+        branch = cfg.alpha_tv > 0 and cfg.overlap_tv
+        if branch:
+            main = torch.cuda.current_stream(self.device)
+            if not hasattr(self, "_side"):
+                self._side = torch.cuda.Stream(device=self.device)
+            self._side.wait_stream(main)
+            with torch.cuda.stream(self._side):
+                self._tv_branch(accumulate=False)
         self.projector.forward(*self.act, out=self.img)
         n_img = self.img.numel()
         B.check(L.gs_l1_loss(B.ptr(self.img), B.ptr(self.target), n_img, 1.0, B.ptr(self.loss),
@@ -124,15 +148,12 @@ class Reconstruction:
                                      self.H, self.W, self.data_range, cfg.alpha_ssim,
                                      B.ptr(self.loss), B.ptr(self.dimg), 1, B.ptr(self.ssim_ws),
                                      self.ssim_ws.numel(), s), "gs_ssim2d_loss")
-        self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=False,
+        if branch:
+            main.wait_stream(self._side)
+        self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=branch,
                                 reuse=not cfg.recompute_lists, stats=self.density_stats)
-        if cfg.alpha_tv > 0:
-            self.voxelizer.forward(*self.act, out=self.vol)
-            dz, dy, dx = self.vol.shape
-            B.check(L.gs_tv3d_loss(B.ptr(self.vol), dx, dy, dz, cfg.alpha_tv, B.ptr(self.loss),
-                                   B.ptr(self.dvol), 0, s), "gs_tv3d_loss")
-            self.voxelizer.backward(*self.act, self.dvol, grads=self.grads, accumulate=True,
-                                    reuse=True)
+        if cfg.alpha_tv > 0 and not branch:
+            self._tv_branch(accumulate=True)
         B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
                                *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
