@@ -4,9 +4,10 @@ single batched call per pass, one Adam launch over all parameters, and the whole
 in one CUDA graph.
 
 Per step: batched projection -> per-instance L1 + D-SSIM (loss kernels on each instance's
-256-byte-aligned image block) -> batched per-Gaussian backward -> batched voxelization of every
-instance's full grid -> per-instance TV -> batched voxelizer backward (accumulated) -> Adam.
-Instance k's loss lands in loss[k].
+256-byte-aligned image block) -> batched per-Gaussian backward (accumulated) -> Adam, with the
+TV branch (batched voxelization of every instance's full grid -> per-instance TV -> batched
+voxelizer backward) on a second stream beside the projection, joined before the projection's
+backward.  Instance k's loss lands in loss[k].
 """
 from __future__ import annotations
 
@@ -103,12 +104,35 @@ class BatchReconstruction:
         return (B.read_status(self.projector.ws).code != B.GS_OK or
                 B.read_status(self.voxelizer.ws).code != B.GS_OK)
 
+    def _tv_branch(self, accumulate: bool):
+        """Batched voxelization -> per-instance TV -> batched voxelizer backward."""
+        L = B.lib()
+        s = B.stream_handle()
+        lp = self.loss.data_ptr()
+        self.voxelizer.forward(*self.act, self.counts, out=self.vol)
+        for k in range(self.K):
+            dz, dy, dx = self.vols[k].shape
+            B.check(L.gs_tv3d_loss(B.ptr(self.vols[k]), dx, dy, dz, self.cfg.alpha_tv, lp + 4 * k,
+                                   B.ptr(self.dvols[k]), 0, s), "gs_tv3d_loss")
+        self.voxelizer.backward(*self.act, self.counts, self.dvol, grads=self.grads,
+                                accumulate=accumulate, reuse=True)
+
     def step(self):
         """One iteration of every instance; losses land in self.loss (device), no host sync."""
         L = B.lib()
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4 * self.K, s), "gs_memset")
+        # the TV branch needs only the parameters: it runs on a second stream beside the
+        # projection and writes the gradients first; the projection's backward adds to them
+        branch = cfg.alpha_tv > 0 and cfg.overlap_tv
+        if branch:
+            main = torch.cuda.current_stream(self.device)
+            if not hasattr(self, "_side"):
+                self._side = torch.cuda.Stream(device=self.device)
+            self._side.wait_stream(main)
+            with torch.cuda.stream(self._side):
+                self._tv_branch(accumulate=False)
         self.projector.forward(*self.act, self.counts, out=self.img)
         lp = self.loss.data_ptr()
         for k in range(self.K):
@@ -121,16 +145,12 @@ class BatchReconstruction:
                                          cfg.alpha_ssim, lp + 4 * k, B.ptr(dimg), 1,
                                          B.ptr(self.ssim_ws), self.ssim_ws.numel(), s),
                         "gs_ssim2d_loss")
+        if branch:
+            main.wait_stream(self._side)
         self.projector.backward(*self.act, self.counts, self.dimg, grads=self.grads,
-                                accumulate=False, reuse=True)
-        if cfg.alpha_tv > 0:
-            self.voxelizer.forward(*self.act, self.counts, out=self.vol)
-            for k in range(self.K):
-                dz, dy, dx = self.vols[k].shape
-                B.check(L.gs_tv3d_loss(B.ptr(self.vols[k]), dx, dy, dz, cfg.alpha_tv, lp + 4 * k,
-                                       B.ptr(self.dvols[k]), 0, s), "gs_tv3d_loss")
-            self.voxelizer.backward(*self.act, self.counts, self.dvol, grads=self.grads,
-                                    accumulate=True, reuse=True)
+                                accumulate=branch, reuse=True)
+        if cfg.alpha_tv > 0 and not branch:
+            self._tv_branch(accumulate=True)
         B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
                                *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),

@@ -1,6 +1,7 @@
 """One optimisation step of Gaussian-splatting CT reconstruction (Eq. 5, Fig. 2 loop) through
-libgsct calls only: project -> L1 + D-SSIM (fused fwd/bwd) -> per-Gaussian backward ->
-voxelize -> TV (fused) -> voxelizer backward (accumulated) -> Adam with activations.
+libgsct calls only: project -> L1 + D-SSIM (fused fwd/bwd) -> per-Gaussian backward -> Adam
+with activations, and beside the projection (second stream) voxelize -> TV (fused) ->
+voxelizer backward, whose gradients the projection's backward adds to.
 
 PyTorch only allocates the device buffers and provides the stream.
 """
