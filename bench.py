@@ -205,9 +205,8 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         rec.step()
     torch.cuda.synchronize()
-    st = rec.projector.status()
-    if st.code != 0:
-        raise RuntimeError(f"projector workspace status {st.code}")
+    if rec.overflowed():
+        raise RuntimeError("a workspace of the step ran out of pair capacity")
 
     clocks = ClockSampler(local)
     stream = torch.cuda.current_stream()
@@ -879,7 +878,7 @@ def scale_up(device, steps=5, warmup=3):
         ms = a.elapsed_time(b) / steps
         out[name] = {"ms_per_step": round(ms, 3), "evals_per_step": evals,
                      "value": evals / (ms * 1e-3), "unit": "evals/s", "tile": tile,
-                     "tile_timings_ms": tune_ms, "status": int(rec.projector.status().code)}
+                     "tile_timings_ms": tune_ms, "status": 1 if rec.overflowed() else 0}
         del rec, target
         torch.cuda.empty_cache()
     return out

@@ -500,6 +500,10 @@ int gs_densify(const float* d_raw_mean_rho, const float* d_raw_scale, const floa
 /* *d_step += 1 on the device (step counter of gs_adam_flat users). */
 int gs_step_incr(int* d_step, void* stream);
 
+/* d_dst[i] += d_src[i] for n floats (both 16-byte aligned; e.g. adding the gradients of a second
+ * set of views computed on another stream). */
+int gs_add(float* d_dst, const float* d_src, int64_t n, void* stream);
+
 /* Activated parameters from raw ones (same activations as gs_adam_step). */
 int gs_activate(const float* d_raw_mean_rho, const float* d_raw_scale, const float* d_raw_quat,
                 float* d_mean_rho, float* d_scale, float* d_quat, int n, void* stream);

@@ -154,6 +154,7 @@ SIGNATURES = {
     "gs_densify_workspace_size": (_SZ, [_I]),
     "gs_densify": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(GsDensifyOpts), _P, _P,
                         _P, _P, _P, _I, _P, _SZ, _P]),
+    "gs_add": (_I, [_P, _P, _I64, _P]),
     "gs_activate": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
     "gs_phantom_project": (_I, [_P, _I, _P, _I, _I, _I, _P, _P]),
     "gs_phantom_voxelize": (_I, [_P, _I, _GRID, _P, _P]),

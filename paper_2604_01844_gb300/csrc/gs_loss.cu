@@ -514,6 +514,23 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void k_step_incr(int* step) { *step += 1; }
 
+// dst += src over n floats (float4 body, scalar tail)
+__global__ void __launch_bounds__(kThreads)
+    k_add(float* __restrict__ dst, const float* __restrict__ src, int64_t n) {
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += stride) {
+    float4 a = d4[i];
+    const float4 b = s4[i];
+    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+    d4[i] = a;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride)
+    dst[i] += src[i];
+}
+
 // sum of squared differences in FP64 (for PSNR)
 __global__ void __launch_bounds__(kThreads)
     k_sse(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
@@ -578,6 +595,13 @@ int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, floa
   if (n == 0) return GS_OK;
   return launch("l1_loss", k_l1, dim3(grid_for(n / 4 + 1)), dim3(kThreads), 0,
                 (cudaStream_t)stream, d_a, d_b, n, weight / (float)n, d_loss, d_grad, accumulate);
+}
+
+int gs_add(float* d_dst, const float* d_src, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_dst || !d_src)) || !al16(d_dst) || !al16(d_src)) return GS_ERR_ARG;
+  if (n == 0) return GS_OK;
+  return launch("add", k_add, dim3(grid_for(n / 4 + 1)), dim3(kThreads), 0, (cudaStream_t)stream,
+                d_dst, d_src, n);
 }
 
 int gs_step_incr(int* d_step, void* stream) {

@@ -66,7 +66,7 @@ def trajectory(rec, score: VolumeScore, iters: int, eval_every: int = 5, ssim: b
         e1.record()
         e1.synchronize()
         ms += e0.elapsed_time(e1)
-        if rec.projector.status().code != B.GS_OK or rec.voxelizer.status().code != B.GS_OK:
+        if rec.overflowed():
             rec.plan()
             replans += 1
             if graph:

@@ -37,6 +37,7 @@ class ReconConfig:
     tv_roi: tuple | None = None  # (lo, dim) of the TV region; None = whole grid
     recompute_lists: bool = False  # backward rebuilds the sorted lists instead of reusing them
     overlap_tv: bool = True  # the TV branch runs on a second stream beside the projection
+    view_streams: int = 2  # the views split into this many chunks, each on its own stream
 
 
 def inverse_softplus(x: np.ndarray) -> np.ndarray:
@@ -69,6 +70,13 @@ class Reconstruction:
         self.target = target.contiguous()
         self.W, self.H = int(W), int(H)
         self.projector = Projector(views, W, H, cut=cfg.cut, tile=cfg.tile, device=dev)
+        # view chunks of the pipelined step: (v0, v1, projector of those views)
+        nv = int(self.target.shape[0])
+        k = max(1, min(int(cfg.view_streams), nv))
+        bounds = [round(i * nv / k) for i in range(k + 1)]
+        self.vchunks = [] if k == 1 else [
+            (a, b, Projector(self.projector.views[a:b], W, H, cut=cfg.cut, tile=cfg.tile,
+                             device=dev)) for a, b in zip(bounds[:-1], bounds[1:])]
         if cfg.tv_roi is None:
             self.voxelizer = Voxelizer(grid, cut=cfg.cut, device=dev)
         else:
@@ -79,13 +87,19 @@ class Reconstruction:
         self.dvol = torch.empty_like(self.vol)
         self.ssim_ws = torch.empty(B.lib().gs_ssim_workspace_size(self.target.numel()),
                                    dtype=torch.uint8, device=dev)
+        per_view = self.target[0].numel()
+        self.chunk_ws = [torch.empty(B.lib().gs_ssim_workspace_size((b - a) * per_view),
+                                     dtype=torch.uint8, device=dev) for a, b, _ in self.vchunks]
+        self.chunk_grads = [[torch.zeros_like(t) for t in self.raw] for _ in self.vchunks[1:]]
+        self._streams = [torch.cuda.Stream(device=dev) for _ in self.vchunks[1:]]
         self.data_range = float(data_range if data_range is not None else float(self.target.max()))
         o = B.GsAdamOpts()
         o.lr_mean, o.lr_rho, o.lr_scale, o.lr_quat = cfg.lr_mean, cfg.lr_rho, cfg.lr_scale, cfg.lr_quat
         o.beta1, o.beta2, o.eps = cfg.beta1, cfg.beta2, cfg.eps
         o.min_log_scale, o.max_log_scale = cfg.min_log_scale, cfg.max_log_scale
         self.adam_opts = o
-        self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set
+        self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set;
+        # the step then runs unchunked (the statistics' per-Gaussian sums are not atomic)
         self.activate()
         self.plan()
 
@@ -98,6 +112,7 @@ class Reconstruction:
         self.act = [torch.empty_like(t) for t in self.raw]
         self.grads = [torch.zeros_like(t) for t in self.raw]
         self.m, self.v = m.contiguous(), v.contiguous()
+        self.chunk_grads = [[torch.zeros_like(t) for t in self.raw] for _ in self.vchunks[1:]]
         self.activate()
         self.plan()
 
@@ -107,9 +122,35 @@ class Reconstruction:
                               self.n, B.stream_handle()), "gs_activate")
 
     def plan(self):
-        """Size both workspaces for the current parameters (synchronous)."""
-        self.projector.ensure_capacity(*self.act)
+        """Size the workspaces for the current parameters (synchronous)."""
+        for _, _, pj in self.vchunks:
+            pj.ensure_capacity(*self.act)
+        if not self.vchunks or self.density_stats is not None:
+            self.projector.ensure_capacity(*self.act)  # the unchunked step's projector
         self.voxelizer.ensure_capacity(*self.act)
+
+    def overflowed(self) -> bool:
+        """True when the last step ran out of pair capacity somewhere (synchronises)."""
+        pjs = [pj for _, _, pj in self.vchunks]
+        if not pjs or self.density_stats is not None:
+            pjs.append(self.projector)
+        return any(pj.status().code != B.GS_OK for pj in pjs) or \
+            self.voxelizer.status().code != B.GS_OK
+
+    def _image_losses(self, a: int, b: int, ws: torch.Tensor):
+        """L1 + D-SSIM of views a..b-1 (their share of the all-view means) into self.loss and
+        self.dimg."""
+        L = B.lib()
+        s = B.stream_handle()
+        img, tgt, dimg = self.img[a:b], self.target[a:b], self.dimg[a:b]
+        share = img.numel() / self.img.numel()
+        B.check(L.gs_l1_loss(B.ptr(img), B.ptr(tgt), img.numel(), share, B.ptr(self.loss),
+                             B.ptr(dimg), 0, s), "gs_l1_loss")
+        if self.cfg.alpha_ssim > 0:
+            B.check(L.gs_ssim2d_loss(B.ptr(img), B.ptr(tgt), b - a, self.H, self.W,
+                                     self.data_range, self.cfg.alpha_ssim * share,
+                                     B.ptr(self.loss), B.ptr(dimg), 1, B.ptr(ws), ws.numel(), s),
+                    "gs_ssim2d_loss")
 
     def _tv_branch(self, accumulate: bool):
         """Voxelize -> TV (fused value and gradient) -> voxelizer backward into self.grads."""
@@ -132,6 +173,8 @@ class Reconstruction:
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
+        if self.vchunks and self.density_stats is None:
+            return self._step_pipelined()
         branch = cfg.alpha_tv > 0 and cfg.overlap_tv
         if branch:
             main = torch.cuda.current_stream(self.device)
@@ -155,6 +198,48 @@ class Reconstruction:
                                 reuse=not cfg.recompute_lists, stats=self.density_stats)
         if cfg.alpha_tv > 0 and not branch:
             self._tv_branch(accumulate=True)
+        B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
+                               *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
+                               self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
+                "gs_adam_step")
+        return self.loss
+
+    def _step_pipelined(self):
+        """The step with the views in chunks, chunk 0 on the current stream and chunk k on
+        stream k: each chunk projects, takes its losses and runs its backward independently, so
+        that one chunk's binning and sorting overlap another's rasterization.  The TV branch
+        (its own stream) writes self.grads first, chunk 0 adds to them, the other chunks write
+        their own gradient buffers, which are added before Adam."""
+        L = B.lib()
+        cfg = self.cfg
+        main = torch.cuda.current_stream(self.device)
+        tv = cfg.alpha_tv > 0
+        if tv:
+            if not hasattr(self, "_side"):
+                self._side = torch.cuda.Stream(device=self.device)
+            self._side.wait_stream(main)
+            with torch.cuda.stream(self._side):
+                self._tv_branch(accumulate=False)
+        for st in self._streams:
+            st.wait_stream(main)
+        for k, (a, b, pj) in enumerate(self.vchunks):
+            st = main if k == 0 else self._streams[k - 1]
+            with torch.cuda.stream(st):
+                pj.forward(*self.act, out=self.img[a:b])
+                self._image_losses(a, b, self.chunk_ws[k])
+                if k == 0:
+                    if tv:
+                        main.wait_stream(self._side)
+                    pj.backward(*self.act, self.dimg[a:b], grads=self.grads, accumulate=tv,
+                                reuse=not cfg.recompute_lists)
+                else:
+                    pj.backward(*self.act, self.dimg[a:b], grads=self.chunk_grads[k - 1],
+                                accumulate=False, reuse=not cfg.recompute_lists)
+        s = B.stream_handle()
+        for st, g in zip(self._streams, self.chunk_grads):
+            main.wait_stream(st)
+            for dst, src in zip(self.grads, g):
+                B.check(L.gs_add(B.ptr(dst), B.ptr(src), dst.numel(), s), "gs_add")
         B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
                                *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
