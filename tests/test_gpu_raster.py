@@ -261,8 +261,10 @@ def test_autograd_function(gsct):
     w = torch.randn_like(img)
     (img * w).sum().backward()
     ref = proj.backward(*[t.detach() for t in d], w, reuse=False)
+    # the two backward calls sum with float atomics in no fixed order: entries agree to a few
+    # ulp of the terms summed, i.e. relative to the gradient's scale, not to each entry
     for t, r in zip(d, ref):
-        assert torch.allclose(t.grad, r, rtol=1e-5, atol=1e-6)
+        assert torch.allclose(t.grad, r, rtol=1e-5, atol=1e-5 * float(r.abs().max()))
 
 
 def test_full_size_sampled_pixels(orc, gsct):
