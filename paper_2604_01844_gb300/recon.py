@@ -163,19 +163,22 @@ class Reconstruction:
         self.voxelizer.backward(*self.act, self.dvol, grads=self.grads, accumulate=accumulate,
                                 reuse=True)
 
-    def step(self):
+    def step(self, serial: bool = False):
         """One full iteration; the loss lands in self.loss (device), no host synchronisation.
 
         With cfg.overlap_tv the TV branch (it needs only the parameters) runs on a second
         stream while the projection, its losses and its backward run on the current one; the
-        branch writes the gradients first and the projection's backward adds to them."""
+        branch writes the gradients first and the projection's backward adds to them.  With
+        cfg.view_streams > 1 the views also run in chunks on their own streams.  serial = True
+        runs everything on the current stream with the views unchunked (the same arithmetic
+        per pixel and voxel; used to time each kernel on its own)."""
         L = B.lib()
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
-        if self.vchunks and self.density_stats is None:
+        if self.vchunks and self.density_stats is None and not serial:
             return self._step_pipelined()
-        branch = cfg.alpha_tv > 0 and cfg.overlap_tv
+        branch = cfg.alpha_tv > 0 and cfg.overlap_tv and not serial
         if branch:
             main = torch.cuda.current_stream(self.device)
             if not hasattr(self, "_side"):
