@@ -244,7 +244,9 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API with host buffers: per step the parameters and the
     # target projections go host->device from pinned memory, the loss and the updated
-    # parameters come back device->host
+    # parameters come back device->host.  The target copy runs on a copy stream (after the
+    # previous step has finished reading the target) and only the image losses wait for it, so
+    # it overlaps the projection forward.
     h_params = [t.detach().cpu().pin_memory() for t in rec.raw]
     h_target = rec.target.detach().cpu().pin_memory()
     h_out = [torch.empty_like(t, device="cpu").pin_memory() for t in rec.act]
@@ -254,13 +256,18 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
+    copy = torch.cuda.Stream(device=device)
     e2.record(stream)
     for _ in range(args.steps):
         for d, h in zip(rec.raw, h_params):
             d.copy_(h, non_blocking=True)
-        rec.target.copy_(h_target, non_blocking=True)
+        copy.wait_stream(stream)
+        with torch.cuda.stream(copy):
+            rec.target.copy_(h_target, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(copy)
         rec.activate()
-        rec.step()
+        rec.step(target_ready=ready)
         for d, h in zip(rec.act, h_out):
             h.copy_(d, non_blocking=True)
         h_loss.copy_(rec.loss, non_blocking=True)

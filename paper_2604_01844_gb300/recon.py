@@ -163,7 +163,7 @@ class Reconstruction:
         self.voxelizer.backward(*self.act, self.dvol, grads=self.grads, accumulate=accumulate,
                                 reuse=True)
 
-    def step(self, serial: bool = False):
+    def step(self, serial: bool = False, target_ready=None):
         """One full iteration; the loss lands in self.loss (device), no host synchronisation.
 
         With cfg.overlap_tv the TV branch (it needs only the parameters) runs on a second
@@ -171,13 +171,15 @@ class Reconstruction:
         branch writes the gradients first and the projection's backward adds to them.  With
         cfg.view_streams > 1 the views also run in chunks on their own streams.  serial = True
         runs everything on the current stream with the views unchunked (the same arithmetic
-        per pixel and voxel; used to time each kernel on its own)."""
+        per pixel and voxel; used to time each kernel on its own).  target_ready: a CUDA event
+        after which self.target holds this step's projections (e.g. a host->device copy on
+        another stream); only the image losses wait for it."""
         L = B.lib()
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
         if self.vchunks and self.density_stats is None and not serial:
-            return self._step_pipelined()
+            return self._step_pipelined(target_ready)
         branch = cfg.alpha_tv > 0 and cfg.overlap_tv and not serial
         if branch:
             main = torch.cuda.current_stream(self.device)
@@ -187,6 +189,8 @@ class Reconstruction:
             with torch.cuda.stream(self._side):
                 self._tv_branch(accumulate=False)
         self.projector.forward(*self.act, out=self.img)
+        if target_ready is not None:
+            torch.cuda.current_stream(self.device).wait_event(target_ready)
         n_img = self.img.numel()
         B.check(L.gs_l1_loss(B.ptr(self.img), B.ptr(self.target), n_img, 1.0, B.ptr(self.loss),
                              B.ptr(self.dimg), 0, s), "gs_l1_loss")
@@ -207,7 +211,7 @@ class Reconstruction:
                 "gs_adam_step")
         return self.loss
 
-    def _step_pipelined(self):
+    def _step_pipelined(self, target_ready=None):
         """The step with the views in chunks, chunk 0 on the current stream and chunk k on
         stream k: each chunk projects, takes its losses and runs its backward independently, so
         that one chunk's binning and sorting overlap another's rasterization.  The TV branch
@@ -229,6 +233,8 @@ class Reconstruction:
             st = main if k == 0 else self._streams[k - 1]
             with torch.cuda.stream(st):
                 pj.forward(*self.act, out=self.img[a:b])
+                if target_ready is not None:
+                    st.wait_event(target_ready)
                 self._image_losses(a, b, self.chunk_ws[k])
                 if k == 0:
                     if tv:
