@@ -377,8 +377,9 @@ int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float
 /* Scratch bytes of gs_ssim2d_loss for n_elems image pixels (3 maps). */
 size_t gs_ssim_workspace_size(int64_t n_elems);
 
-/* Scratch bytes of gs_ssim3d_loss for n_voxels voxels: 3 maps plus 5 volumes of xy-filtered
- * planes (the 3D filter runs as an xy pass per plane and a streaming z pass). */
+/* Scratch bytes of gs_ssim3d_loss for n_voxels voxels: the 3 derivative maps plus 5 volumes
+ * of z-filtered moments (the 3D filter runs as a streaming z pass and an xy pass per plane),
+ * each stored as float2 pairs plus one float volume. */
 size_t gs_ssim3d_workspace_size(int64_t n_voxels);
 
 /* D-SSIM term of Eq. 5: weight * (1 - mean SSIM(x, y)) over n_img images of H x W, SSIM of
