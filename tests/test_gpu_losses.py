@@ -156,3 +156,37 @@ def test_recon_step_decreases_loss(B):
     for _ in range(30):
         losses.append(float(rec.step().item()))
     assert losses[-1] < 0.8 * losses[0], losses[::5]
+
+
+@pytest.mark.parametrize("chunks", [2, 3])
+def test_pipelined_step_equals_serial_step(B, chunks):
+    """The step with the TV branch and view chunks on their own streams computes what the serial
+    step computes: the same images and volume (bit-identical), the loss to rounding (its terms
+    are summed in another order), the same parameter update up to Adam's sign flips of
+    gradients near zero (unordered float atomics)."""
+    import synth
+    import paper_2604_01844_gb300 as g
+    from paper_2604_01844_gb300.recon import ReconConfig, Reconstruction
+
+    views = synth.cone_views(9, 64, 56)
+    model = synth.gaussians(40, 2000, scale_median=0.03)
+    tgt = synth.gaussians(41, 2000, scale_median=0.03)
+    target = g.Projector(views, 64, 56).forward(*[torch.from_numpy(a).cuda() for a in tgt])
+    recs = [Reconstruction(views, 64, 56, target.clone(), synth.cube_grid(40), *model,
+                           cfg=ReconConfig(lr_mean=1e-3, lr_rho=2e-2, view_streams=k))
+            for k in (chunks, 1)]
+    assert len(recs[0].vchunks) == chunks and not recs[1].vchunks
+    la = float(recs[0].step().item())
+    lb = float(recs[1].step(serial=True).item())
+    torch.cuda.synchronize()
+    assert torch.equal(recs[0].img, recs[1].img)
+    assert torch.equal(recs[0].vol, recs[1].vol)
+    assert abs(la - lb) <= 1e-5 * abs(lb), (la, lb)
+    for x, y in zip(recs[0].act, recs[1].act):
+        close = torch.isclose(x, y, rtol=1e-5, atol=1e-6).float().mean().item()
+        assert close > 0.99, close
+    # and over a few more steps the two runs stay together
+    for _ in range(4):
+        la = float(recs[0].step().item())
+        lb = float(recs[1].step(serial=True).item())
+    assert abs(la - lb) <= 1e-3 * abs(lb), (la, lb)
