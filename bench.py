@@ -72,10 +72,19 @@ def alu_peaks(device, blocks_per_sm=8, iters=2048):
     return out
 
 
-def eval_peak(kernel, peaks):
-    """Roofline of an evaluation kernel in evaluations/s and its binding unit."""
-    sfu = peaks["ex2_per_s"]
-    fp32 = peaks["fma_per_s"] / FP32_OPS_PER_EVAL[kernel]
+# Unit counts per SM per clock: 128 FP32 lanes; 32 ex2 on the special-function unit (GB300
+# doubles the 16 of earlier parts; the probe kernels measure 31.5 and 118 per SM per clock,
+# 98 % and 92 % of these counts, and their rates are reported beside the roofline).
+FP32_LANES_PER_SM = 128
+EX2_PER_SM = 32
+
+
+def eval_peak(kernel, sms, f_mhz):
+    """Roofline of an evaluation kernel in evaluations/s (SMs x clock x the binding unit's
+    rate per evaluation) and the binding unit."""
+    clk = sms * f_mhz * 1e6
+    sfu = clk * EX2_PER_SM
+    fp32 = clk * FP32_LANES_PER_SM / FP32_OPS_PER_EVAL[kernel]
     return (sfu, "sfu") if sfu <= fp32 else (fp32, "fp32")
 
 
@@ -295,17 +304,18 @@ def run_ours(args, ws, rank, local):
     per_clk = {k: round(v / (sms * f_mhz * 1e6), 2) for k, v in peaks.items() if k != "sms"}
     if name in FP32_OPS_PER_EVAL:
         units = evals_px if name.startswith("raster") else evals_vox
-        peak_s, unit_name = eval_peak(name, peaks)
+        peak_s, unit_name = eval_peak(name, sms, f_mhz)
         peak = peak_s / 1e9
         ach = units / (avg_ms * 1e-3) / 1e9
         roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2),
                 "unit": "Geval/s", "frac": round(ach / peak, 4), "traffic": read_traffic(name),
-                "peak_basis": f"measured by the probe kernels: ex2 {peaks['ex2_per_s'] / 1e9:.0f} "
-                              f"G/s ({per_clk['ex2_per_s']} per SM per clock at {f_mhz:.0f} MHz), "
-                              f"fp32 fma {peaks['fma_per_s'] / 1e9:.0f} G/s "
-                              f"({per_clk['fma_per_s']}); one ex2 and "
-                              f"{FP32_OPS_PER_EVAL[name]} FP32 operations per evaluation, "
-                              f"bound by the {unit_name}",
+                "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz (median sampled) x min({EX2_PER_SM} "
+                              f"ex2, {FP32_LANES_PER_SM} FP32 lanes / "
+                              f"{FP32_OPS_PER_EVAL[name]} ops) per SM per clock: one ex2 and "
+                              f"{FP32_OPS_PER_EVAL[name]} FP32 operations per evaluation, bound "
+                              f"by the {unit_name}; the probe kernels measure "
+                              f"{per_clk['ex2_per_s']} ex2 and {per_clk['fma_per_s']} fma per "
+                              f"SM per clock",
                 "avg_launch_ms": round(avg_ms, 4), "launches": nl}
     else:
         roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": mp.get("hbm_gbs"),
@@ -319,7 +329,7 @@ def run_ours(args, ws, rank, local):
             continue
         kl, kt = per_kernel[kname]
         units = evals_px if kname.startswith("raster") else evals_vox
-        kpeak = eval_peak(kname, peaks)[0] / 1e9
+        kpeak = eval_peak(kname, sms, f_mhz)[0] / 1e9
         kach = units / ((kt / max(kl, 1)) * 1e-3) / 1e9
         kernel_roofs[kname] = {"achieved": round(kach, 2), "peak": round(kpeak, 2),
                                "unit": "Geval/s", "frac": round(kach / kpeak, 4),
