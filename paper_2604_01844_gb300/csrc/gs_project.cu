@@ -467,16 +467,37 @@ struct BlockShape {
 template <int T>
 using BwdBlocks = BlockShape<T, (T >= 16 ? 16 : 8)>;
 
+// Raster forward (and the in-cut evaluation counter) with records on lanes, one warp per
+// 4 x BW block of the (view, tile).  Per batch of staged records each warp lists the records
+// whose cut ellipse reaches its block (the block masks of the backward) and takes them one per
+// lane; every lane walks the block's pixels in the same unrolled order (pixel pairs in packed
+// FP32x2 arithmetic, the exponent and the cut exactly as the backward computes them) and adds
+// A 2^e to its own accumulator of each pixel.  The accumulators live through all batches; at
+// the end one butterfly reduce-scatter over the warp's lanes sums them per pixel, lane l
+// keeping pixels 2l and 2l + 1.  A pixel's sum is thus taken in a fixed order: per lane in
+// list order, then over the lanes.
+template <int T>
+struct FwdBlocks {
+  static constexpr int BW = T >= 16 ? 16 : 8;  // block width; 4 rows
+  static constexpr int LBW = BW == 16 ? 4 : 3;
+  static constexpr int NBX = T / BW, NBY = T / 4, NB = NBX * NBY;
+  static constexpr int NW = NB;  // one block per warp
+  static constexpr int NT = 32 * NW;
+  static constexpr int NP = 2 * BW;  // float2 accumulators per lane (4 rows x BW / 2 pairs)
+};
+
 template <int T, bool COUNT>
-__global__ void __launch_bounds__(RasterShape<T>::NT, 2048 / RasterShape<T>::NT)
+__global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlocks<T>::NT)
     k_raster_fwd(const __grid_constant__ Batch b, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ vals, const float4* __restrict__ geo,
                  const float4* __restrict__ conic, const short4* __restrict__ rect,
                  float* __restrict__ img, gs_status* st) {
-  using S = RasterShape<T>;
+  using S = FwdBlocks<T>;
+  constexpr int BW = S::BW, HP = BW / 2;  // pixel pairs per row
   __shared__ float4 s_geo[S::NT];
   __shared__ float4 s_con[S::NT];
-  __shared__ uint32_t s_mask[S::NT];  // bit k: the record's box touches warp block k
+  __shared__ uint32_t s_mask[S::NT];
+  __shared__ uint16_t s_list[S::NW][S::NT];
   __shared__ unsigned long long s_cnt;
   if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
@@ -486,82 +507,108 @@ __global__ void __launch_bounds__(RasterShape<T>::NT, 2048 / RasterShape<T>::NT)
   const int W = I.W, H = I.H;
   const int tx0 = (tile % I.TW) * T, ty0 = (tile / I.TW) * T;
   const uint2 r = ranges[key];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int px0[S::BPW], py[S::BPW];
-  float fx[S::BPW][S::PX], fy[S::BPW], acc[S::BPW][S::PX];
-  uint32_t cnt = 0;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int bxl = (w % S::NBX) * BW, byl = (w / S::NBX) * 4;  // the warp's block in the tile
+  const float fx0 = (float)(tx0 + bxl), fy0 = (float)(ty0 + byl);
+  const unsigned lt = gsd::lanemask_lt();
+  constexpr int NPR = 4 * HP;  // float2 accumulators per lane: pair ry * HP + p
+  float2 acc[NPR];
 #pragma unroll
-  for (int k = 0; k < S::BPW; ++k) {
-    const int wb = w + k * S::NW;
-    px0[k] = tx0 + (wb % S::NBX) * S::BW + (lane & 7);
-    py[k] = ty0 + (wb / S::NBX) * 4 + (lane >> 3);
-    fy[k] = (float)py[k];
-#pragma unroll
-    for (int q = 0; q < S::PX; ++q) {
-      fx[k][q] = (float)(px0[k] + 8 * q);
-      acc[k][q] = 0.f;
-    }
-  }
-  if (COUNT && threadIdx.x == 0) s_cnt = 0ull;
+  for (int i = 0; i < NPR; ++i) acc[i] = make_float2(0.f, 0.f);
+  uint32_t cnt_eval = 0;
+  if (COUNT && t == 0) s_cnt = 0ull;
   for (uint32_t base = r.x; base < r.y; base += S::NT) {
     const int m = (int)min((uint32_t)S::NT, r.y - base);
     __syncthreads();
-    if ((int)threadIdx.x < m) {
-      const uint32_t rec = vals[base + threadIdx.x];
+    if (t < m) {
+      const uint32_t rec = vals[base + t];
       const float4 g = geo[rec], c = conic[rec];
-      s_geo[threadIdx.x] = g;
-      s_con[threadIdx.x] = c;
-      s_mask[threadIdx.x] =
-          block_mask<T, S::BW, S::LBW, S::NBX, S::NBY>(g, c, rect[rec], tx0, ty0);
+      s_geo[t] = g;
+      s_con[t] = c;
+      s_mask[t] = block_mask<T, BW, S::LBW, S::NBX, S::NBY>(g, c, rect[rec], tx0, ty0);
     }
     __syncthreads();
+    int cnt = 0;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      const int jl = j0 + lane;
+      const bool hit = jl < m && ((s_mask[jl] >> w) & 1u);
+      const unsigned bits = __ballot_sync(0xffffffffu, hit);
+      if (hit) s_list[w][cnt + __popc(bits & lt)] = (uint16_t)jl;
+      cnt += __popc(bits);
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      const int li = c0 + lane;
+      const bool active = li < cnt;
+      const int j = active ? s_list[w][li] : 0;
+      const float4 g = s_geo[j];
+      const float4 c = s_con[j];
+      const float cut = active ? g.w : 1.f;  // e <= 0 < 1: an idle lane never passes
+      float2 dx[HP];
 #pragma unroll
-    for (int k = 0; k < S::BPW; ++k) {
-      const int wb = w + k * S::NW;
-      // each warp visits only the records that touch its block: a ballot over 32 records
-      // at a time, then one iteration per set bit
-      for (int j0 = 0; j0 < m; j0 += 32) {
-        const int jl = j0 + lane;
-        unsigned bits = __ballot_sync(0xffffffffu, jl < m && ((s_mask[jl] >> wb) & 1u));
-        while (bits) {
-          const int j = j0 + __ffs(bits) - 1;
-          bits &= bits - 1u;
-          const float4 g = s_geo[j];
-          const float4 c = s_con[j];
-          const float dy = fy[k] - g.y;
-          const float bdy = row_b(c, dy), cdy2 = row_c(c, dy);
+      for (int p = 0; p < HP; ++p)
+        dx[p] = make_float2(fx0 + (float)(2 * p) - g.x, fx0 + (float)(2 * p + 1) - g.x);
+      const float2 ca = make_float2(c.x, c.x), A2 = make_float2(g.z, g.z);
 #pragma unroll
-          for (int q = 0; q < S::PX; ++q) {
-            const float e = expo(c, fx[k][q] - g.x, bdy, cdy2);
-            if (COUNT) {
-              cnt += (e > g.w && fx[k][q] < (float)W && fy[k] < (float)H) ? 1u : 0u;
-            } else {
-              const float val = ex2(e);
-              acc[k][q] = e > g.w ? fmaf(g.z, val, acc[k][q]) : acc[k][q];
-            }
+      for (int ry = 0; ry < 4; ++ry) {
+        const float dy = (fy0 + (float)ry) - g.y;
+        const float B = row_b(c, dy), cdy2 = row_c(c, dy);
+        const float2 B2 = make_float2(B, B), C2 = make_float2(cdy2, cdy2);
+#pragma unroll
+        for (int p = 0; p < HP; ++p) {
+          const float2 e = __ffma2_rn(__ffma2_rn(ca, dx[p], B2), dx[p], C2);
+          if (COUNT) {
+            const int x = tx0 + bxl + 2 * p, y = ty0 + byl + ry;
+            cnt_eval += (e.x > cut && x < W && y < H) ? 1u : 0u;
+            cnt_eval += (e.y > cut && x + 1 < W && y < H) ? 1u : 0u;
+          } else {
+            const float2 val =
+                make_float2(e.x > cut ? ex2(e.x) : 0.f, e.y > cut ? ex2(e.y) : 0.f);
+            acc[ry * HP + p] = __ffma2_rn(A2, val, acc[ry * HP + p]);
           }
         }
       }
     }
+    __syncwarp();
   }
   if (COUNT) {
     __syncthreads();
-    const uint32_t ws = gsd::warp_sum(cnt);
+    const uint32_t ws = gsd::warp_sum(cnt_eval);
     if (lane == 0 && ws) atomicAdd(&s_cnt, (unsigned long long)ws);
     __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) atomicAdd((unsigned long long*)&st->evals, s_cnt);
+    if (t == 0 && s_cnt) atomicAdd((unsigned long long*)&st->evals, s_cnt);
     return;
   }
-  float* im = img + I.img_off + (int64_t)v * H * W;
+  // butterfly reduce-scatter of the warp's 4 x BW pixel sums: at each stage a lane keeps the
+  // half of its pairs on its side of the partner bit and adds the partner's copy of that half;
+  // after log2(NPR) stages lane l holds the sum of pair l % NPR over its group of NPR lanes
 #pragma unroll
-  for (int k = 0; k < S::BPW; ++k) {
-    if (py[k] >= H) continue;
+  for (int half = NPR / 2; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
 #pragma unroll
-    for (int q = 0; q < S::PX; ++q) {
-      const int x = px0[k] + 8 * q;
-      if (x < W) im[(size_t)py[k] * W + x] = acc[k][q];
+    for (int i = 0; i < half; ++i) {
+      const float2 mine = up ? acc[i + half] : acc[i];
+      const float2 send = up ? acc[i] : acc[i + half];
+      float2 recv;
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, half);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, half);
+      acc[i] = __fadd2_rn(mine, recv);
     }
   }
+  // fewer pairs than lanes (BW = 8): the groups' sums are added across the remaining bits
+#pragma unroll
+  for (int k = NPR; k < 32; k <<= 1) {
+    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, acc[0].x, k),
+                                 __shfl_xor_sync(0xffffffffu, acc[0].y, k));
+    acc[0] = __fadd2_rn(acc[0], o);
+  }
+  const int pi = lane % NPR;  // pair index: row pi / HP, columns 2 (pi % HP) + {0, 1}
+  if (lane >= NPR) return;
+  const int y = ty0 + byl + pi / HP, x = tx0 + bxl + 2 * (pi % HP);
+  if (y >= H) return;
+  float* row = img + I.img_off + ((int64_t)v * H + y) * W;
+  if (x < W) row[x] = acc[0].x;
+  if (x + 1 < W) row[x + 1] = acc[0].y;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -870,7 +917,7 @@ int bin_pairs(const Plan& p, const Layout& L, const float* mr, const float* sc, 
 template <int T>
 int raster_fwd(const Plan& p, const Layout& L, const uint32_t* vals, float* img, bool count,
                cudaStream_t s) {
-  dim3 grid((unsigned)p.n_keys), block(RasterShape<T>::NT);
+  dim3 grid((unsigned)p.n_keys), block(FwdBlocks<T>::NT);
   if (count)
     return launch("raster_count", k_raster_fwd<T, true>, grid, block, 0, s, p.b,
                   (const uint2*)L.ranges, vals, (const float4*)L.geo, (const float4*)L.conic,
