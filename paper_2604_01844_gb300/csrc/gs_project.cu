@@ -484,6 +484,7 @@ struct FwdBlocks {
   static constexpr int NW = NB;  // one block per warp
   static constexpr int NT = 32 * NW;
   static constexpr int NP = 2 * BW;  // float2 accumulators per lane (4 rows x BW / 2 pairs)
+  static constexpr int SB = 2 * NT;  // records staged per batch (two per thread)
 };
 
 template <int T, bool COUNT>
@@ -494,10 +495,10 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
                  float* __restrict__ img, gs_status* st) {
   using S = FwdBlocks<T>;
   constexpr int BW = S::BW, HP = BW / 2;  // pixel pairs per row
-  __shared__ float4 s_geo[S::NT];
-  __shared__ float4 s_con[S::NT];
-  __shared__ uint32_t s_mask[S::NT];
-  __shared__ uint16_t s_list[S::NW][S::NT];
+  __shared__ float4 s_geo[S::SB];
+  __shared__ float4 s_con[S::SB];
+  __shared__ uint32_t s_mask[S::SB];
+  __shared__ uint16_t s_list[S::NW][S::SB];
   __shared__ unsigned long long s_cnt;
   if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
@@ -517,15 +518,15 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
   for (int i = 0; i < NPR; ++i) acc[i] = make_float2(0.f, 0.f);
   uint32_t cnt_eval = 0;
   if (COUNT && t == 0) s_cnt = 0ull;
-  for (uint32_t base = r.x; base < r.y; base += S::NT) {
-    const int m = (int)min((uint32_t)S::NT, r.y - base);
+  for (uint32_t base = r.x; base < r.y; base += S::SB) {
+    const int m = (int)min((uint32_t)S::SB, r.y - base);
     __syncthreads();
-    if (t < m) {
-      const uint32_t rec = vals[base + t];
+    for (int q = t; q < m; q += S::NT) {
+      const uint32_t rec = vals[base + q];
       const float4 g = geo[rec], c = conic[rec];
-      s_geo[t] = g;
-      s_con[t] = c;
-      s_mask[t] = block_mask<T, BW, S::LBW, S::NBX, S::NBY>(g, c, rect[rec], tx0, ty0);
+      s_geo[q] = g;
+      s_con[q] = c;
+      s_mask[q] = block_mask<T, BW, S::LBW, S::NBX, S::NBY>(g, c, rect[rec], tx0, ty0);
     }
     __syncthreads();
     int cnt = 0;
