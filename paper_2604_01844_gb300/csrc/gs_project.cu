@@ -634,12 +634,13 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
   using S = BwdBlocks<T>;
   constexpr int BW = S::BW;
   __shared__ __align__(16) float s_g[T][T];
-  __shared__ float4 s_geo[S::NT];
-  __shared__ float4 s_con[S::NT];
-  __shared__ uint32_t s_rec[S::NT];
-  __shared__ uint32_t s_mask[S::NT];
-  __shared__ float s_acc[6][S::NT];
-  __shared__ uint16_t s_list[S::NW][S::NT];
+  constexpr int SB = 2 * S::NT;  // records staged per batch (two per thread)
+  __shared__ float4 s_geo[SB];
+  __shared__ float4 s_con[SB];
+  __shared__ uint32_t s_rec[SB];
+  __shared__ uint32_t s_mask[SB];
+  __shared__ float s_acc[6][SB];
+  __shared__ uint16_t s_list[S::NW][SB];
   if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
   const uint2 r = ranges[key];
@@ -656,19 +657,19 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
     s_g[p / T][p % T] = (x < W && y < H) ? dv[(size_t)y * W + x] : 0.f;
   }
   const unsigned lt = gsd::lanemask_lt();
-  for (uint32_t base = r.x; base < r.y; base += S::NT) {
-    const int m = (int)min((uint32_t)S::NT, r.y - base);
+  for (uint32_t base = r.x; base < r.y; base += SB) {
+    const int m = (int)min((uint32_t)SB, r.y - base);
     __syncthreads();
-    if (t < m) {
-      const uint32_t rec = vals[base + t];
+    for (int q = t; q < m; q += S::NT) {
+      const uint32_t rec = vals[base + q];
       const float4 g = geo[rec], c = conic[rec];
       const short4 bx = rect[rec];
-      s_rec[t] = rec;
-      s_geo[t] = g;
-      s_con[t] = c;
+      s_rec[q] = rec;
+      s_geo[q] = g;
+      s_con[q] = c;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) s_acc[q][t] = 0.f;
-      s_mask[t] = block_mask<T, S::BW, S::LBW, S::NBX, S::NBY>(g, c, bx, tx0, ty0);
+      for (int k = 0; k < 6; ++k) s_acc[k][q] = 0.f;
+      s_mask[q] = block_mask<T, S::BW, S::LBW, S::NBX, S::NBY>(g, c, bx, tx0, ty0);
     }
     __syncthreads();
 #pragma unroll 1
@@ -739,11 +740,11 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
       __syncwarp();
     }
     __syncthreads();
-    if (t < m) {
-      const float a0 = s_acc[0][t], a1 = s_acc[1][t], a2 = s_acc[2][t];
-      const float a3 = s_acc[3][t], a4 = s_acc[4][t], a5 = s_acc[5][t];
+    for (int q = t; q < m; q += S::NT) {
+      const float a0 = s_acc[0][q], a1 = s_acc[1][q], a2 = s_acc[2][q];
+      const float a3 = s_acc[3][q], a4 = s_acc[4][q], a5 = s_acc[5][q];
       if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f) {
-        const uint32_t rec = s_rec[t];
+        const uint32_t rec = s_rec[q];
         atomicAdd(&fpgrad[2 * (size_t)rec], make_float4(a0, a1, a2, a3));
         atomicAdd(&fpgrad[2 * (size_t)rec + 1], make_float4(a4, a5, 0.f, 0.f));
       }
