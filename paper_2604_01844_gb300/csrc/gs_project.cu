@@ -484,7 +484,7 @@ struct FwdBlocks {
   static constexpr int NW = NB;  // one block per warp
   static constexpr int NT = 32 * NW;
   static constexpr int NP = 2 * BW;  // float2 accumulators per lane (4 rows x BW / 2 pairs)
-  static constexpr int SB = 2 * NT;  // records staged per batch (two per thread)
+  static constexpr int SB = (T == 32 ? 2 : 4) * NT;  // records staged per batch
 };
 
 template <int T, bool COUNT>
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
   using S = BwdBlocks<T>;
   constexpr int BW = S::BW;
   __shared__ __align__(16) float s_g[T][T];
-  constexpr int SB = 2 * S::NT;  // records staged per batch (two per thread)
+  constexpr int SB = 2 * S::NT;  // records staged per batch (more costs occupancy here)
   __shared__ float4 s_geo[SB];
   __shared__ float4 s_con[SB];
   __shared__ uint32_t s_rec[SB];
