@@ -439,19 +439,6 @@ __device__ __forceinline__ uint32_t block_mask(const float4 g, const float4 c, c
   return mask;
 }
 
-// Raster CTA shape: warps own blocks of 4 rows x (8 PX) columns; a lane owns PX pixels of one
-// row, 8 columns apart, so that one record's row terms serve PX pixels.
-template <int T>
-struct RasterShape {
-  static constexpr int PX = T >= 16 ? 2 : 1;     // pixels per lane
-  static constexpr int BW = 8 * PX;              // warp block width
-  static constexpr int LBW = PX == 2 ? 4 : 3;    // log2(BW)
-  static constexpr int NBX = T / BW, NBY = T / 4, NB = NBX * NBY;  // warp blocks per tile
-  static constexpr int NW = NB < 8 ? NB : 8;     // warps per CTA
-  static constexpr int NT = 32 * NW;             // threads per CTA
-  static constexpr int BPW = NB / NW;            // warp blocks per warp
-};
-
 // Backward CTA shape: warps own blocks of 4 rows x BW columns (records on lanes, one pixel
 // column per unrolled step).  16 columns measured faster than 8 (fewer record visits outweigh
 // the lower in-cut share of a wider block).
