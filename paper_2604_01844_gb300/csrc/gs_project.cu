@@ -740,21 +740,29 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
 }
 
 // ------------------------------------------------------------------------------------------
-// chain: one warp per Gaussian, lanes over its views
+// chain: a thread per (Gaussian, chunk of kChainViews views), consecutive threads on
+// consecutive Gaussians of one chunk, so that the moment loads of a warp are one contiguous
+// run and the view frame is the same for all its lanes; each thread chains its views'
+// moments to the Gaussian's parameters and adds its sums with float4 atomics (the gradients
+// are zeroed first unless accumulating)
 // ------------------------------------------------------------------------------------------
+constexpr int kChainViews = 8;
+
 __global__ void __launch_bounds__(kThreads)
     k_project_chain(const __grid_constant__ Batch b, const float4* __restrict__ mean_rho,
                     const float4* __restrict__ scale, const float4* __restrict__ quat,
-                    int total_n, const ViewFrame* __restrict__ frames,
+                    int total_n, int vchunks, const ViewFrame* __restrict__ frames,
                     const float4* __restrict__ fpgrad, float4* __restrict__ g_mr,
-                    float4* __restrict__ g_sc, float4* __restrict__ g_q, int accumulate,
+                    float4* __restrict__ g_sc, float4* __restrict__ g_q,
                     const uint32_t* __restrict__ counts, float* __restrict__ stat,
                     int* __restrict__ vis) {
-  const int gi = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (gi >= total_n) return;
+  const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (tid >= (int64_t)total_n * vchunks) return;
+  const int gi = (int)(tid % total_n), ch = (int)(tid / total_n);
   const Inst& I = b.in[inst_of_gaussian(b, gi)];
   const int il = gi - I.g_off;
+  const int v0 = ch * kChainViews, v1 = min(v0 + kChainViews, I.nv);
+  if (v0 >= v1) return;
   const float4 mr = mean_rho[gi], sc = scale[gi], qt = quat[gi];
   float acc[11];
 #pragma unroll
@@ -763,7 +771,7 @@ __global__ void __launch_bounds__(kThreads)
   // number of views with a listed tile
   float st_acc = 0.f;
   int vis_acc = 0;
-  for (int v = lane; v < I.nv; v += 32) {
+  for (int v = v0; v < v1; ++v) {
     const size_t rec = (size_t)(I.item_off + (int64_t)v * I.n + il);
     if (stat && counts[rec] > 0u) ++vis_acc;
     const float4 m0 = fpgrad[2 * rec], m1 = fpgrad[2 * rec + 1];
@@ -786,29 +794,17 @@ __global__ void __launch_bounds__(kThreads)
     acc[4] += gs3[0]; acc[5] += gs3[1]; acc[6] += gs3[2];
     acc[7] += gq[0]; acc[8] += gq[1]; acc[9] += gq[2]; acc[10] += gq[3];
   }
+  bool any = false;
 #pragma unroll
-  for (int k = 0; k < 11; ++k) acc[k] = gsd::warp_sum(acc[k]);
-  if (lane == 0) {
-    float4 a = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    float4 bb = make_float4(acc[4], acc[5], acc[6], 0.f);
-    float4 c = make_float4(acc[7], acc[8], acc[9], acc[10]);
-    if (accumulate) {
-      const float4 pa = g_mr[gi], pb = g_sc[gi], pc = g_q[gi];
-      a.x += pa.x; a.y += pa.y; a.z += pa.z; a.w += pa.w;
-      bb.x += pb.x; bb.y += pb.y; bb.z += pb.z; bb.w += pb.w;
-      c.x += pc.x; c.y += pc.y; c.z += pc.z; c.w += pc.w;
-    }
-    g_mr[gi] = a;
-    g_sc[gi] = bb;
-    g_q[gi] = c;
+  for (int k = 0; k < 11; ++k) any |= acc[k] != 0.f;
+  if (any) {
+    atomicAdd(&g_mr[gi], make_float4(acc[0], acc[1], acc[2], acc[3]));
+    atomicAdd(&g_sc[gi], make_float4(acc[4], acc[5], acc[6], 0.f));
+    atomicAdd(&g_q[gi], make_float4(acc[7], acc[8], acc[9], acc[10]));
   }
   if (stat) {
-    st_acc = gsd::warp_sum(st_acc);
-    vis_acc = gsd::warp_sum(vis_acc);
-    if (lane == 0) {
-      stat[gi] += st_acc;
-      vis[gi] += vis_acc;
-    }
+    if (st_acc != 0.f) atomicAdd(&stat[gi], st_acc);
+    if (vis_acc) atomicAdd(&vis[gi], vis_acc);
   }
 }
 
@@ -1040,11 +1036,21 @@ int gs_project_batch_backward_stats(const float* d_mean_rho, const float* d_scal
     case 16: GS_TRY(raster_bwd<16>(p, L, v, d_dimg, s)); break;
     default: GS_TRY(raster_bwd<32>(p, L, v, d_dimg, s)); break;
   }
-  const int blocks = (int)(((int64_t)p.total_n * 32 + kThreads - 1) / kThreads);
+  if (!accumulate) {
+    const size_t bytes = (size_t)p.total_n * sizeof(float4);
+    GS_CUDA(cudaMemsetAsync(d_g_mean_rho, 0, bytes, s));
+    GS_CUDA(cudaMemsetAsync(d_g_scale, 0, bytes, s));
+    GS_CUDA(cudaMemsetAsync(d_g_quat, 0, bytes, s));
+  }
+  int max_nv = 1;
+  for (int k = 0; k < p.b.count; ++k) max_nv = std::max(max_nv, p.b.in[k].nv);
+  const int vchunks = (max_nv + kChainViews - 1) / kChainViews;
+  const int64_t threads = (int64_t)p.total_n * vchunks;
+  const int blocks = (int)((threads + kThreads - 1) / kThreads);
   return launch("project_chain", k_project_chain, dim3(blocks), dim3(kThreads), 0, s, p.b,
                 (const float4*)d_mean_rho, (const float4*)d_scale, (const float4*)d_quat,
-                p.total_n, (const ViewFrame*)L.frames, (const float4*)L.fpgrad,
-                (float4*)d_g_mean_rho, (float4*)d_g_scale, (float4*)d_g_quat, accumulate,
+                p.total_n, vchunks, (const ViewFrame*)L.frames, (const float4*)L.fpgrad,
+                (float4*)d_g_mean_rho, (float4*)d_g_scale, (float4*)d_g_quat,
                 (const uint32_t*)L.counts, d_grad_stat, (int*)d_vis);
 }
 
