@@ -86,7 +86,6 @@ class DensityControl:
         self.stat = torch.zeros(n, dtype=torch.float32, device=dev)
         self.vis = torch.zeros(n, dtype=torch.int32, device=dev)
         self.rec.density_stats = (self.stat, self.vis)
-        self.rec.plan()  # the statistics run the unchunked step: its projector needs room
 
     def due(self, it: int) -> bool:
         c = self.cfg

@@ -98,8 +98,7 @@ class Reconstruction:
         o.beta1, o.beta2, o.eps = cfg.beta1, cfg.beta2, cfg.eps
         o.min_log_scale, o.max_log_scale = cfg.min_log_scale, cfg.max_log_scale
         self.adam_opts = o
-        self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set;
-        # the step then runs unchunked (the statistics' per-Gaussian sums are not atomic)
+        self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set
         self.activate()
         self.plan()
 
@@ -125,15 +124,13 @@ class Reconstruction:
         """Size the workspaces for the current parameters (synchronous)."""
         for _, _, pj in self.vchunks:
             pj.ensure_capacity(*self.act)
-        if not self.vchunks or self.density_stats is not None:
-            self.projector.ensure_capacity(*self.act)  # the unchunked step's projector
+        if not self.vchunks:
+            self.projector.ensure_capacity(*self.act)
         self.voxelizer.ensure_capacity(*self.act)
 
     def overflowed(self) -> bool:
         """True when the last step ran out of pair capacity somewhere (synchronises)."""
-        pjs = [pj for _, _, pj in self.vchunks]
-        if not pjs or self.density_stats is not None:
-            pjs.append(self.projector)
+        pjs = [pj for _, _, pj in self.vchunks] or [self.projector]
         return any(pj.status().code != B.GS_OK for pj in pjs) or \
             self.voxelizer.status().code != B.GS_OK
 
@@ -178,7 +175,7 @@ class Reconstruction:
         s = B.stream_handle()
         cfg = self.cfg
         B.check(L.gs_memset(B.ptr(self.loss), 0, 4, s), "gs_memset")
-        if self.vchunks and self.density_stats is None and not serial:
+        if self.vchunks and not serial:
             return self._step_pipelined(target_ready)
         branch = cfg.alpha_tv > 0 and cfg.overlap_tv and not serial
         if branch:
@@ -240,10 +237,11 @@ class Reconstruction:
                     if tv:
                         main.wait_stream(self._side)
                     pj.backward(*self.act, self.dimg[a:b], grads=self.grads, accumulate=tv,
-                                reuse=not cfg.recompute_lists)
+                                reuse=not cfg.recompute_lists, stats=self.density_stats)
                 else:
                     pj.backward(*self.act, self.dimg[a:b], grads=self.chunk_grads[k - 1],
-                                accumulate=False, reuse=not cfg.recompute_lists)
+                                accumulate=False, reuse=not cfg.recompute_lists,
+                                stats=self.density_stats)
         s = B.stream_handle()
         for st, g in zip(self._streams, self.chunk_grads):
             main.wait_stream(st)
