@@ -250,6 +250,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     B.timing_enable(False)
     per_kernel = B.timing_read()
+    pairs = int(rec.projector.status().pairs)  # (view, tile) pairs of the serial step
 
     # end to end through the public API with host buffers: per step the parameters and the
     # target projections go host->device from pinned memory, the loss and the updated
@@ -335,6 +336,23 @@ def run_ours(args, ws, rank, local):
                                "unit": "Geval/s", "frac": round(kach / kpeak, 4),
                                "evals_per_launch": units}
 
+    # HBM rooflines of the step's memory-heavy kernels from algorithmic bytes: a radix pass
+    # reads and writes every (key, value) pair (16 B), the 2D SSIM passes read and write each
+    # image or map pixel once
+    n_keys = int(WORKLOAD["views"]) * ((WORKLOAD["W"] + WORKLOAD["tile"] - 1) // WORKLOAD["tile"]) * \
+        ((WORKLOAD["H"] + WORKLOAD["tile"] - 1) // WORKLOAD["tile"])
+    passes = (max(1, (n_keys - 1).bit_length()) + 9) // 10
+    px = int(WORKLOAD["views"]) * WORKLOAD["W"] * WORKLOAD["H"]
+    step_bytes = {"radix_scatter": 16 * pairs * passes, "ssim2d_fwd": 20 * px,
+                  "ssim2d_bwd": 24 * px}
+    hbm_roofs = {}
+    for k, nb in step_bytes.items():
+        if k in per_kernel and mp.get("hbm_gbs"):
+            kms = per_kernel[k][1] / args.steps  # ms per step
+            gbs = nb / (kms * 1e-3) / 1e9
+            hbm_roofs[k] = {"bytes_per_step": nb, "achieved_gbs": round(gbs, 1),
+                            "peak_gbs": mp["hbm_gbs"], "frac": round(gbs / mp["hbm_gbs"], 3)}
+
     value = R.job_rate(evals_px, ms, ws)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -347,7 +365,8 @@ def run_ours(args, ws, rank, local):
                    "target": "projections of a second seeded Gaussian set",
                    "l2": "working set per step > 0.5 GB (images, SSIM maps, 256^3 volume) > L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "roofline": roof, "kernel_rooflines": kernel_roofs,
+        "roofline": roof, "kernel_rooflines": kernel_roofs, "hbm_rooflines": hbm_roofs,
+        "pairs_per_step": pairs,
         "alu_peaks": {"ex2_per_s": round(peaks["ex2_per_s"]), "fma_per_s": round(peaks["fma_per_s"]),
                       "per_sm_per_clock": per_clk, "sm_mhz": f_mhz,
                       "note": "probe kernels gs_probe_rate, 8 CTAs of 256 threads per SM"},
@@ -959,11 +978,32 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     evals = vox.count_evals(*f.params)
     del vox, f, gt
     torch.cuda.empty_cache()
+    # the volume passes' HBM rooflines: algorithmic bytes per voxel (each input and output
+    # volume once; halos and re-reads not counted) over the measured copy bandwidth
+    nvox = side ** 3
+    hbm = (measured_peaks() or {}).get("hbm_gbs")
+    bytes_per_voxel = {
+        "ssim3d_z_fwd": 28,   # X, Y in; five moments out
+        "ssim3d_z_bwd": 24,   # three maps in; three filtered maps out
+        "ssim3d_xy_fwd": 32,  # five moments in; three maps out
+        "ssim3d_xy_bwd": 24,  # three filtered maps, X and Y in; the gradient out
+        "vox_fwd": 4,         # the volume out
+        "vox_bwd": 4,         # dL/dV in
+    }
+    hbm_roofs = {}
+    for k, bpv in bytes_per_voxel.items():
+        if k in per_kernel and per_kernel[k] > 0 and hbm:
+            gbs = bpv * nvox / (per_kernel[k] * 1e-3) / 1e9
+            hbm_roofs[k] = {"bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),
+                            "peak_gbs": hbm, "frac": round(gbs / hbm, 3)}
     return {"workload": f"gs_fit_volume, {n} Gaussians, {side}^3 ground truth, bricks 16^3",
             "ms_per_iter": round(ms, 3), "voxel_evals_per_iter": evals,
             "value": evals / (ms * 1e-3), "unit": "Gaussian-voxel evals/s",
             "status": int(st.code), "loss_last": float(loss[-1].item()),
-            "kernels_ms_per_iter": per_kernel}
+            "kernels_ms_per_iter": per_kernel,
+            "hbm_rooflines": hbm_roofs,
+            "hbm_note": "achieved = algorithmic bytes per voxel x voxels / kernel ms; the voxel "
+                        "kernels are evaluation-bound (see their ALU rooflines in the step)"}
 
 
 def read_traffic(kernel: str):
