@@ -338,10 +338,11 @@ def run_ours(args, ws, rank, local):
 
     # HBM rooflines of the step's memory-heavy kernels from algorithmic bytes: a radix pass
     # reads and writes every (key, value) pair (16 B), the 2D SSIM passes read and write each
-    # image or map pixel once
-    n_keys = int(WORKLOAD["views"]) * ((WORKLOAD["W"] + WORKLOAD["tile"] - 1) // WORKLOAD["tile"]) * \
+    # image or map pixel once.  The pairs sort over the tile bits of their keys in passes of
+    # at most 8 bits (two passes of 5 bits for the 1024 tiles of 512^2 at tile 16).
+    tiles = ((WORKLOAD["W"] + WORKLOAD["tile"] - 1) // WORKLOAD["tile"]) * \
         ((WORKLOAD["H"] + WORKLOAD["tile"] - 1) // WORKLOAD["tile"])
-    passes = (max(1, (n_keys - 1).bit_length()) + 9) // 10
+    passes = ((tiles - 1).bit_length() + 7) // 8
     px = int(WORKLOAD["views"]) * WORKLOAD["W"] * WORKLOAD["H"]
     step_bytes = {"radix_scatter": 16 * pairs * passes, "ssim2d_fwd": 20 * px,
                   "ssim2d_bwd": 24 * px}

@@ -203,7 +203,9 @@ int gs_project_count_evals(const float* d_mean_rho, const float* d_scale, const 
  * a host array, read during the call (passed to the kernels by value, so a call makes no
  * host-to-device copy and can be captured in a CUDA graph).  n may be 0 for some instances;
  * n_views, W, H must be >= 1 and W, H <= 32767; the totals must stay below 2^31 (pairs,
- * (view, Gaussian) records and (view, tile) keys).  GS_ERR_ARG otherwise.
+ * (view, Gaussian) records and (view, tile) keys), and the total view count times
+ * 2^ceil(log2(largest tile count)) must not exceed 2^32 (32-bit pair keys).  GS_ERR_ARG
+ * otherwise.
  * ------------------------------------------------------------------------------------- */
 #define GS_MAX_INSTANCES 32
 
@@ -650,8 +652,11 @@ int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream);
 /* ---------------------------------------------------------------------------------------
  * Binning internals exposed for testing: the sorted (key, value) lists of the last binning
  * in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).  Rasterizer:
- * key = (first key of the instance) + view * tiles + tile, value = record index (first record
- * of the instance + view * n + Gaussian).  Voxelizer: key = brick, value = Gaussian.
+ * key = (global view << b) | tile, where the global view is the instance's first view + view,
+ * tile = ty * tiles_x + tx, and b = ceil(log2(largest tile count of the batch's instances));
+ * value = record index (first record of the instance + view * n + Gaussian).  The list is
+ * ordered by (tile, global view, record): every key's pairs are contiguous and in record order,
+ * but keys do not ascend.  Voxelizer: key = brick, value = Gaussian, ordered by (key, value).
  * ------------------------------------------------------------------------------------- */
 int gs_read_pairs(const void* d_ws, size_t ws_bytes, void* stream, int64_t cap,
                   uint32_t* h_keys, uint32_t* h_vals, int64_t* h_pairs);

@@ -7,7 +7,8 @@
 //   4. radix_sort: stable LSD radix sort over only the key bits in use, reduce-then-scan per
 //      pass (histogram, per-digit scan over blocks, stable scatter) -- no inter-block
 //      spin-waits anywhere;
-//   5. build_ranges: [start, end) of every key.
+//   5. build_ranges: [start, end) of every key (the rasterizer, whose sorted lists are grouped
+//      by tile rather than ascending in key, has its own ranges kernel).
 // The pair count stays on the device (status block) so that no step needs a host read-back.
 #include <algorithm>
 
@@ -65,20 +66,66 @@ __device__ __forceinline__ void chunk_of(const gs_status* st, int G, int64_t& lo
   hi = min(lo + chunk, count);
 }
 
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, const gs_status* st, int shift,
-                             int dbits, uint32_t* __restrict__ hist, int G) {
+// Digit histogram of a block's chunk, four consecutive keys per thread through one 16-byte
+// load (lo is a multiple of the sort tile).  Digits of up to 5 bits (LANE = true) go to per-lane
+// counters in shared memory, [warp][digit][lane]: plain increments in the lane's own bank, no
+// atomics, then one conflict-free reduction.  Wider digits use shared atomics.
+constexpr int kLaneHistMaxBits = 5;
+template <bool LANE>
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_hist(const uint32_t* __restrict__ keys, const gs_status* st, int shift, int dbits,
+                 uint32_t* __restrict__ hist, int G) {
   extern __shared__ uint32_t sh_hist[];
   if (st->code != GS_OK) return;
+  constexpr int NW = kSortThreads / 32;
+  static_assert(32 % NW == 0 && (NW << kLaneHistMaxBits) <= kSortThreads, "reduction layout");
   const int D = 1 << dbits;
   const uint32_t mask = (uint32_t)D - 1u;
-  for (int d = threadIdx.x; d < D; d += blockDim.x) sh_hist[d] = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int words = LANE ? NW * D * 32 : D;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) sh_hist[i] = 0;
   __syncthreads();
   int64_t lo, hi;
   chunk_of(st, G, lo, hi);
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    atomicAdd(&sh_hist[(keys[i] >> shift) & mask], 1u);
+  uint32_t* own = sh_hist + (size_t)w * D * 32 + lane;  // LANE: counter of digit d at d * 32
+  for (int64_t i = lo + 4 * (int64_t)threadIdx.x; i < hi; i += 4 * (int64_t)blockDim.x) {
+    uint32_t k[4];
+    if (i + 4 <= hi) {
+      const uint4 q = *reinterpret_cast<const uint4*>(keys + i);
+      k[0] = q.x, k[1] = q.y, k[2] = q.z, k[3] = q.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = i + j < hi ? keys[i + j] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (i + j < hi) {
+        const uint32_t d = (k[j] >> shift) & mask;
+        if (LANE)
+          own[d * 32] += 1u;
+        else
+          atomicAdd(&sh_hist[d], 1u);
+      }
+    }
+  }
   __syncthreads();
-  for (int d = threadIdx.x; d < D; d += blockDim.x) hist[(size_t)d * G + blockIdx.x] = sh_hist[d];
+  if (LANE) {
+    // thread t sums warp (t % NW)'s 32 lane counters of digit t / NW, the lanes rotated by t
+    // so that a warp's reads fall in 32 distinct banks; then the NW partials of a digit (NW
+    // consecutive threads) meet by shuffles
+    const int t = threadIdx.x, d = t / NW, ww = t % NW;
+    uint32_t sum = 0;
+    if (d < D) {
+      const uint32_t* row = sh_hist + ((size_t)ww * D + d) * 32;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) sum += row[(l + t) & 31];
+    }
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (d < D && ww == 0) hist[(size_t)d * G + blockIdx.x] = sum;
+  } else {
+    for (int d = threadIdx.x; d < D; d += blockDim.x) hist[(size_t)d * G + blockIdx.x] = sh_hist[d];
+  }
 }
 
 // One block per digit: exclusive scan over the G blocks' counts of that digit; totals[d].
@@ -257,11 +304,12 @@ int bits_for(int64_t n_keys) {
   return b;
 }
 
-SortPlan make_sort_plan(int key_bits) {
+SortPlan make_sort_plan(int key_bits, int max_digit_bits) {
   SortPlan p;
   p.grid = std::min(1024, 4 * num_sms());
   if (key_bits <= 0) return p;
-  p.passes = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+  max_digit_bits = std::max(1, std::min(max_digit_bits, kMaxDigitBits));
+  p.passes = (key_bits + max_digit_bits - 1) / max_digit_bits;
   int shift = 0;
   for (int i = 0; i < p.passes; ++i) {
     int rem = key_bits - shift;
@@ -306,8 +354,14 @@ int radix_sort(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt, uint32_t* v
     const int db = plan.dbits[pass], sh = plan.shift[pass];
     const int D = 1 << db;
     uint32_t* totals = hist + (size_t)D * G;
-    GS_TRY(launch("radix_hist", k_radix_hist, dim3(G), dim3(kSortThreads), D * sizeof(uint32_t),
-                  s, (const uint32_t*)*keys, (const gs_status*)st, sh, db, hist, G));
+    if (db <= kLaneHistMaxBits)
+      GS_TRY(launch("radix_hist", k_radix_hist<true>, dim3(G), dim3(kSortThreads),
+                    (size_t)(kSortThreads / 32) * D * 32 * sizeof(uint32_t), s,
+                    (const uint32_t*)*keys, (const gs_status*)st, sh, db, hist, G));
+    else
+      GS_TRY(launch("radix_hist", k_radix_hist<false>, dim3(G), dim3(kSortThreads),
+                    D * sizeof(uint32_t), s, (const uint32_t*)*keys, (const gs_status*)st, sh, db,
+                    hist, G));
     const int scan_threads = (G + 31) / 32 * 32;
     GS_TRY(launch("radix_digit_scan", k_radix_digit_scan, dim3(D), dim3(scan_threads), 0, s,
                   hist, totals, (const gs_status*)st, G));

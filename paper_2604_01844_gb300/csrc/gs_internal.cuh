@@ -93,7 +93,9 @@ struct SortPlan {
   int shift[4] = {0, 0, 0, 0};
   int grid = 0;  // blocks of the histogram / scatter kernels
 };
-SortPlan make_sort_plan(int key_bits);
+// Passes of at most max_digit_bits each, balanced.  Narrower digits give the scatter longer
+// runs of one digit per 2048-item tile (better coalesced writes) at the cost of more passes.
+SortPlan make_sort_plan(int key_bits, int max_digit_bits = kMaxDigitBits);
 size_t sort_hist_words(const SortPlan& p);
 
 // Scan of producer block sums; writes block offsets, the pair total and the capacity status.

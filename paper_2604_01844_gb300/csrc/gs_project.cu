@@ -35,16 +35,22 @@ using gsd::ex2;
 
 constexpr int kThreads = 256;
 constexpr int kMaxInst = GS_MAX_INSTANCES;
+// widest digit of the tile-key sort: 10 tile bits (512^2 at tile 16) sort in two passes of 5
+constexpr int kTileDigitBits = 8;
 
 struct Inst {
   int n, nv, W, H, TW, TH, g_off, v_off;
   long long item_off, key_off, img_off;
 };
 
+// Pair keys are (global view << tbits) | tile, tbits the bits of the largest instance's tile
+// count.  Pairs are emitted in view order, so the radix sort runs over the tile bits only: the
+// sorted lists are grouped by tile, then view, then record, which keeps every (view, tile)
+// list contiguous and in record order with fewer, narrower passes than a sort of the full key.
 struct Batch {
   int count, T;
   float cut2, eps, znear;
-  int pad;
+  int tbits;
   Inst in[kMaxInst];
 };
 
@@ -105,7 +111,7 @@ int make_plan(const gs_instance* inst, int n_inst, const gs_opts* o, int64_t cap
   b.cut2 = o->cut * o->cut;
   b.eps = o->eps;
   b.znear = o->znear;
-  int64_t items = 0, keys = 0, img = 0, gsum = 0, vsum = 0;
+  int64_t items = 0, keys = 0, img = 0, gsum = 0, vsum = 0, max_tiles = 1;
   for (int k = 0; k < n_inst; ++k) {
     const gs_instance& s = inst[k];
     if (s.n < 0 || s.n_views < 1 || s.W < 1 || s.H < 1 || s.W > 32767 || s.H > 32767)
@@ -124,12 +130,14 @@ int make_plan(const gs_instance* inst, int n_inst, const gs_opts* o, int64_t cap
     d.img_off = img;
     items += (int64_t)s.n * s.n_views;
     keys += (int64_t)s.n_views * d.TW * d.TH;
+    max_tiles = std::max<int64_t>(max_tiles, (int64_t)d.TW * d.TH);
     img += ((int64_t)s.n_views * s.W * s.H + 63) / 64 * 64;  // blocks start 256-byte aligned
     gsum += s.n;
     vsum += s.n_views;
   }
+  b.tbits = bits_for(max_tiles);
   if (items > ((int64_t)1 << 31) - kThreads || keys > ((int64_t)1 << 31) - 1 ||
-      gsum > ((int64_t)1 << 31) - 1)
+      gsum > ((int64_t)1 << 31) - 1 || (vsum << b.tbits) > ((int64_t)1 << 32))
     return GS_ERR_ARG;
   p.total_n = (int)gsum;
   p.total_v = (int)vsum;
@@ -137,8 +145,8 @@ int make_plan(const gs_instance* inst, int n_inst, const gs_opts* o, int64_t cap
   p.n_keys = keys;
   p.cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
   p.nblocks = (int)((items + kThreads - 1) / kThreads);
-  p.key_bits = bits_for(keys);
-  p.sort = make_sort_plan(p.key_bits);
+  p.key_bits = b.tbits;
+  p.sort = make_sort_plan(p.key_bits, kTileDigitBits);
   return GS_OK;
 }
 
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(kThreads)
     const int v = (int)((idx - I.item_off) / I.n);
     r = rect[idx];
     TW = I.TW;
-    kbase = (uint32_t)(I.key_off + (int64_t)v * I.TW * I.TH);
+    kbase = (uint32_t)(I.v_off + v) << b.tbits;
     tx0i = r.x / T;
     ty0i = r.y / T;
     ntx = r.z / T - tx0i + 1;
@@ -373,6 +381,46 @@ __global__ void __launch_bounds__(kThreads)
         vals[off] = (uint32_t)idx;
         ++off;
       }
+  }
+}
+
+// [start, end) of every (view, tile) list.  The sorted keys are grouped by tile and then view,
+// so each key's pairs are contiguous (though keys are not ascending); a boundary's key maps to
+// its (instance, view, tile) slot.  Four keys per thread through one 16-byte load.
+__device__ __forceinline__ uint32_t range_slot(const Batch& b, uint32_t key) {
+  const int gv = (int)(key >> b.tbits);
+  const Inst& I = b.in[inst_of_view(b, gv)];
+  return (uint32_t)(I.key_off + (int64_t)(gv - I.v_off) * I.TW * I.TH +
+                    (key & ((1u << b.tbits) - 1u)));
+}
+__global__ void __launch_bounds__(kThreads)
+    k_tile_ranges(const __grid_constant__ Batch b, const uint32_t* __restrict__ keys,
+                  uint2* __restrict__ ranges, const gs_status* st) {
+  if (st->code != GS_OK) return;
+  const int64_t n = st->pairs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * q < n; q += stride) {
+    const int64_t i0 = 4 * q;
+    uint32_t k[4];
+    if (i0 + 4 <= n) {
+      const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+      k[0] = v.x, k[1] = v.y, k[2] = v.z, k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0u;
+    }
+    const uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0u;
+    const uint32_t next = i0 + 4 < n ? keys[i0 + 4] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i < n) {
+        const bool first = i == 0 || (j == 0 ? prev : k[j - 1]) != k[j];
+        const bool last = i == n - 1 || (j == 3 ? next : k[j + 1]) != k[j];
+        if (first) ranges[range_slot(b, k[j])].x = (uint32_t)i;
+        if (last) ranges[range_slot(b, k[j])].y = (uint32_t)(i + 1);
+      }
+    }
   }
 }
 
@@ -893,7 +941,9 @@ int bin_pairs(const Plan& p, const Layout& L, const float* mr, const float* sc, 
                 p.items, L.keys, L.vals, L.st, (int64_t)((char*)fk - (char*)ws),
                 (int64_t)((char*)fv - (char*)ws)));
   GS_TRY(radix_sort(&k, &v, L.keys_alt, L.vals_alt, L.hist, p.sort, L.st, p.cap, s));
-  GS_TRY(build_ranges(k, L.ranges, p.n_keys, L.st, p.cap, s));
+  GS_CUDA(cudaMemsetAsync(L.ranges, 0, (size_t)p.n_keys * sizeof(uint2), s));
+  GS_TRY(launch("ranges", k_tile_ranges, dim3(4 * num_sms()), dim3(kThreads), 0, s, p.b,
+                (const uint32_t*)k, L.ranges, (const gs_status*)L.st));
   *skeys = k;
   *svals = v;
   return GS_OK;

@@ -201,8 +201,9 @@ class Projector:
         return int(self.status().evals)
 
     def read_pairs(self):
-        """Sorted (key, record) lists of the last binning (synchronises); key = view * tiles +
-        tile, record = view * n + Gaussian."""
+        """Sorted (key, record) lists of the last binning (synchronises): key = (view << b) |
+        tile with b = ceil(log2(tiles)), record = view * n + Gaussian, ordered by (tile, view,
+        record), so every key's pairs are contiguous."""
         st = self.status()
         n = int(st.pairs)
         keys = np.zeros(max(n, 1), dtype=np.uint32)

@@ -93,8 +93,8 @@ def test_batch_backward_matches_oracle(orc, gsct, reuse):
 
 
 def test_batch_keys_and_records(gsct):
-    """Keys are offset per instance, records are (instance offset + view * n + Gaussian); the
-    sorted list is ordered by key, then record."""
+    """Keys are (global view, tile), records are (instance offset + view * n + Gaussian); the
+    sorted list is ordered by tile, then global view, then record."""
     import ctypes
 
     inst = _instances(SPECS[:3], seed=300)
@@ -111,19 +111,26 @@ def test_batch_keys_and_records(gsct):
         keys.ctypes.data_as(ctypes.c_void_p), vals.ctypes.data_as(ctypes.c_void_p),
         ctypes.byref(cnt)), "gs_read_pairs")
     k, r = keys[:n].astype(np.int64), vals[:n].astype(np.int64)
-    assert np.all((np.diff(k) > 0) | ((np.diff(k) == 0) & (np.diff(r) > 0)))
-    # each record's instance and view agree with its key's
-    key_off = rec_off = 0
-    for (mr, _, _, views, W, H) in inst:
-        T = 16
-        tiles = ((W + T - 1) // T) * ((H + T - 1) // T)
-        nk, nr = len(views) * tiles, len(views) * mr.shape[0]
-        sel = (k >= key_off) & (k < key_off + nk)
+    T = 16
+    tiles = [((W + T - 1) // T) * ((H + T - 1) // T) for *_, W, H in inst]
+    tb = (max(tiles) - 1).bit_length()  # key = (global view << tb) | tile
+    gv, t = k >> tb, k & ((1 << tb) - 1)
+    # ordered by (tile, global view, record): every key's pairs contiguous, records ascending
+    order = np.stack([t, gv, r])
+    d = np.diff(order, axis=1)
+    assert np.all((d[0] > 0) | ((d[0] == 0) & (d[1] > 0)) | ((d[0] == 0) & (d[1] == 0) & (d[2] > 0)))
+    # each record's instance and view agree with its key's, and the tile lies in the instance
+    v_off = rec_off = 0
+    for (mr, _, _, views, W, H), nt in zip(inst, tiles):
+        nv, nr = len(views), len(views) * mr.shape[0]
+        sel = (gv >= v_off) & (gv < v_off + nv)
         assert np.all((r[sel] >= rec_off) & (r[sel] < rec_off + nr))
+        assert np.all(t[sel] < nt)
         if mr.shape[0]:
-            assert np.array_equal((k[sel] - key_off) // tiles, (r[sel] - rec_off) // mr.shape[0])
-        key_off += nk
+            assert np.array_equal(gv[sel] - v_off, (r[sel] - rec_off) // mr.shape[0])
+        v_off += nv
         rec_off += nr
+    assert np.all(gv < v_off)
 
 
 def test_batch_of_one_equals_single(gsct):

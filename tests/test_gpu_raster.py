@@ -94,8 +94,9 @@ def test_empty_and_single(orc, gsct):
 
 @pytest.mark.parametrize("tile", [8, 16])
 def test_keys_and_sort_order_bit_exact(orc, gsct, tile):
-    """Culling, key duplication and the stable sort order equal the oracle's on every
-    (view, Gaussian) pair outside the guard band."""
+    """Culling, key duplication and the sort order equal the oracle's on every (view, Gaussian)
+    pair outside the guard band: the device groups the oracle's (key, Gaussian)-ordered list
+    by tile, stably."""
     W = H = 64
     mr, sc, qt, views = _case(6, 2000, 8, W, H)
     P, V = orc.params64(mr, sc, qt), orc.views64(views)
@@ -106,20 +107,28 @@ def test_keys_and_sort_order_bit_exact(orc, gsct, tile):
     proj.forward(*to_dev(mr, sc, qt))
     keys_g, recs_g = proj.read_pairs()
     TWH = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
-    # the device's values are (view, Gaussian) record indices v * n + i
-    n = mr.shape[0]
-    assert np.array_equal(recs_g.astype(np.int64) // n, keys_g.astype(np.int64) // TWH)
-    vals_g = recs_g.astype(np.int64) % n
+    tb = (TWH - 1).bit_length()  # key = (view << tb) | tile
+    n, nv = mr.shape[0], len(views)
+    kd, rd = keys_g.astype(np.int64), recs_g.astype(np.int64)
+    v_g, t_g = kd >> tb, kd & ((1 << tb) - 1)
+    assert np.all(t_g < TWH) and np.all(v_g < nv)
+    # the device's values are (view, Gaussian) record indices v * n + i of the key's view
+    assert np.array_equal(rd // n, v_g)
+    vals_g = rd % n
+    # the list is ordered by (tile, view, Gaussian): keys contiguous, Gaussians ascending
+    assert np.all(np.diff((t_g * nv + v_g) * n + vals_g) > 0)
 
     def strip(k, v):
         keep = ~amb[k // TWH, v]
         return k[keep], v[keep]
 
+    # the oracle's list (by key, then Gaussian) regrouped by tile, stably
     ko, vo = strip(keys_o.astype(np.int64), vals_o.astype(np.int64))
-    kg, vg = strip(keys_g.astype(np.int64), vals_g.astype(np.int64))
+    perm = np.argsort(ko % TWH, kind="stable")
+    ko, vo = ko[perm], vo[perm]
+    kg, vg = strip(v_g * TWH + t_g, vals_g)
     assert np.array_equal(ko, kg) and np.array_equal(vo, vg)
     assert int(amb.sum()) < 0.01 * amb.size  # the guard band is rare
-    assert np.all(np.diff(keys_g.astype(np.int64)) >= 0)
 
 
 def test_count_evals_matches_oracle(orc, gsct):
