@@ -53,3 +53,30 @@ def test_round_trip_error_bound_and_layout():
     assert np.all(dsc[:, 3] == 0)
     # decode is exact on representable values: a second round trip changes nothing
     assert np.array_equal(C.encode(dmr, dsc, dq), bits)
+
+
+def _golden_sizes():
+    import pathlib
+
+    out = {}
+    for line in (pathlib.Path(__file__).parent / "golden" / "compression_sizes.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def test_paper_storage_sizes():
+    """The codec's byte count reproduces the sizes printed for the compression study: 22 bytes
+    per Gaussian, 0.84 MB for 40,000 Gaussians, against 64 MB for the raw 256^3 float32 volume."""
+    g = _golden_sizes()
+    n = int(g["gaussians"])
+    rng = np.random.default_rng(3)
+    mr = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+    sc = rng.uniform(1e-3, 0.1, (n, 4)).astype(np.float32)
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    bits = C.encode(mr, sc, q)
+    assert bits.shape[0] == int(g["values_per_gaussian"])
+    assert bits.nbytes == int(g["bytes_per_gaussian"]) * n
+    assert round(bits.nbytes / 2 ** 20, 2) == g["gaussians_fp16_mb"]
+    assert int(g["volume_side"]) ** 3 * 4 / 2 ** 20 == g["raw_float32_mb"]
