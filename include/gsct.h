@@ -203,9 +203,8 @@ int gs_project_count_evals(const float* d_mean_rho, const float* d_scale, const 
  * a host array, read during the call (passed to the kernels by value, so a call makes no
  * host-to-device copy and can be captured in a CUDA graph).  n may be 0 for some instances;
  * n_views, W, H must be >= 1 and W, H <= 32767; the totals must stay below 2^31 (pairs,
- * (view, Gaussian) records and (view, tile) keys), and the total view count times
- * 2^ceil(log2(largest tile count)) must not exceed 2^32 (32-bit pair keys).  GS_ERR_ARG
- * otherwise.
+ * (view, Gaussian) records and (view, tile) keys; the last bound also keeps the 32-bit pair
+ * keys (view << ceil(log2(tiles))) | tile in range).  GS_ERR_ARG otherwise.
  * ------------------------------------------------------------------------------------- */
 #define GS_MAX_INSTANCES 32
 

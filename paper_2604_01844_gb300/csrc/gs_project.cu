@@ -137,7 +137,8 @@ int make_plan(const gs_instance* inst, int n_inst, const gs_opts* o, int64_t cap
   }
   b.tbits = bits_for(max_tiles);
   if (items > ((int64_t)1 << 31) - kThreads || keys > ((int64_t)1 << 31) - 1 ||
-      gsum > ((int64_t)1 << 31) - 1 || (vsum << b.tbits) > ((int64_t)1 << 32))
+      gsum > ((int64_t)1 << 31) - 1 ||
+      (vsum << b.tbits) > ((int64_t)1 << 32))  // implied by the key bound (2^tbits < 2 tiles)
     return GS_ERR_ARG;
   p.total_n = (int)gsum;
   p.total_v = (int)vsum;
