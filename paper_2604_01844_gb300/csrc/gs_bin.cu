@@ -88,18 +88,24 @@ __global__ void __launch_bounds__(kSortThreads)
   int64_t lo, hi;
   chunk_of(st, G, lo, hi);
   uint32_t* own = sh_hist + (size_t)w * D * 32 + lane;  // LANE: counter of digit d at d * 32
-  for (int64_t i = lo + 4 * (int64_t)threadIdx.x; i < hi; i += 4 * (int64_t)blockDim.x) {
-    uint32_t k[4];
-    if (i + 4 <= hi) {
-      const uint4 q = *reinterpret_cast<const uint4*>(keys + i);
-      k[0] = q.x, k[1] = q.y, k[2] = q.z, k[3] = q.w;
-    } else {
+  // two 16-byte loads in flight per thread: keys [i, i + 4) and [i + 4 NT, i + 4 NT + 4)
+  constexpr int64_t kStep = 4 * (int64_t)kSortThreads;
+  for (int64_t i = lo + 4 * (int64_t)threadIdx.x; i < hi; i += 2 * kStep) {
+    uint32_t k[8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) k[j] = i + j < hi ? keys[i + j] : 0u;
+    for (int h = 0; h < 2; ++h) {
+      const int64_t ih = i + h * kStep;
+      if (ih + 4 <= hi) {
+        const uint4 q = *reinterpret_cast<const uint4*>(keys + ih);
+        k[4 * h] = q.x, k[4 * h + 1] = q.y, k[4 * h + 2] = q.z, k[4 * h + 3] = q.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[4 * h + j] = ih + j < hi ? keys[ih + j] : 0u;
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (i + j < hi) {
+    for (int j = 0; j < 8; ++j) {
+      if (i + (j >> 2) * kStep + (j & 3) < hi) {
         const uint32_t d = (k[j] >> shift) & mask;
         if (LANE)
           own[d * 32] += 1u;
@@ -173,27 +179,21 @@ __global__ void __launch_bounds__(kSortThreads)
   uint32_t* lstart = wcnt + NW * D;      // [D]
   uint32_t* tk = lstart + D;             // [kSortTile]
   uint32_t* tv = tk + kSortTile;         // [kSortTile]
-  __shared__ uint32_t part[kSortThreads];
   __shared__ uint32_t wtot[NW];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 
   // digit bases: exclusive scan of totals, each thread owning a contiguous run of digits
+  // (block-wide scan of the per-thread sums by warp shuffles and the warps' totals)
   const int per = (D + kSortThreads - 1) / kSortThreads;
-  uint32_t s0 = 0;
-  for (int d = t * per; d < min(D, t * per + per); ++d) s0 += totals[d];
-  part[t] = s0;
-  __syncthreads();
-  if (t == 0) {
-    uint32_t acc = 0;
-    for (int i = 0; i < kSortThreads; ++i) {
-      uint32_t x = part[i];
-      part[i] = acc;
-      acc += x;
-    }
-  }
-  __syncthreads();
   {
-    uint32_t acc = part[t];
+    uint32_t s0 = 0;
+    for (int d = t * per; d < min(D, t * per + per); ++d) s0 += totals[d];
+    const uint32_t incl = gsd::warp_inclusive_scan(s0);
+    if (lane == 31) wtot[w] = incl;
+    __syncthreads();
+    uint32_t acc = incl - s0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) acc += ww < w ? wtot[ww] : 0u;
     for (int d = t * per; d < min(D, t * per + per); ++d) {
       run[d] = acc + hist[(size_t)d * G + blockIdx.x];
       acc += totals[d];
