@@ -430,13 +430,12 @@ __global__ void __launch_bounds__(kThreads)
 // ------------------------------------------------------------------------------------------
 // Exponent of a footprint record at pixel offset (dx, dy), base 2 and pre-scaled by
 // -1/2 log2(e): e = a' dx^2 + b' dx dy + c' dy^2, evaluated as ((a' dx + b' dy) dx + c' dy^2)
-// with the row terms b' dy and c' dy^2 shared by every pixel of a row.  The forward, the
-// evaluation counter and the backward all decide the cut e > e_cut with this exact sequence.
+// with the row terms b' dy and c' dy^2 shared by every pixel of a row: per pixel
+// fma(fma(a', dx, b' dy), dx, c' dy^2), two pixels at a time in packed FP32x2 (each component
+// rounds like the scalar fmaf).  The forward, the evaluation counter and the backward all
+// decide the cut e > e_cut with this exact sequence.
 __device__ __forceinline__ float row_b(const float4 c, float dy) { return c.y * dy; }
 __device__ __forceinline__ float row_c(const float4 c, float dy) { return (c.z * dy) * dy; }
-__device__ __forceinline__ float expo(const float4 c, float dx, float bdy, float cdy2) {
-  return fmaf(fmaf(c.x, dx, bdy), dx, cdy2);
-}
 
 // Rows [ylo, yhi] (tile-local, clamped to [0, T-1]; ylo > yhi if none) that a record's cut
 // ellipse, enlarged like the tight tile rule (e > 1.001 e_cut), reaches inside the column
@@ -519,7 +518,6 @@ struct FwdBlocks {
   static constexpr int NBX = T / BW, NBY = T / 4, NB = NBX * NBY;
   static constexpr int NW = NB;  // one block per warp
   static constexpr int NT = 32 * NW;
-  static constexpr int NP = 2 * BW;  // float2 accumulators per lane (4 rows x BW / 2 pairs)
   static constexpr int SB = (T == 32 ? 2 : 4) * NT;  // records staged per batch
 };
 
@@ -608,44 +606,44 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
     }
     __syncwarp();
   }
-  if (COUNT) {
+  if constexpr (COUNT) {
     __syncthreads();
     const uint32_t ws = gsd::warp_sum(cnt_eval);
     if (lane == 0 && ws) atomicAdd(&s_cnt, (unsigned long long)ws);
     __syncthreads();
     if (t == 0 && s_cnt) atomicAdd((unsigned long long*)&st->evals, s_cnt);
-    return;
-  }
-  // butterfly reduce-scatter of the warp's 4 x BW pixel sums: at each stage a lane keeps the
-  // half of its pairs on its side of the partner bit and adds the partner's copy of that half;
-  // after log2(NPR) stages lane l holds the sum of pair l % NPR over its group of NPR lanes
+  } else {
+    // butterfly reduce-scatter of the warp's 4 x BW pixel sums: at each stage a lane keeps the
+    // half of its pairs on its side of the partner bit and adds the partner's copy of that half;
+    // after log2(NPR) stages lane l holds the sum of pair l % NPR over its group of NPR lanes
 #pragma unroll
-  for (int half = NPR / 2; half >= 1; half >>= 1) {
-    const bool up = (lane & half) != 0;
+    for (int half = NPR / 2; half >= 1; half >>= 1) {
+      const bool up = (lane & half) != 0;
 #pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float2 mine = up ? acc[i + half] : acc[i];
-      const float2 send = up ? acc[i] : acc[i + half];
-      float2 recv;
-      recv.x = __shfl_xor_sync(0xffffffffu, send.x, half);
-      recv.y = __shfl_xor_sync(0xffffffffu, send.y, half);
-      acc[i] = __fadd2_rn(mine, recv);
+      for (int i = 0; i < half; ++i) {
+        const float2 mine = up ? acc[i + half] : acc[i];
+        const float2 send = up ? acc[i] : acc[i + half];
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, half);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, half);
+        acc[i] = __fadd2_rn(mine, recv);
+      }
     }
-  }
-  // fewer pairs than lanes (BW = 8): the groups' sums are added across the remaining bits
+    // fewer pairs than lanes (BW = 8): the groups' sums are added across the remaining bits
 #pragma unroll
-  for (int k = NPR; k < 32; k <<= 1) {
-    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, acc[0].x, k),
-                                 __shfl_xor_sync(0xffffffffu, acc[0].y, k));
-    acc[0] = __fadd2_rn(acc[0], o);
+    for (int k = NPR; k < 32; k <<= 1) {
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, acc[0].x, k),
+                                   __shfl_xor_sync(0xffffffffu, acc[0].y, k));
+      acc[0] = __fadd2_rn(acc[0], o);
+    }
+    const int pi = lane % NPR;  // pair index: row pi / HP, columns 2 (pi % HP) + {0, 1}
+    if (lane >= NPR) return;
+    const int y = ty0 + byl + pi / HP, x = tx0 + bxl + 2 * (pi % HP);
+    if (y >= H) return;
+    float* row = img + I.img_off + ((int64_t)v * H + y) * W;
+    if (x < W) row[x] = acc[0].x;
+    if (x + 1 < W) row[x + 1] = acc[0].y;
   }
-  const int pi = lane % NPR;  // pair index: row pi / HP, columns 2 (pi % HP) + {0, 1}
-  if (lane >= NPR) return;
-  const int y = ty0 + byl + pi / HP, x = tx0 + bxl + 2 * (pi % HP);
-  if (y >= H) return;
-  float* row = img + I.img_off + ((int64_t)v * H + y) * W;
-  if (x < W) row[x] = acc[0].x;
-  if (x + 1 < W) row[x + 1] = acc[0].y;
 }
 
 // ------------------------------------------------------------------------------------------
