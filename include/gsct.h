@@ -390,6 +390,15 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);
 
+/* The projection terms of Eq. 5 in the two launches of gs_ssim2d_loss:
+ * l1_weight * mean |x - y| + ssim_weight * (1 - mean SSIM(x, y)), the L1 sum taken in the SSIM
+ * forward kernel and its gradient l1_weight * sign(x - y) / N (sign(0) = 0) added in the SSIM
+ * backward kernel.  Same arguments, workspace and errors as gs_ssim2d_loss, which is this call
+ * with l1_weight = 0. */
+int gs_l1_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W,
+                      float data_range, float l1_weight, float ssim_weight, float* d_loss,
+                      float* d_grad, int accumulate, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Allocation-free variant of gs_ssim2d_loss.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory themselves -- for instance a host
  * framework that owns the whole device memory budget and hands none to plug-ins, or a

@@ -138,13 +138,14 @@ class BatchReconstruction:
         for k in range(self.K):
             img, tgt, dimg = self.imgs[k], self.targets[k], self.dimgs[k]
             nv, H, W = img.shape
-            B.check(L.gs_l1_loss(B.ptr(img), B.ptr(tgt), img.numel(), 1.0, lp + 4 * k,
-                                 B.ptr(dimg), 0, s), "gs_l1_loss")
-            if cfg.alpha_ssim > 0:
-                B.check(L.gs_ssim2d_loss(B.ptr(img), B.ptr(tgt), nv, H, W, self.data_range[k],
-                                         cfg.alpha_ssim, lp + 4 * k, B.ptr(dimg), 1,
-                                         B.ptr(self.ssim_ws), self.ssim_ws.numel(), s),
-                        "gs_ssim2d_loss")
+            if cfg.alpha_ssim > 0:  # both terms in the two SSIM kernels
+                B.check(L.gs_l1_ssim2d_loss(B.ptr(img), B.ptr(tgt), nv, H, W, self.data_range[k],
+                                            1.0, cfg.alpha_ssim, lp + 4 * k, B.ptr(dimg), 0,
+                                            B.ptr(self.ssim_ws), self.ssim_ws.numel(), s),
+                        "gs_l1_ssim2d_loss")
+            else:
+                B.check(L.gs_l1_loss(B.ptr(img), B.ptr(tgt), img.numel(), 1.0, lp + 4 * k,
+                                     B.ptr(dimg), 0, s), "gs_l1_loss")
         if branch:
             main.wait_stream(self._side)
         self.projector.backward(*self.act, self.counts, self.dimg, grads=self.grads,

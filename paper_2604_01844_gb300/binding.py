@@ -145,6 +145,8 @@ SIGNATURES = {
     "gs_ssim3d_workspace_size": (_SZ, [_I64]),
     "gs_ssim2d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
                             _SZ, _P]),
+    "gs_l1_ssim2d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, _P, _P, _I, _P, _SZ, _P]),
     "gs_ssim3d_loss": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P, _I, _P,
                             _SZ, _P]),
     "gs_ssim2d_loss_noalloc": (_I, [_P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _P,

@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kThreads)
 
 // xy filtering and completion of a tile of one slice (an image of a 2D batch or a z-plane of a
 // volume; slice = blockIdx.z, nx x ny elements, channels cstride elements apart).
-//   MODE 0  2D forward: X, Y -> moments (x, y), (x^2, y^2) and x y -> SSIM, maps, loss
+//   MODE 0  2D forward: X, Y -> moments (x, y), (x^2, y^2) and x y -> SSIM, maps, loss (plus
+//           l1g * sum |x - y| over the tile when fused with an L1 term)
 //   MODE 1  3D forward: the five z-filtered moments -> SSIM, maps, loss
 //   MODE 2  backward (2D, or 3D after the z pass): maps m1, m2, m3 (filtered in z for 3D)
 //           -> dL/dx = w * m1 + 2 x (w * m2) + y (w * m3) (+ l1g sign(x - y) when fused
@@ -413,12 +414,16 @@ __global__ void __launch_bounds__(kSsimThreads)
   }
   // ---- completion
   const int x = blockIdx.x * kT2 + tx;
-  float contrib = 0.f;
+  float contrib = 0.f, l1 = 0.f;
 #pragma unroll
   for (int j = 0; j < kG; ++j) {
     const int y = blockIdx.y * kT2 + ty0 + j;
     if (x >= nx || y >= ny) continue;
     const size_t o = slice + (size_t)y * nx + x;
+    if (MODE == 0) {  // the pixel's (x, y), staged with the halo
+      const float2 xy = in2[0][ty0 + j + kR][tx + kR];
+      l1 += fabsf(xy.x - xy.y);
+    }
     if (MODE == 2) {
       const float xv = X[o], yv = Y[o];
       float g = f2[0][j].x + 2.f * xv * f2[0][j].y + yv * f1[0][j];
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(kSsimThreads)
       contrib += 1.f - Sv;
     }
   }
-  if (MODE != 2 && loss) block_add(contrib * (-gscale), loss);
+  if (MODE != 2 && loss) block_add(contrib * (-gscale) + (MODE == 0 ? l1g * l1 : 0.f), loss);
 }
 
 // Sets the dynamic shared-memory limit of the xy kernels that need more than 48 KB (host-side
@@ -568,18 +573,20 @@ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 namespace gs {
 namespace {
-// The two 2D SSIM launches: moments, SSIM and maps; then the gradient from the maps.
+// The two 2D SSIM launches: moments, SSIM and maps; then the gradient from the maps.  l1s
+// (the L1 weight over the pixel count, 0 for none) fuses an L1 term: its sum in the first
+// launch, its sign gradient in the second.
 int ssim2d(const float* d_x, const float* d_y, int H, int W, dim3 grid, float C1, float C2,
            float gscale, float* d_loss, float* maps, int64_t plane, float* d_grad,
-           int accumulate, cudaStream_t s) {
+           int accumulate, float l1s, cudaStream_t s) {
   const Win Wn = host_window();
   const dim3 block(kSsimThreads);
   GS_TRY(launch("ssim2d_fwd", k_ssim_xy<0>, grid, block, XyShape<0>::smem, s, Wn, d_x, d_y,
                 plane, W, H, C1, C2, gscale, d_loss, maps, (const float*)nullptr,
-                (const float*)nullptr, (float*)nullptr, 0, 0.f));
+                (const float*)nullptr, (float*)nullptr, 0, l1s));
   return launch("ssim2d_bwd", k_ssim_xy<2>, grid, block, XyShape<2>::smem, s, Wn,
                 (const float*)maps, (const float*)nullptr, plane, W, H, C1, C2, gscale,
-                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate, 0.f);
+                (float*)nullptr, (float*)nullptr, d_x, d_y, d_grad, accumulate, l1s);
 }
 }  // namespace
 }  // namespace gs
@@ -629,9 +636,9 @@ int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float
 
 size_t gs_ssim_workspace_size(int64_t n_elems) { return (size_t)(3 * n_elems) * sizeof(float) + 256; }
 
-int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, float data_range,
-                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
-                   size_t ws_bytes, void* stream) {
+int gs_l1_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W,
+                      float data_range, float l1_weight, float ssim_weight, float* d_loss,
+                      float* d_grad, int accumulate, void* d_ws, size_t ws_bytes, void* stream) {
   if (!d_x || !d_y || !d_grad || !d_ws || n_img < 1 || H < 1 || W < 1 || !(data_range > 0.f))
     return GS_ERR_ARG;
   if (n_img > 65535) return GS_ERR_ARG;
@@ -640,11 +647,18 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
   cudaStream_t s = (cudaStream_t)stream;
   const float C1 = (0.01f * data_range) * (0.01f * data_range);
   const float C2 = (0.03f * data_range) * (0.03f * data_range);
-  const float gscale = -weight / (float)plane;
+  const float gscale = -ssim_weight / (float)plane;
   const dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img);
   float* maps = (float*)d_ws;
   return ssim2d(d_x, d_y, H, W, grid, C1, C2, gscale, d_loss, maps, plane, d_grad, accumulate,
-                s);
+                l1_weight / (float)plane, s);
+}
+
+int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, float data_range,
+                   float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
+                   size_t ws_bytes, void* stream) {
+  return gs_l1_ssim2d_loss(d_x, d_y, n_img, H, W, data_range, 0.f, weight, d_loss, d_grad,
+                           accumulate, d_ws, ws_bytes, stream);
 }
 
 }  // extern "C"
@@ -706,7 +720,7 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
   const dim3 grid((W + kT2 - 1) / kT2, (H + kT2 - 1) / kT2, n_img);
   // kernel 1 writes every map entry kernel 2 reads, so the array needs no clearing between calls
   return ssim2d(d_x, d_y, H, W, grid, C1, C2, gscale, d_loss, maps, plane, d_grad, accumulate,
-                s);
+                0.f, s);
 }
 
 size_t gs_ssim3d_workspace_size(int64_t n_voxels) {

@@ -141,13 +141,14 @@ class Reconstruction:
         s = B.stream_handle()
         img, tgt, dimg = self.img[a:b], self.target[a:b], self.dimg[a:b]
         share = img.numel() / self.img.numel()
-        B.check(L.gs_l1_loss(B.ptr(img), B.ptr(tgt), img.numel(), share, B.ptr(self.loss),
-                             B.ptr(dimg), 0, s), "gs_l1_loss")
-        if self.cfg.alpha_ssim > 0:
-            B.check(L.gs_ssim2d_loss(B.ptr(img), B.ptr(tgt), b - a, self.H, self.W,
-                                     self.data_range, self.cfg.alpha_ssim * share,
-                                     B.ptr(self.loss), B.ptr(dimg), 1, B.ptr(ws), ws.numel(), s),
-                    "gs_ssim2d_loss")
+        if self.cfg.alpha_ssim > 0:  # both terms in the two SSIM kernels
+            B.check(L.gs_l1_ssim2d_loss(B.ptr(img), B.ptr(tgt), b - a, self.H, self.W,
+                                        self.data_range, share, self.cfg.alpha_ssim * share,
+                                        B.ptr(self.loss), B.ptr(dimg), 0, B.ptr(ws), ws.numel(),
+                                        s), "gs_l1_ssim2d_loss")
+        else:
+            B.check(L.gs_l1_loss(B.ptr(img), B.ptr(tgt), img.numel(), share, B.ptr(self.loss),
+                                 B.ptr(dimg), 0, s), "gs_l1_loss")
 
     def _tv_branch(self, accumulate: bool):
         """Voxelize -> TV (fused value and gradient) -> voxelizer backward into self.grads."""
@@ -188,14 +189,7 @@ class Reconstruction:
         self.projector.forward(*self.act, out=self.img)
         if target_ready is not None:
             torch.cuda.current_stream(self.device).wait_event(target_ready)
-        n_img = self.img.numel()
-        B.check(L.gs_l1_loss(B.ptr(self.img), B.ptr(self.target), n_img, 1.0, B.ptr(self.loss),
-                             B.ptr(self.dimg), 0, s), "gs_l1_loss")
-        if cfg.alpha_ssim > 0:
-            B.check(L.gs_ssim2d_loss(B.ptr(self.img), B.ptr(self.target), self.img.shape[0],
-                                     self.H, self.W, self.data_range, cfg.alpha_ssim,
-                                     B.ptr(self.loss), B.ptr(self.dimg), 1, B.ptr(self.ssim_ws),
-                                     self.ssim_ws.numel(), s), "gs_ssim2d_loss")
+        self._image_losses(0, self.img.shape[0], self.ssim_ws)
         if branch:
             main.wait_stream(self._side)
         self.projector.backward(*self.act, self.dimg, grads=self.grads, accumulate=branch,

@@ -43,6 +43,11 @@ def _run_loss(B, name, x, y, *extra, ws=None, weight=1.0, accumulate_into=None):
         n, H, W = x.shape
         rc = L.gs_ssim2d_loss(B.ptr(xd), B.ptr(yd), n, H, W, extra[0], weight, B.ptr(loss),
                               B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
+    elif name == "l1ssim2d":  # extra = (data range, L1 weight); weight = SSIM weight
+        wsb = torch.empty(L.gs_ssim_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
+        n, H, W = x.shape
+        rc = L.gs_l1_ssim2d_loss(B.ptr(xd), B.ptr(yd), n, H, W, extra[0], extra[1], weight,
+                                 B.ptr(loss), B.ptr(grad), acc, B.ptr(wsb), wsb.numel(), _s())
     else:
         wsb = torch.empty(L.gs_ssim3d_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
         dz, dy, dx = x.shape
@@ -88,6 +93,29 @@ def test_ssim2d(B, shape):
     assert abs(val - want) <= 2e-5 * max(1.0, abs(want)), (val, want)
     scale = np.abs(gw).max()
     assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
+
+
+@pytest.mark.parametrize("shape", [(3, 37, 53), (2, 64, 64), (1, 5, 7)])
+def test_l1_ssim2d_fused(B, shape):
+    """L1 + D-SSIM in the two SSIM kernels equals the oracle's sum of both terms, and the
+    separate L1 and SSIM calls, value and gradient; accumulate adds onto the gradient."""
+    rng = np.random.default_rng(5)
+    y = _x32(rng.random(shape))
+    x = _x32(np.clip(y + 0.1 * rng.standard_normal(shape), 0, None))
+    x.flat[::7] = y.flat[::7]  # ties: sign(0) = 0 on both paths
+    L = float(y.max())
+    val, g = _run_loss(B, "l1ssim2d", x, y, L, 0.6, weight=0.25)
+    want, gw = OL.value_and_grad(lambda a, b: 0.6 * OL.l1(a, b) + 0.25 * (1 - OL.ssim2d(a, b, L)),
+                                 x, y)
+    assert abs(val - want) <= 2e-5 * max(1.0, abs(want)), (val, want)
+    scale = np.abs(gw).max()
+    assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
+    v1, g1 = _run_loss(B, "l1", x, y, weight=0.6)
+    v2, g2 = _run_loss(B, "ssim2d", x, y, L, weight=0.25, accumulate_into=g1)
+    assert abs(val - (v1 + v2)) <= 1e-5 * max(1.0, abs(val))
+    np.testing.assert_allclose(g, g2, rtol=1e-5, atol=1e-6 * scale)
+    va, ga = _run_loss(B, "l1ssim2d", x, y, L, 0.6, weight=0.25, accumulate_into=np.ones_like(x))
+    np.testing.assert_allclose(ga, g + 1.0, rtol=1e-6, atol=1e-7)
 
 
 @pytest.mark.parametrize("shape", [(21, 19, 35), (12, 16, 16), (4, 40, 33), (1, 9, 70)])
