@@ -90,6 +90,13 @@ def test_argument_errors_are_host_side(built):
     # misaligned workspace pointer
     rc = L.gs_project(16, 16, 16, 10, 16, 1, 8, 8, ctypes.byref(o), 16, 17, 1 << 20, None)
     assert rc == binding.GS_ERR_ARG
+    # image losses: null inputs, a non-positive data range, a workspace below the 3 maps
+    rc = L.gs_l1_ssim2d_loss(None, 16, 1, 8, 8, 1.0, 1.0, 0.2, 16, 16, 0, 16, 1 << 20, None)
+    assert rc == binding.GS_ERR_ARG
+    rc = L.gs_l1_ssim2d_loss(16, 16, 1, 8, 8, 0.0, 1.0, 0.2, 16, 16, 0, 16, 1 << 20, None)
+    assert rc == binding.GS_ERR_ARG
+    rc = L.gs_l1_ssim2d_loss(16, 16, 1, 8, 8, 1.0, 1.0, 0.2, 16, 16, 0, 16, 64, None)
+    assert rc == binding.GS_ERR_CAPACITY
 
 
 def test_batch_table_validation(built):
