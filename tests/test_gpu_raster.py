@@ -58,6 +58,14 @@ def test_forward_ragged_detector(orc, gsct):
         _image_parity(orc, gsct, mr, sc, qt, views, 83, 45, tile)
 
 
+def test_forward_single_tile_views(orc, gsct):
+    """Views that fit in one tile (tile 32: no tile bits, the lists need no sort pass) and in
+    four (tile 16: a 2-bit sort)."""
+    mr, sc, qt, views = _case(8, 600, 5, 24, 20, median=0.03)
+    for tile in (32, 16):
+        _image_parity(orc, gsct, mr, sc, qt, views, 24, 20, tile)
+
+
 def test_forward_parallel_beam(orc, gsct):
     mr, sc, qt = synth.gaussians(2, 800, scale_median=0.03)
     views = synth.parallel_views(4, 48, 40)
