@@ -625,6 +625,41 @@ def test_ssim_constant_images_interior():
     assert full != 1.0
 
 
+def _ssim_by_scipy(x, y, L, sigma):
+    """Mean SSIM (Wang et al. 2004) with the local statistics taken by scipy's separable
+    Gaussian filter (sigma 1.5, radius 5 = the 11-tap window, zero padding): a filtering path
+    independent of the oracle's convolutions."""
+    from scipy import ndimage
+    def filt(t):
+        return ndimage.gaussian_filter(t, sigma=sigma, mode="constant", cval=0.0,
+                                       truncate=5.0 / 1.5)
+    C1, C2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    mx, my = filt(x), filt(y)
+    vx, vy, cxy = filt(x * x) - mx * mx, filt(y * y) - my * my, filt(x * y) - mx * my
+    s = (2 * mx * my + C1) * (2 * cxy + C2) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+    return float(s.mean())
+
+
+def test_ssim_matches_scipy_gaussian_filter():
+    """Random images and volumes with non-zero local variances (so C2, the covariance term
+    and the zero-padded borders all matter): the oracle's SSIM equals the one built on
+    scipy's Gaussian filter, in 2D (per image) and 3D."""
+    pytest.importorskip("scipy")
+    from oracle import losses
+    rng = np.random.default_rng(11)
+    y = rng.random((2, 13, 17))
+    x = np.clip(y + 0.2 * rng.standard_normal(y.shape), 0, None)
+    for L in (1.0, 0.2):
+        want = _ssim_by_scipy(x, y, L, sigma=(0, 1.5, 1.5))
+        got = float(losses.ssim2d(torch.from_numpy(x), torch.from_numpy(y), L))
+        assert abs(got - want) < 1e-12, (L, got, want)
+    v = rng.random((9, 12, 14))
+    u = np.clip(v + 0.2 * rng.standard_normal(v.shape), 0, None)
+    want = _ssim_by_scipy(u, v, 1.0, sigma=1.5)
+    got = float(losses.ssim3d(torch.from_numpy(u), torch.from_numpy(v), 1.0))
+    assert abs(got - want) < 1e-12, (got, want)
+
+
 def test_tv_ramp_and_psnr():
     from oracle import losses
     D, H, W = 5, 6, 7
