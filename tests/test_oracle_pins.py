@@ -782,3 +782,30 @@ def test_brick_render_reference_special_case():
          ((ax[:, None, None] - 4.0) / s[2]) ** 2)
     want = np.where(q < 9, want, 0.0)
     np.testing.assert_allclose(img.numpy(), want, atol=1e-12)
+
+
+def test_brick_render_rotated_matches_voxelizer(orc):
+    """The MLP's brick renderer for one rotated, off-centre Gaussian (the other 31 at zero
+    density) equals the main oracle's voxelizer of the decoded Gaussian on the brick's 16^3
+    unit-voxel grid: the two share no code, so this pins the renderer's quaternion convention,
+    its inverse covariance and its 3-sigma cut against the pinned projection-side rotation."""
+    from oracle import mlp as OM
+    raw = torch.zeros(1, 352, dtype=torch.float64)
+    r = raw.view(1, 32, 11)
+    r[:, :, 10] = -60.0
+    g = 21  # lattice cell (1, 1, 1)
+    r[0, g, 0:3] = torch.tensor([0.3, -0.2, 0.1])
+    r[0, g, 3:6] = torch.tensor([0.4, -0.3, 0.2])
+    r[0, g, 6:10] = torch.tensor([0.2, 0.5, -0.3, 0.4])
+    r[0, g, 10] = 2.0
+    img = OM.render(raw, margin=0)[0].reshape(16, 16, 16).numpy()
+    c, s, q, rho = (t[0, g].numpy() for t in OM.decode(r))
+    P = orc.params64(np.array([[c[0], c[1], c[2], rho]]), np.array([[s[0], s[1], s[2], 0.0]]),
+                     np.array([q]))
+    grid = synth.cube_grid(16)
+    grid["origin"] = (0.0, 0.0, 0.0)
+    grid["voxel"] = (1.0, 1.0, 1.0)
+    vol, _ = orc.voxelize(P, grid)
+    # the other 31 Gaussians add at most 31 * softplus(-60) ~ 3e-25
+    np.testing.assert_allclose(img, vol, rtol=1e-9, atol=1e-20)
+    assert vol.max() > 0.5 and (vol > 0).sum() > 100
