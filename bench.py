@@ -111,7 +111,7 @@ def measured_peaks():
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -132,7 +132,10 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Stops sampling and summarises the samples whose timestamps fall in window = (t0, t1)
+        (host epoch seconds around the timed region; all samples when none do or when the
+        timestamps cannot be read)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -141,26 +144,47 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, val in zip(names, parts[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(nm)
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return summarise_clocks(lines, window)
+
+
+def _stamp(text):
+    """nvidia-smi's local timestamp ('YYYY/MM/DD HH:MM:SS.mmm') as epoch seconds, or None."""
+    import datetime
+
+    try:
+        return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
+
+
+def summarise_clocks(lines, window=None):
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            sm, mx = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        active = {nm for nm, val in zip(names, parts[6:10]) if val.lower() == "active"}
+        rows.append((_stamp(parts[0]), sm, mx, active))
+    if not rows:
+        return None
+    inside = rows
+    if window is not None:
+        t0, t1 = window
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+    scope = "timed region"
+    if not inside:
+        inside, scope = rows, "whole run of the sampler (no sample inside the timed region)"
+    return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+            "samples": len(inside), "reasons": sorted(set().union(*(r[3] for r in inside))),
+            "scope": scope}
 
 
 # ------------------------------------------------------------------------------------------
@@ -228,12 +252,14 @@ def run_ours(args, ws, rank, local):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_start = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         rec.step()
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    t_end = time.time()
+    clk = clocks.stop((t_start, t_end))
     launches = B.launch_count() - launches0
     ms = R.slowest(e0.elapsed_time(e1) / args.steps, device)
     loss = float(rec.loss.item())
@@ -1097,7 +1123,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

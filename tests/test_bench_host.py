@@ -1,0 +1,28 @@
+"""Host-side pieces of bench.py: the clock record keeps only samples inside the timed region."""
+import datetime
+import time
+
+import bench
+
+
+def _line(t, sm, power_cap="Not Active"):
+    ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return (f"{ts}, 0, {sm}, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, "
+            f"Not Active, {power_cap}\n")
+
+
+def test_clock_summary_keeps_the_timed_window():
+    now = time.time()
+    lines = [_line(now - 1.0, 345), _line(now + 0.1, 2070), _line(now + 0.3, 2055, "Active"),
+             _line(now + 0.5, 2070), _line(now + 2.0, 400)]
+    c = bench.summarise_clocks(lines, (now, now + 1.0))
+    assert c["samples"] == 3 and c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["scope"] == "timed region"
+
+
+def test_clock_summary_falls_back_and_rejects_garbage():
+    now = time.time()
+    lines = [_line(now, 2000), _line(now + 0.2, 2070)]
+    c = bench.summarise_clocks(lines, (now + 10, now + 11))
+    assert c["samples"] == 2 and c["scope"].startswith("whole run")
+    assert bench.summarise_clocks(["garbage\n", ""], (now, now + 1)) is None
