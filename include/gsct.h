@@ -606,7 +606,7 @@ int gs_fit_volume_status(const void* d_ws, size_t ws_bytes, int n, const gs_grid
 
 /* ---------------------------------------------------------------------------------------
  * BF16 tensor-core GEMM (tcgen05, tensor memory, TMA) and helpers of the per-brick MLP
- * initializer.  The paper has no learned initializer; the MLP is this build's addition.
+ * initializer.  The paper has no learned initializer; the MLP is an addition to its method.
  * ------------------------------------------------------------------------------------- */
 
 #define GS_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up (recorded in *d_err) */
