@@ -26,3 +26,25 @@ def test_clock_summary_falls_back_and_rejects_garbage():
     c = bench.summarise_clocks(lines, (now + 10, now + 11))
     assert c["samples"] == 2 and c["scope"].startswith("whole run")
     assert bench.summarise_clocks(["garbage\n", ""], (now, now + 1)) is None
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one JSON line with
+    the contract's keys; a tiny time budget makes each step a prefix of the Gaussians."""
+    import argparse
+    import json
+
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 0.5)
+    bench.run_reference(argparse.Namespace(steps=2, warmup=1), 1, 0)
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert "the first" in d["cpu_baseline"]["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # rank > 0 prints nothing
+    bench.run_reference(argparse.Namespace(steps=2, warmup=1), 2, 1)
+    assert capsys.readouterr().out == ""
