@@ -46,7 +46,11 @@ def adam_step(raw, m, v, grads_act, t, lr, beta1, beta2, eps, min_log_scale, max
         vv += (1 - beta2) * g * g
         mhat = mm / (1 - beta1 ** t)
         vhat = vv / (1 - beta2 ** t)
-        out.append(p - lrv * mhat / (np.sqrt(vhat) + eps))
+        # a component whose gradients have all been zero has m = v = 0 and does not move
+        # (with eps = 0 the quotient would read 0/0)
+        den = np.sqrt(vhat) + eps
+        step = np.divide(mhat, den, out=np.zeros_like(mhat), where=den > 0)
+        out.append(p - lrv * step)
     out[1][:, :3] = np.clip(out[1][:, :3], min_log_scale, max_log_scale)
     out[1][:, 3] = raw_sc[:, 3]
     return out

@@ -674,21 +674,167 @@ def test_tv_ramp_and_psnr():
 
 def test_adam_reference_special_cases():
     """With beta1 = beta2 = 0 and no bias correction left, Adam moves every raw parameter by
-    lr * g / (|g| + eps); the activations are softplus/exp as stated."""
+    lr * g / (|g| + eps); the activations are softplus/exp as stated (against numpy's
+    logaddexp, a library form of log(1 + e^x))."""
     from oracle import optim as OO
     rng = np.random.default_rng(0)
     raw = [rng.standard_normal((5, 4)) for _ in range(3)]
     raw[1][:, 3] = 0
     g = [rng.standard_normal((5, 4)) for _ in range(3)]
+    g[1][:, 3] = 0
     m = [np.zeros((5, 4)) for _ in range(3)]
     v = [np.zeros((5, 4)) for _ in range(3)]
-    out = OO.adam_step(raw, m, v, g, 1, (0.1, 0.2, 0.3, 0.4), 0.0, 0.0, 0.0, -50, 50)
+    with np.errstate(all="raise"):
+        out = OO.adam_step(raw, m, v, g, 1, (0.1, 0.2, 0.3, 0.4), 0.0, 0.0, 0.0, -50, 50)
     graw_q = g[2]
     np.testing.assert_allclose(out[2], raw[2] - 0.4 * np.sign(graw_q), atol=1e-12)
     np.testing.assert_allclose(out[0][:, :3], raw[0][:, :3] - 0.1 * np.sign(g[0][:, :3]), atol=1e-12)
+    assert np.array_equal(out[1][:, 3], raw[1][:, 3])
     mr, sc, q = OO.activate(*raw)
-    np.testing.assert_allclose(mr[:, 3], np.log1p(np.exp(raw[0][:, 3])), rtol=1e-12)
+    np.testing.assert_allclose(mr[:, 3], np.logaddexp(0.0, raw[0][:, 3]), rtol=1e-12)
     np.testing.assert_allclose(sc[:, :3], np.exp(raw[1][:, :3]), rtol=1e-12)
+
+
+# Pins of Adam with beta != 0 (Kingma and Ba 2015, Algorithm 1: m_t = b1 m + (1 - b1) g,
+# v_t = b2 v + (1 - b2) g^2, m^_t = m_t / (1 - b1^t), v^_t = v_t / (1 - b2^t),
+# theta_t = theta - lr m^_t / (sqrt(v^_t) + eps)).  Each helper takes an adam_step-like
+# function, so the same checks also run against planted mutations of the oracle below.
+_B1, _B2 = 0.9, 0.999
+_LR = (0.01, 0.02, 0.03, 0.04)
+
+
+def _adam_run(step_fn, raw0, grads, eps, lo=-50.0, hi=50.0):
+    raw = [a.copy() for a in raw0]
+    m = [np.zeros_like(a) for a in raw0]
+    v = [np.zeros_like(a) for a in raw0]
+    for t, g in enumerate(grads, start=1):
+        raw = step_fn(raw, m, v, g, t, _LR, _B1, _B2, eps, lo, hi)
+    return raw
+
+
+def _adam_pin_constant_gradient(step_fn):
+    """A constant gradient g on the chain-free components (mean, quaternion): the bias
+    correction makes m^_t = g and v^_t = g^2 exactly for every t, so each of 5 steps moves
+    the raw value by lr g / (|g| + eps).  Catches a missing bias correction, a bias
+    correction taken with t - 1 and a wrong decay in either moment."""
+    rng = np.random.default_rng(21)
+    raw0 = [rng.standard_normal((6, 4)) for _ in range(3)]
+    raw0[1][:, 3] = 0
+    g = [rng.standard_normal((6, 4)) for _ in range(3)]
+    g[1][:] = 0  # scale: no gradient, stays put
+    eps = 1e-3
+    with np.errstate(all="ignore"):
+        out = _adam_run(step_fn, raw0, [g] * 5, eps)
+    want_q = raw0[2] - 5 * _LR[3] * g[2] / (np.abs(g[2]) + eps)
+    want_m = raw0[0][:, :3] - 5 * _LR[0] * g[0][:, :3] / (np.abs(g[0][:, :3]) + eps)
+    return (np.allclose(out[2], want_q, rtol=0, atol=1e-12)
+            and np.allclose(out[0][:, :3], want_m, rtol=0, atol=1e-12)
+            and np.array_equal(out[1], raw0[1]))
+
+
+def _adam_pin_alternating_gradient(step_fn):
+    """Gradients +g, -g, +g on the quaternion, worked by hand from the definition:
+    m_1 = 0.1 g, m_2 = -0.01 g, m_3 = 0.091 g; v^_t = g^2 for every t (g^2 is constant);
+    m^_t = g, -0.01/0.19 g, 0.091/0.271 g.  With eps = 0 the three updates are
+    -lr sign(g) (1 - 1/19 + 91/271).  Catches swapped beta1 / beta2 (m^_2 would be -5e-4 g)."""
+    rng = np.random.default_rng(22)
+    raw0 = [rng.standard_normal((4, 4)) for _ in range(3)]
+    raw0[1][:, 3] = 0
+    g = [np.zeros((4, 4)) for _ in range(3)]
+    g[2] = rng.standard_normal((4, 4))
+    neg = [-a for a in g]
+    with np.errstate(all="ignore"):
+        out = _adam_run(step_fn, raw0, [g, neg, g], 0.0)
+    want = raw0[2] - _LR[3] * np.sign(g[2]) * (1.0 - 1.0 / 19.0 + 91.0 / 271.0)
+    return np.allclose(out[2], want, rtol=0, atol=1e-12)
+
+
+def _adam_pin_activation_chain(step_fn):
+    """The density and scale gradients arrive with respect to the activated values and are
+    chained to the raw ones: g_raw = g_act d(activation)/d(raw).  With beta1 = beta2 = 0 and
+    eps = 10 the first step moves a raw value by lr g_raw / (|g_raw| + 10), a one-to-one
+    function of g_raw, and g_raw is taken here by FP64 central differences of the oracle's
+    own activate().  Catches a dropped sigmoid (softplus') or exp (scale) factor, which a
+    sign-only check cannot see."""
+    from oracle import optim as OO
+    rng = np.random.default_rng(23)
+    n = 6
+    raw0 = [rng.standard_normal((n, 4)) for _ in range(3)]
+    raw0[1][:, :3] = np.log(0.05) + 0.5 * raw0[1][:, :3]
+    raw0[1][:, 3] = 0
+    g = [rng.standard_normal((n, 4)) * 3.0 for _ in range(3)]
+    g[1][:, 3] = 0
+    h = 1e-6
+    jr = np.zeros(n)
+    js = np.zeros((n, 3))
+    up = [a.copy() for a in raw0]
+    dn = [a.copy() for a in raw0]
+    up[0][:, 3] += h; dn[0][:, 3] -= h
+    up[1][:, :3] += h; dn[1][:, :3] -= h
+    a_up, a_dn = OO.activate(*up), OO.activate(*dn)
+    jr = (a_up[0][:, 3] - a_dn[0][:, 3]) / (2 * h)
+    js = (a_up[1][:, :3] - a_dn[1][:, :3]) / (2 * h)
+    eps = 10.0
+    m = [np.zeros_like(a) for a in raw0]
+    v = [np.zeros_like(a) for a in raw0]
+    with np.errstate(all="ignore"):
+        out = step_fn([a.copy() for a in raw0], m, v, g, 1, _LR, 0.0, 0.0, eps, -50.0, 50.0)
+    g_rho = g[0][:, 3] * jr
+    g_sc = g[1][:, :3] * js
+    want_rho = raw0[0][:, 3] - _LR[1] * g_rho / (np.abs(g_rho) + eps)
+    want_sc = raw0[1][:, :3] - _LR[2] * g_sc / (np.abs(g_sc) + eps)
+    return (np.allclose(out[0][:, 3], want_rho, rtol=0, atol=1e-9)
+            and np.allclose(out[1][:, :3], want_sc, rtol=0, atol=1e-9))
+
+
+def _adam_pin_scale_clamp(step_fn):
+    """The log-scale is clamped to [min, max] after the update; a large step hits both."""
+    raw0 = [np.zeros((2, 4)) for _ in range(3)]
+    raw0[1][:, :3] = [[-0.995, 0.0, 0.995], [0.5, -0.5, 0.2]]
+    g = [np.zeros((2, 4)) for _ in range(3)]
+    g[1][:, :3] = [[1.0, 0.0, -1.0], [0.0, 0.0, 0.0]]
+    with np.errstate(all="ignore"):
+        out = step_fn([a.copy() for a in raw0], [np.zeros((2, 4)) for _ in range(3)],
+                      [np.zeros((2, 4)) for _ in range(3)], g, 1, (0.0, 0.0, 1.0, 0.0),
+                      0.0, 0.0, 0.0, -1.0, 1.0)
+    return np.allclose(out[1][0, :3], [-1.0, 0.0, 1.0], atol=1e-15) and \
+        np.allclose(out[1][1, :3], raw0[1][1, :3], atol=1e-15)
+
+
+_ADAM_PINS = (_adam_pin_constant_gradient, _adam_pin_alternating_gradient,
+              _adam_pin_activation_chain, _adam_pin_scale_clamp)
+
+
+@pytest.mark.parametrize("pin", _ADAM_PINS, ids=lambda f: f.__name__[10:])
+def test_adam_pins(pin):
+    from oracle import optim as OO
+    assert pin(OO.adam_step)
+
+
+def _mutant_adam(old, new):
+    """The oracle's adam_step with one planted mistake (source text replaced), on the CPU."""
+    import inspect
+    from oracle import optim as OO
+    src = inspect.getsource(OO.adam_step)
+    assert old in src, old
+    ns = dict(vars(OO))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns["adam_step"]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("mhat = mm / (1 - beta1 ** t)", "mhat = mm"),                         # no bias correction
+    ("vhat = vv / (1 - beta2 ** t)", "vhat = vv"),
+    ("1 - beta1 ** t", "1 - beta1 ** (t - 1) + 1e-300"),                   # t - 1
+    ("1 - beta2 ** t", "1 - beta2 ** (t - 1) + 1e-300"),
+    ("* sigmoid(raw_mr[:, 3])", ""),                                        # dropped sigmoid
+    ("* np.exp(raw_sc[:, :3])", ""),                                        # dropped exp
+    ("mm *= beta1", "mm *= beta2"),                                         # swapped betas
+])
+def test_adam_pins_catch_planted_mutations(old, new):
+    """Every planted mistake fails at least one of the pins above."""
+    fn = _mutant_adam(old, new)
+    assert not all(pin(fn) for pin in _ADAM_PINS), (old, new)
 
 
 # ------------------------------------------------------------------------------------------
