@@ -435,6 +435,7 @@ def run_ours(args, ws, rank, local):
                                                    det=args.warm_det),
             "adaptive_control": lambda: adaptive_control(device),
             "compression": lambda: compression(device),
+            "gemm": lambda: gemm_rate(device),
         }
         chosen = list(legs) if args.extras == "all" else args.extras.split(",")
         for name in chosen:
@@ -1004,7 +1005,9 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     e1 = torch.cuda.Event(enable_timing=True)
     loss = torch.zeros(iters, device=device)
     e0.record()
+    torch.cuda.nvtx.range_push("fit_volume_timed")  # lets a profiler select these launches
     f.run(gt, iters, opts, None, loss)
+    torch.cuda.nvtx.range_pop()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
@@ -1046,6 +1049,55 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
             "hbm_rooflines": hbm_roofs,
             "hbm_note": "achieved = algorithmic bytes per voxel x voxels / kernel ms; the voxel "
                         "kernels are evaluation-bound (see their ALU rooflines in the step)"}
+
+
+def gemm_rate(device, M=118016, reps=20, warmup=3):
+    """CUDA-event throughput of the tcgen05 BF16 GEMM (gs_gemm_bf16) at the per-brick MLP's
+    layer shapes for M bricks (forward layers, the first layer's weight gradient and a hidden
+    layer's input gradient), against the measured bf16 peak.  2 M N K flops per call."""
+    import torch
+
+    from paper_2604_01844_gb300 import binding as B
+
+    shapes = {"fwd_l1 (Mx256x4096)": (M, 256, 4096), "fwd_l2 (Mx256x256)": (M, 256, 256),
+              "fwd_l4 (Mx384x256)": (M, 384, 256), "dW_l1 (256x4096xM)": (256, 4096, M),
+              "dX_l4 (Mx256x384)": (M, 256, 384)}
+    mp = measured_peaks() or {}
+    peak = mp.get("bf16_tflops")
+    err = torch.zeros(1, dtype=torch.int32, device=device)
+    out = {}
+    g = torch.Generator(device=device)
+    g.manual_seed(0)
+    for name, (m, n, k) in shapes.items():
+        a = torch.randn((m, k), device=device, generator=g).to(torch.bfloat16)
+        b = torch.randn((n, k), device=device, generator=g).to(torch.bfloat16)
+        c = torch.empty((m, n), device=device, dtype=torch.bfloat16)
+        s = B.stream_handle()
+
+        def call():
+            B.check(B.lib().gs_gemm_bf16(B.ptr(a), B.ptr(b), m, n, k, None, 0, None, B.ptr(c), n,
+                                         B.ptr(err), s), "gs_gemm_bf16")
+
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tf = 2.0 * m * n * k / (ms * 1e-3) / 1e12
+        out[name] = {"ms": round(ms, 4), "tflops": round(tf, 1),
+                     "frac_of_measured_bf16": round(tf / peak, 3) if peak else None}
+        del a, b, c
+    out["status"] = int(err.item())
+    out["peak_tflops"] = peak
+    out["note"] = ("back-to-back calls of one shape (operands L2-resident for the smaller ones); "
+                   "BF16 output, no bias")
+    return out
 
 
 def read_traffic(kernel: str):
@@ -1161,7 +1213,7 @@ def main():
     ap.add_argument("--extras", default="all",
                     help="comma-separated study legs to run after the headline step "
                          "(time_to_psnr, learned_init, batched, fit_volume, scale_up, "
-                         "warm_start, adaptive_control, compression) or 'all'")
+                         "warm_start, adaptive_control, compression, gemm) or 'all'")
     ap.add_argument("--fit-side", type=int, default=1024)
     ap.add_argument("--fit-gaussians", type=int, default=500000)
     ap.add_argument("--warm-side", type=int, default=512)

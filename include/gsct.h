@@ -409,9 +409,12 @@ int gs_l1_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int 
  *   - n_img * H * W above GS_SSIM2D_NOALLOC_MAX_PIXELS returns GS_ERR_CAPACITY (message in
  *     gs_last_error) before any launch.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *     with that device current) and caches it; make that first call before any stream
- *     capture.  The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
- *     routine).
+ *     with that device current) and caches it.  With CUDA's lazy module loading that lookup
+ *     may load this library's loss module on the device, which is when the 24 MiB array is
+ *     reserved, and it may synchronise the device: make the first call outside latency-
+ *     critical regions and before any stream capture.  Apart from that one-time module load
+ *     the call allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ *   - d_loss may be NULL (gradient only); accumulate = 1 adds the gradient to d_grad.
  *   - All calls share the one array, which keeps the last call's contents; every entry a call
  *     reads it writes first, so nothing needs clearing.  Calls whose kernels overlap on the
  *     GPU (e.g. on two streams at once) race on the array: serialise them.

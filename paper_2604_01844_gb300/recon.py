@@ -99,6 +99,9 @@ class Reconstruction:
         o.min_log_scale, o.max_log_scale = cfg.min_log_scale, cfg.max_log_scale
         self.adam_opts = o
         self.density_stats = None  # (grad_stat, vis) accumulated by the backward when set
+        # weight of these views' image terms in the loss: the fraction of all the problem's
+        # views they are (1 unless the views are sharded over several processes)
+        self.view_share = 1.0
         self.activate()
         self.plan()
 
@@ -140,7 +143,7 @@ class Reconstruction:
         L = B.lib()
         s = B.stream_handle()
         img, tgt, dimg = self.img[a:b], self.target[a:b], self.dimg[a:b]
-        share = img.numel() / self.img.numel()
+        share = self.view_share * (img.numel() / self.img.numel())
         if self.cfg.alpha_ssim > 0:  # both terms in the two SSIM kernels
             B.check(L.gs_l1_ssim2d_loss(B.ptr(img), B.ptr(tgt), b - a, self.H, self.W,
                                         self.data_range, share, self.cfg.alpha_ssim * share,
@@ -196,11 +199,16 @@ class Reconstruction:
                                 reuse=not cfg.recompute_lists, stats=self.density_stats)
         if cfg.alpha_tv > 0 and not branch:
             self._tv_branch(accumulate=True)
+        self._before_adam()
         B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
                                *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),
                 "gs_adam_step")
         return self.loss
+
+    def _before_adam(self):
+        """Runs on the current stream once the step's gradients and loss are complete, just
+        before the Adam update (the view-sharded step sums them over processes here)."""
 
     def _step_pipelined(self, target_ready=None):
         """The step with the views in chunks, chunk 0 on the current stream and chunk k on
@@ -241,6 +249,7 @@ class Reconstruction:
             main.wait_stream(st)
             for dst, src in zip(self.grads, g):
                 B.check(L.gs_add(B.ptr(dst), B.ptr(src), dst.numel(), s), "gs_add")
+        self._before_adam()
         B.check(L.gs_adam_step(*[B.ptr(t) for t in self.raw], B.ptr(self.m), B.ptr(self.v),
                                *[B.ptr(t) for t in self.grads], *[B.ptr(t) for t in self.act],
                                self.n, B.ptr(self.step_count), ctypes.byref(self.adam_opts), s),

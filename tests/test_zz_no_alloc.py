@@ -32,23 +32,25 @@ def _inputs(seed, shape):
     return torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), float(y.max())
 
 
-def _workspace_version(B, x, y, L, weight):
+def _workspace_version(B, x, y, L, weight, grad0=None, with_loss=True):
     n, H, W = x.shape
     loss = torch.zeros(1, device="cuda")
-    grad = torch.zeros_like(x)
+    grad = torch.zeros_like(x) if grad0 is None else grad0.clone()
     ws = torch.empty(B.lib().gs_ssim_workspace_size(x.numel()), dtype=torch.uint8, device="cuda")
-    B.check(B.lib().gs_ssim2d_loss(B.ptr(x), B.ptr(y), n, H, W, L, weight, B.ptr(loss),
-                                   B.ptr(grad), 0, B.ptr(ws), ws.numel(),
+    B.check(B.lib().gs_ssim2d_loss(B.ptr(x), B.ptr(y), n, H, W, L, weight,
+                                   B.ptr(loss) if with_loss else None, B.ptr(grad),
+                                   0 if grad0 is None else 1, B.ptr(ws), ws.numel(),
                                    torch.cuda.current_stream().cuda_stream), "gs_ssim2d_loss")
     return loss, grad
 
 
-def _noalloc_version(B, x, y, L, weight):
+def _noalloc_version(B, x, y, L, weight, grad0=None, with_loss=True):
     n, H, W = x.shape
     loss = torch.zeros(1, device="cuda")
-    grad = torch.zeros_like(x)
-    B.check(B.lib().gs_ssim2d_loss_noalloc(B.ptr(x), B.ptr(y), n, H, W, L, weight, B.ptr(loss),
-                                           B.ptr(grad), 0,
+    grad = torch.zeros_like(x) if grad0 is None else grad0.clone()
+    B.check(B.lib().gs_ssim2d_loss_noalloc(B.ptr(x), B.ptr(y), n, H, W, L, weight,
+                                           B.ptr(loss) if with_loss else None, B.ptr(grad),
+                                           0 if grad0 is None else 1,
                                            torch.cuda.current_stream().cuda_stream),
             "gs_ssim2d_loss_noalloc")
     return loss, grad
@@ -65,6 +67,25 @@ def test_noalloc_matches_workspace_version_twice(B):
         assert abs(float(got_loss) - float(want_loss)) <= 1e-5 * max(1.0, abs(float(want_loss)))
         scale = float(want_grad.abs().max())
         assert float((got_grad - want_grad).abs().max()) <= 1e-5 * scale
+
+
+def test_noalloc_accumulates_and_takes_no_loss_pointer(B):
+    """accumulate = 1 adds onto a non-zero gradient, and d_loss = NULL computes the gradient
+    alone; both equal the workspace version called the same way."""
+    x, y, L = _inputs(3, (4, 96, 80))
+    grad0 = torch.randn_like(x)
+    want_loss, want_grad = _workspace_version(B, x, y, L, 0.5, grad0=grad0)
+    got_loss, got_grad = _noalloc_version(B, x, y, L, 0.5, grad0=grad0)
+    torch.cuda.synchronize()
+    assert abs(float(got_loss) - float(want_loss)) <= 1e-5 * max(1.0, abs(float(want_loss)))
+    scale = float(want_grad.abs().max())
+    assert float((got_grad - want_grad).abs().max()) <= 1e-5 * scale
+    assert float((got_grad - grad0).abs().max()) > 0
+    _, want_grad = _workspace_version(B, x, y, L, 0.5, with_loss=False)
+    loss, got_grad = _noalloc_version(B, x, y, L, 0.5, with_loss=False)
+    torch.cuda.synchronize()
+    assert float(loss) == 0.0
+    assert float((got_grad - want_grad).abs().max()) <= 1e-5 * float(want_grad.abs().max())
 
 
 def test_noalloc_rejects_oversize(B):
