@@ -998,8 +998,13 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     u = torch.from_numpy(np.random.default_rng(11).random((n, 4)).astype(np.float32)).to(device)
     f = VolumeFit(grid, n, max_pairs=16 * n, device=device)
     opts = fit_opts(data_range=float(gt.abs().max()))
-    f.run(gt, warmup, opts, u)  # init + warm-up iterations
+    f.run(gt, warmup, opts, u)  # init + warm-up iterations (16-voxel bricks)
     torch.cuda.synchronize()
+    # the voxelizer's brick side chosen by the autotuner on the fit's current Gaussians
+    from paper_2604_01844_gb300.autotune import tune_brick
+
+    brick, brick_ms = tune_brick(grid, *f.params, device=device)
+    opts.brick = brick
     opts.init = 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -1041,14 +1046,31 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
             gbs = bpv * nvox / (per_kernel[k] * 1e-3) / 1e9
             hbm_roofs[k] = {"bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),
                             "peak_gbs": hbm, "frac": round(gbs / hbm, 3)}
-    return {"workload": f"gs_fit_volume, {n} Gaussians, {side}^3 ground truth, bricks 16^3",
+    # the voxel passes against their binding roofline: the larger of the HBM floor (the volume
+    # or dL/dV streamed once, 4 B per voxel) and the ALU floor (in-cut evaluations at the
+    # evaluation rate of the FP32 / ex2 unit counts, at the maximum SM clock)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    f_max = (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
+    vox_roofs = {}
+    for k in ("vox_fwd", "vox_bwd"):
+        if k in per_kernel and per_kernel[k] > 0 and hbm:
+            hbm_ms = 4.0 * nvox / (hbm * 1e9) * 1e3
+            alu_ms = evals / eval_peak(k, sms, f_max)[0] * 1e3
+            floor = max(hbm_ms, alu_ms)
+            vox_roofs[k] = {"ms": per_kernel[k], "hbm_floor_ms": round(hbm_ms, 4),
+                            "alu_floor_ms": round(alu_ms, 4),
+                            "bound": "hbm" if hbm_ms >= alu_ms else "alu",
+                            "frac": round(floor / per_kernel[k], 3),
+                            "evals_per_s": evals / (per_kernel[k] * 1e-3)}
+    return {"workload": f"gs_fit_volume, {n} Gaussians, {side}^3 ground truth",
+            "brick": brick, "brick_timings_ms": {k: round(v, 3) for k, v in brick_ms.items()},
             "ms_per_iter": round(ms, 3), "voxel_evals_per_iter": evals,
             "value": evals / (ms * 1e-3), "unit": "Gaussian-voxel evals/s",
             "status": int(st.code), "loss_last": float(loss[-1].item()),
             "kernels_ms_per_iter": per_kernel,
-            "hbm_rooflines": hbm_roofs,
+            "hbm_rooflines": hbm_roofs, "vox_rooflines": vox_roofs,
             "hbm_note": "achieved = algorithmic bytes per voxel x voxels / kernel ms; the voxel "
-                        "kernels are evaluation-bound (see their ALU rooflines in the step)"}
+                        "passes' frac is their binding floor (HBM or ALU) over their time"}
 
 
 def gemm_rate(device, M=118016, reps=20, warmup=3):

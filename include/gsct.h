@@ -78,7 +78,9 @@ typedef struct gs_grid {
  * eps: factored-in density (Sec. 3.5): the cut shrinks to min(cut^2, 2 ln(|A|/eps)) and a pair
  * whose amplitude |A| <= eps is culled; 0 disables it.  znear: cone-beam pairs whose depth
  * along the central ray is <= znear are culled.  tile: raster tile side (8, 16 or 32).
- * brick: voxel brick side (16). */
+ * brick: side of the voxelizer's bricks, the binning unit of its (brick, Gaussian) pairs: 16,
+ * 32 or 64 voxels (0 = 16); larger bricks make fewer pairs and longer per-brick lists.  The
+ * volume does not depend on it (bit for bit). */
 typedef struct gs_opts {
   float cut;
   float eps;
@@ -583,7 +585,7 @@ typedef struct gs_fit_opts {
   float data_range;                       /* SSIM data range L; <= 0: max |V_gt| (one sync) */
   float cut;                              /* truncation radius, 0 = 3 */
   int32_t init;                           /* 1: initialise from V_gt; 0: use the given params */
-  int32_t pad;
+  int32_t brick;                          /* voxelizer brick side: 16, 32 or 64 (0 = 16) */
 } gs_fit_opts;
 
 /* Workspace of gs_fit_volume for n Gaussians on `grid` with room for max_pairs (brick,

@@ -54,7 +54,7 @@ class GsFitOpts(ctypes.Structure):
                 ("eps", ctypes.c_float), ("min_log_scale", ctypes.c_float),
                 ("max_log_scale", ctypes.c_float), ("threshold_frac", ctypes.c_float),
                 ("density_k", ctypes.c_float), ("data_range", ctypes.c_float),
-                ("cut", ctypes.c_float), ("init", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("cut", ctypes.c_float), ("init", ctypes.c_int32), ("brick", ctypes.c_int32)]
 
 
 class GsInstance(ctypes.Structure):

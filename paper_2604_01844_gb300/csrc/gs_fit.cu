@@ -106,7 +106,7 @@ int gs_fit_volume(const float* d_vol_gt, const gs_grid* grid, int n, int iters,
     return GS_ERR_ARG;
   if (fo->init && !d_uniforms) return GS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  gs_opts o = {fo->cut > 0.f ? fo->cut : 3.f, 0.f, 0.1f, 16, 16, {0, 0, 0}};
+  gs_opts o = {fo->cut > 0.f ? fo->cut : 3.f, 0.f, 0.1f, 16, fo->brick, {0, 0, 0}};
   const int32_t lo[3] = {0, 0, 0};
   // the voxelizer's share is whatever the fixed buffers leave
   const size_t fixed = carve_fit(nullptr, n, grid, 0, 0).bytes;

@@ -5,16 +5,34 @@
 //   vox_prep    one thread per Gaussian: inverse covariance (pre-scaled to a base-2 exponent),
 //               the 3-sigma ellipsoid's axis-aligned index box clipped to the region of
 //               interest, and its brick count; warp-shuffle block sums
-//   scan/emit/sort/ranges   as for the rasterizer, key = brick
-//   vox_fwd     one CTA per 16^3 brick: 256 threads, each owning one z-column of 16 voxels in
-//               registers; Gaussian records staged through shared memory; a warp skips records
-//               whose box misses its 8x4 column patch; along a column the exponent is a
-//               quadratic in z evaluated with two FMAs per voxel
-//   vox_bwd     one CTA per brick with dL/dV of the brick in shared memory; one warp per
-//               (Gaussian, brick) pair, lanes over the (x, y) columns of its box, each lane
-//               walking the exact z chord of its column; the ten moment sums of g exp(-q/2)
-//               are warp-shuffle reduced, then three float4 atomics per pair
+//   scan/emit/sort/ranges   as for the rasterizer, key = brick (side 16, 32 or 64 voxels)
+//   vox_fwd     one CTA per 16^3 sub-brick of a brick (a brick's record list is shared by
+//               its sub-bricks): 256 threads, each owning one z-column of 16 voxels (8 packed
+//               FP32x2 accumulators); a warp owns an 8 x 4 column patch.  Per batch of staged
+//               records, eight threads per record decide for every warp patch whether the cut
+//               ellipsoid reaches it and which z pairs it can reach (closed form, below);
+//               warps then walk only those records, over a fixed window of pairs that holds
+//               the record's range, two voxels per packed instruction
+//   vox_bwd     the same visits, over each record's exact pair range, with dL/dV of the lane's
+//               column in registers; per visited record
+//               each lane sums its column's three z moments of g exp(-q/2), forms the ten
+//               moment sums, and a 12-shuffle reduce-scatter leaves each sum in one lane, which
+//               adds it to the record's shared accumulators; after the sub-brick, three
+//               float4 atomics per record
 //   vox_chain   one thread per Gaussian: moments -> d(mean, rho, scale, quaternion)
+//
+// Visit test of a record against a warp patch.  In the pre-scaled base-2 exponent
+// E(dx, dy, dz) = c00 dx^2 + c01 dx dy + c11 dy^2 + dz (c02 dx + c12 dy) + c22 dz^2 (E <= 0;
+// a voxel is in the cut when E > E_cut) the maximum over dz of a column (dx, dy) is
+// E2(dx, dy) = A dx^2 + B dx dy + C dy^2 (the Schur complement of c22), reached at
+// dz* = a dx + b dy, and the column's in-cut chord is |dz - dz*| <= sqrt((E_cut - E2) / c22).
+// Over the patch's rectangle of column centres the maximum of the concave E2 is closed form
+// (0 if the centre lies inside, else the best of the four clamped edge maxima), dz* is linear
+// (extremes at the corners), so the z range [min dz* - h, max dz* + h], h from the rectangle's
+// maximum of E2, holds every in-cut voxel of the patch.  The test uses a cut widened by 0.1 %
+// and the range 0.02 voxel wider, so FP32 rounding cannot drop an in-cut voxel; each voxel is
+// still decided by the exact per-voxel test, so volumes are bit-identical for every brick
+// side (a voxel's sum runs over its records in Gaussian order either way).
 #include <algorithm>
 #include <cmath>
 
@@ -26,7 +44,9 @@ namespace {
 using gsd::ex2;
 
 constexpr int kThreads = 256;
-constexpr int kB = 16;  // brick side
+constexpr int kS = 16;       // sub-brick side: the voxels one CTA pass covers per axis
+constexpr int kWarps = kThreads / 32;
+constexpr uint8_t kNoVisit = 0xFF;
 
 struct VGrid {
   int dims[3];
@@ -63,6 +83,8 @@ struct VInst {
 struct VBatch {
   int count;
   float cut2;
+  int brick;  // brick side (16, 32 or 64)
+  int sub;    // sub-bricks per axis (brick / 16)
   VInst in[kMaxInst];
 };
 
@@ -81,6 +103,7 @@ struct Plan {
   VBatch b;
   int n = 0;  // Gaussians over all instances
   int64_t n_keys = 0, cap = 0;
+  int64_t n_ctas = 0;  // CTAs of the walking kernels: one per (brick, 16^3 sub-brick)
   int nblocks = 0, key_bits = 0;
   SortPlan sort;
 };
@@ -89,10 +112,13 @@ int make_plan(const gs_voxel_instance* inst, int n_inst, const gs_opts* o, int64
               Plan& p) {
   if (!inst || n_inst < 1 || n_inst > kMaxInst || !o || cap < 0) return GS_ERR_ARG;
   if (!(o->cut > 0.f)) return GS_ERR_ARG;
-  if (o->brick != 0 && o->brick != kB) return GS_ERR_ARG;
+  const int brick = o->brick == 0 ? kS : o->brick;
+  if (brick != 16 && brick != 32 && brick != 64) return GS_ERR_ARG;
   memset(&p.b, 0, sizeof(p.b));
   p.b.count = n_inst;
   p.b.cut2 = o->cut * o->cut;
+  p.b.brick = brick;
+  p.b.sub = brick / kS;
   int64_t n = 0, keys = 0, vox = 0;
   for (int q = 0; q < n_inst; ++q) {
     const gs_voxel_instance& s = inst[q];
@@ -108,7 +134,7 @@ int make_plan(const gs_voxel_instance* inst, int n_inst, const gs_opts* o, int64
       d.g.h[k] = s.grid.voxel[k];
       d.g.lo[k] = s.roi_lo[k];
       d.g.dim[k] = s.roi_dim[k];
-      d.g.nb[k] = (s.roi_dim[k] + kB - 1) / kB;
+      d.g.nb[k] = (s.roi_dim[k] + brick - 1) / brick;
     }
     d.n = s.n;
     d.g_off = (int)n;
@@ -121,6 +147,8 @@ int make_plan(const gs_voxel_instance* inst, int n_inst, const gs_opts* o, int64
   if (n > ((int64_t)1 << 31) - kThreads || keys > ((int64_t)1 << 31) - 1) return GS_ERR_ARG;
   p.n = (int)n;
   p.n_keys = keys;
+  p.n_ctas = keys * (int64_t)p.b.sub * p.b.sub * p.b.sub;
+  if (p.n_ctas > ((int64_t)1 << 31) - 1) return GS_ERR_ARG;
   p.cap = std::min<int64_t>(cap, ((int64_t)1 << 31) - 1);
   p.nblocks = (p.n + kThreads - 1) / kThreads;
   p.key_bits = bits_for(p.n_keys);
@@ -218,9 +246,10 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (live) {
       cnt = 1;
+      const int B = bt.brick;
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        cnt *= (uint32_t)((hi[k] - g.lo[k]) / kB - (lo[k] - g.lo[k]) / kB + 1);
+        cnt *= (uint32_t)((hi[k] - g.lo[k]) / B - (lo[k] - g.lo[k]) / B + 1);
       const float c = gsd::kNegHalfLog2e;
       geo[i] = mr;
       cov0[i] = make_float4(c * o.Si[0][0], 2.f * c * o.Si[0][1], 2.f * c * o.Si[0][2],
@@ -284,17 +313,119 @@ __global__ void __launch_bounds__(kThreads)
   const VGrid& g = I.g;
   const uint32_t kbase = (uint32_t)I.key_off;
   const short4 a = lo_in[i], b = hi_in[i];
-  for (int bz = (a.z - g.lo[2]) / kB; bz <= (b.z - g.lo[2]) / kB; ++bz)
-    for (int by = (a.y - g.lo[1]) / kB; by <= (b.y - g.lo[1]) / kB; ++by)
-      for (int bx = (a.x - g.lo[0]) / kB; bx <= (b.x - g.lo[0]) / kB; ++bx) {
+  const int B = bt.brick;
+  for (int bz = (a.z - g.lo[2]) / B; bz <= (b.z - g.lo[2]) / B; ++bz)
+    for (int by = (a.y - g.lo[1]) / B; by <= (b.y - g.lo[1]) / B; ++by)
+      for (int bx = (a.x - g.lo[0]) / B; bx <= (b.x - g.lo[0]) / B; ++bx) {
         keys[off] = kbase + (uint32_t)((bz * g.nb[1] + by) * g.nb[0] + bx);
         vals[off] = (uint32_t)i;
         ++off;
       }
 }
 
+// Per-record quantities of the visit test (see the file comment), from the staged exponent
+// coefficients c0 = (c00, c01, c02, c11), c1 = (c12, c22, E_cut, 0).
+struct VisitCoef {
+  float A, B, C;        // E2 = A dx^2 + B dx dy + C dy^2
+  float ua, va;         // argmax of E2 along an edge: v = ua u on u = const, u = va v on v = const
+  float az, bz;         // dz* = az dx + bz dy
+  float ic22, ecm;      // 1 / c22, the widened cut
+};
+
+// The visit range only needs to hold every in-cut voxel, and the widened cut and range margins
+// dwarf the few-ulp errors of the fast reciprocals used here.
+__device__ __forceinline__ VisitCoef visit_coef(const float4 c0, const float4 c1) {
+  VisitCoef v;
+  const float ic = __fdividef(1.f, c1.y);
+  v.A = c0.x - 0.25f * c0.z * c0.z * ic;
+  v.B = c0.y - 0.5f * c0.z * c1.x * ic;
+  v.C = c0.w - 0.25f * c1.x * c1.x * ic;
+  v.ua = __fdividef(-0.5f * v.B, v.C);
+  v.va = __fdividef(-0.5f * v.B, v.A);
+  v.az = -0.5f * c0.z * ic;
+  v.bz = -0.5f * c1.x * ic;
+  v.ic22 = ic;
+  v.ecm = 1.001f * c1.z;
+  return v;
+}
+
+// Maximum of the concave E2 over [u0, u1] x [v0, v1] (0 if the rectangle holds the centre).
+__device__ __forceinline__ float rect_max_e2(const VisitCoef& v, float u0, float u1, float v0,
+                                             float v1) {
+  if (u0 <= 0.f && u1 >= 0.f && v0 <= 0.f && v1 >= 0.f) return 0.f;
+  if (!(v.A < 0.f && v.C < 0.f)) return 0.f;  // degenerate rounding: visit
+  const float va0 = fminf(fmaxf(v.ua * u0, v0), v1), va1 = fminf(fmaxf(v.ua * u1, v0), v1);
+  const float ub0 = fminf(fmaxf(v.va * v0, u0), u1), ub1 = fminf(fmaxf(v.va * v1, u0), u1);
+  const float e0 = fmaf(fmaf(v.A, u0, v.B * va0), u0, v.C * va0 * va0);
+  const float e1 = fmaf(fmaf(v.A, u1, v.B * va1), u1, v.C * va1 * va1);
+  const float e2 = fmaf(fmaf(v.C, v0, v.B * ub0), v0, v.A * ub0 * ub0);
+  const float e3 = fmaf(fmaf(v.C, v1, v.B * ub1), v1, v.A * ub1 * ub1);
+  return fmaxf(fmaxf(e0, e1), fmaxf(e2, e3));
+}
+
+// Visit code of a staged record for warp patch w of the sub-brick whose first voxel is
+// (sx, sy, sz): kNoVisit, or the first and last z pair the cut can reach, p0 | p1 << 4.  A patch
+// is visited when the record's index box meets its columns and the cut ellipsoid reaches one
+// of its columns.
+__device__ __forceinline__ uint8_t visit_code(const VGrid& g, const float4 G, const VisitCoef& vc,
+                                              const short4 a, const short4 b, int sx, int sy,
+                                              int sz, int w, float inv_hz) {
+  const int x0 = sx + (w & 1) * 8, y0 = sy + (w >> 1) * 4;
+  if (b.z < sz || a.z > sz + kS - 1 || b.x < x0 || a.x > x0 + 7 || b.y < y0 || a.y > y0 + 3)
+    return kNoVisit;
+  // column-centre offsets of the patch's rectangle, as the walking lanes compute them
+  const float u0 = g.o[0] + ((float)x0 + 0.5f) * g.h[0] - G.x;
+  const float u1 = g.o[0] + ((float)(x0 + 7) + 0.5f) * g.h[0] - G.x;
+  const float v0 = g.o[1] + ((float)y0 + 0.5f) * g.h[1] - G.y;
+  const float v1 = g.o[1] + ((float)(y0 + 3) + 0.5f) * g.h[1] - G.y;
+  const float e2 = rect_max_e2(vc, u0, u1, v0, v1);
+  if (!(e2 > vc.ecm)) return kNoVisit;
+  const float hz = g.h[2];
+  const float dz0 = (g.o[2] + ((float)sz + 0.5f) * hz) - G.z;
+  const float hh = (vc.ecm - e2) * vc.ic22;  // > 0 here
+  const float h = hh * rsqrtf(hh);
+  const float cmin = fminf(vc.az * u0, vc.az * u1) + fminf(vc.bz * v0, vc.bz * v1);
+  const float cmax = fmaxf(vc.az * u0, vc.az * u1) + fmaxf(vc.bz * v0, vc.bz * v1);
+  const int kmax = min(kS - 1, g.lo[2] + g.dim[2] - 1 - sz);
+  const int k0 = max(0, (int)ceilf((cmin - h - dz0) * inv_hz - 0.02f));
+  const int k1 = min(kmax, (int)floorf((cmax + h - dz0) * inv_hz + 0.02f));
+  return k0 <= k1 ? (uint8_t)((k0 >> 1) | ((k1 >> 1) << 4)) : kNoVisit;
+}
+
+// Codes of all (record, patch) items of m staged records, eight threads per record.
+__device__ __forceinline__ void visit_codes(const VGrid& g, const float4* s_geo,
+                                            const VisitCoef* s_vc, const short4* s_lo,
+                                            const short4* s_hi, int m, int sx, int sy, int sz,
+                                            uint8_t* s_zr) {
+  const float inv_hz = 1.f / g.h[2];
+  for (int t = threadIdx.x; t < m * kWarps; t += kThreads) {
+    const int j = t >> 3, w = t & 7;
+    s_zr[w * kThreads + j] = visit_code(g, s_geo[j], s_vc[j], s_lo[j], s_hi[j], sx, sy, sz, w,
+                                        inv_hz);
+  }
+}
+
+// z pairs a visit walks: a window of four pairs starting at pair 0, 2 or 4 when the record's
+// range fits in it, else all eight.  Pairs outside the range hold no in-cut voxel, so walking
+// them adds exactly nothing; a fixed window keeps the walk free of branches.
+__device__ __forceinline__ int walk_window(int p0, int p1) {
+  if (p1 <= 3) return 0;
+  if (p0 >= 2 && p1 <= 5) return 1;
+  if (p0 >= 4) return 2;
+  return 3;
+}
+
+// First voxel of sub-brick sb of key brick `brick` of instance grid g.
+__device__ __forceinline__ void sub_origin(const VGrid& g, int brick, int B, int sub, int sb,
+                                           int& sx, int& sy, int& sz) {
+  const int bx = brick % g.nb[0], by = (brick / g.nb[0]) % g.nb[1], bz = brick / (g.nb[0] * g.nb[1]);
+  sx = g.lo[0] + bx * B + (sb % sub) * kS;
+  sy = g.lo[1] + by * B + ((sb / sub) % sub) * kS;
+  sz = g.lo[2] + bz * B + (sb / (sub * sub)) * kS;
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     k_vox_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
               const float4* __restrict__ geo, const float4* __restrict__ cov0,
               const float4* __restrict__ cov1, const short4* __restrict__ lo_in,
@@ -305,188 +436,284 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ float4 s_c1[kThreads];
   __shared__ short4 s_lo[kThreads];
   __shared__ short4 s_hi[kThreads];
+  __shared__ VisitCoef s_vc[kThreads];
+  __shared__ uint8_t s_zr[kWarps * kThreads];
   __shared__ unsigned long long s_cnt;
   if (st->code != GS_OK) return;
-  const VInst& I = bt.in[inst_of_key(bt, blockIdx.x)];
+  // one CTA per (brick, sub-brick)
+  const int nsub = bt.sub * bt.sub * bt.sub;
+  const int key = (int)(blockIdx.x / nsub), sb = (int)(blockIdx.x % nsub);
+  const VInst& I = bt.in[inst_of_key(bt, key)];
   const VGrid& g = I.g;
-  const int brick = (int)(blockIdx.x - I.key_off);
-  const int bx = brick % g.nb[0], by = (brick / g.nb[0]) % g.nb[1], bz = brick / (g.nb[0] * g.nb[1]);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int wx0 = g.lo[0] + bx * kB + (w & 1) * 8;
-  const int wy0 = g.lo[1] + by * kB + (w >> 1) * 4;
-  const int z0 = g.lo[2] + bz * kB;
-  const int x = wx0 + (lane & 7), y = wy0 + (lane >> 3);
+  int sx, sy, sz;
+  sub_origin(g, (int)(key - I.key_off), bt.brick, bt.sub, sb, sx, sy, sz);
+  const int xend = g.lo[0] + g.dim[0], yend = g.lo[1] + g.dim[1], zend = g.lo[2] + g.dim[2];
+  if (sx >= xend || sy >= yend || sz >= zend) return;  // sub-brick outside the region
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint2 r = ranges[key];
+  const float hz = g.h[2];
+  if (COUNT && tid == 0) s_cnt = 0ull;
+  uint32_t cnt = 0;
+  const int x = sx + (w & 1) * 8 + (lane & 7), y = sy + (w >> 1) * 4 + (lane >> 3);
   const float xc = g.o[0] + ((float)x + 0.5f) * g.h[0];
   const float yc = g.o[1] + ((float)y + 0.5f) * g.h[1];
-  const float zc0 = g.o[2] + ((float)z0 + 0.5f) * g.h[2];
-  const float hz = g.h[2];
-  float acc[kB];
+  const float zc0 = g.o[2] + ((float)sz + 0.5f) * hz;
+  float2 acc[kS / 2];
 #pragma unroll
-  for (int k = 0; k < kB; ++k) acc[k] = 0.f;
-  uint32_t cnt = 0;
-  if (COUNT && threadIdx.x == 0) s_cnt = 0ull;
-  const uint2 r = ranges[blockIdx.x];
+  for (int p = 0; p < kS / 2; ++p) acc[p] = make_float2(0.f, 0.f);
   for (uint32_t base = r.x; base < r.y; base += kThreads) {
     const int m = (int)min((uint32_t)kThreads, r.y - base);
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-      const uint32_t i = vals[base + threadIdx.x];
-      s_geo[threadIdx.x] = geo[i];
-      s_c0[threadIdx.x] = cov0[i];
-      s_c1[threadIdx.x] = cov1[i];
-      s_lo[threadIdx.x] = lo_in[i];
-      s_hi[threadIdx.x] = hi_in[i];
+    __syncthreads();  // the warps are done with the previous batch
+    if (tid < m) {
+      const uint32_t i = vals[base + tid];
+      const float4 c0 = cov0[i], c1 = cov1[i];
+      s_geo[tid] = geo[i];
+      s_c0[tid] = c0;
+      s_c1[tid] = c1;
+      s_lo[tid] = lo_in[i];
+      s_hi[tid] = hi_in[i];
+      s_vc[tid] = visit_coef(c0, c1);
     }
     __syncthreads();
-    for (int j = 0; j < m; ++j) {
-      const short4 a = s_lo[j], b = s_hi[j];
-      // warp-uniform: skip records whose box misses this warp's 8x4 column patch
-      if (b.x < wx0 || a.x > wx0 + 7 || b.y < wy0 || a.y > wy0 + 3) continue;
-      const float4 G = s_geo[j], c0 = s_c0[j], c1 = s_c1[j];
-      const float dx = xc - G.x, dy = yc - G.y;
-      // exponent(z) = qxy + dz (lin + e22 dz) in base 2, already scaled by -1/2 log2(e)
-      const float qxy = fmaf(fmaf(c0.y, dy, c0.x * dx), dx, c0.w * dy * dy);
-      const float lin = fmaf(c0.z, dx, c1.x * dy);
-      const float dz0 = zc0 - G.z;
+    visit_codes(g, s_geo, s_vc, s_lo, s_hi, m, sx, sy, sz, s_zr);
+    __syncthreads();
+    const uint8_t* zrw = s_zr + w * kThreads;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      const uint8_t mine = j0 + lane < m ? zrw[j0 + lane] : kNoVisit;
+      unsigned todo = __ballot_sync(0xffffffffu, mine != kNoVisit);
+      while (todo) {
+        const int t = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int j = j0 + t;
+        const int code = __shfl_sync(0xffffffffu, (int)mine, t);
+        const float4 G = s_geo[j], c0 = s_c0[j], c1 = s_c1[j];
+        const float dx = xc - G.x, dy = yc - G.y;
+        // exponent(z) = qxy + dz (lin + c22 dz) in base 2, already scaled by -1/2 log2(e)
+        const float qxy = fmaf(fmaf(c0.y, dy, c0.x * dx), dx, c0.w * dy * dy);
+        const float lin = fmaf(c0.z, dx, c1.x * dy);
+        const float dz0 = zc0 - G.z;
+        const float2 q2 = make_float2(qxy, qxy), l2 = make_float2(lin, lin);
+        const float2 c22 = make_float2(c1.y, c1.y), r2 = make_float2(G.w, G.w);
+        // closed-form exponent per voxel pair: the pairs are independent, so the unrolled walk
+        // interleaves them
+        auto pair = [&](int p) {
+          const float2 dz = make_float2(fmaf((float)(2 * p), hz, dz0),
+                                        fmaf((float)(2 * p + 1), hz, dz0));
+          const float2 e = __ffma2_rn(__ffma2_rn(c22, dz, l2), dz, q2);
+          if (COUNT) {
+            cnt += (e.x > c1.z && sz + 2 * p < zend) ? 1u : 0u;
+            cnt += (e.y > c1.z && sz + 2 * p + 1 < zend) ? 1u : 0u;
+          } else {
+            const float2 val = make_float2(e.x > c1.z ? ex2(e.x) : 0.f,
+                                           e.y > c1.z ? ex2(e.y) : 0.f);
+            acc[p] = __ffma2_rn(r2, val, acc[p]);
+          }
+        };
+        switch (walk_window(code & 15, code >> 4)) {  // warp-uniform
+          case 0:
 #pragma unroll
-      for (int k = 0; k < kB; ++k) {
-        const float dz = fmaf((float)k, hz, dz0);
-        const float e = fmaf(fmaf(c1.y, dz, lin), dz, qxy);
-        if (COUNT) {
-          cnt += (e > c1.z && z0 + k < g.lo[2] + g.dim[2]) ? 1u : 0u;
-        } else {
-          const float val = ex2(e);
-          acc[k] = e > c1.z ? fmaf(G.w, val, acc[k]) : acc[k];
+            for (int p = 0; p < 4; ++p) pair(p);
+            break;
+          case 1:
+#pragma unroll
+            for (int p = 2; p < 6; ++p) pair(p);
+            break;
+          case 2:
+#pragma unroll
+            for (int p = 4; p < 8; ++p) pair(p);
+            break;
+          default:
+#pragma unroll
+            for (int p = 0; p < 8; ++p) pair(p);
         }
       }
     }
   }
-  const bool in_xy = x < g.lo[0] + g.dim[0] && y < g.lo[1] + g.dim[1];
+  const bool in_xy = x < xend && y < yend;
   if (COUNT) {
     __syncthreads();
     const uint32_t ws = gsd::warp_sum(in_xy ? cnt : 0u);
     if (lane == 0 && ws) atomicAdd(&s_cnt, (unsigned long long)ws);
     __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) atomicAdd((unsigned long long*)&st->evals, s_cnt);
+    if (tid == 0 && s_cnt) atomicAdd((unsigned long long*)&st->evals, s_cnt);
     return;
   }
   if (!in_xy) return;
-  const size_t sx = (size_t)g.dim[0], sxy = (size_t)g.dim[0] * g.dim[1];
-  const size_t col = (size_t)(y - g.lo[1]) * sx + (x - g.lo[0]);
-  float* vo = vol + I.vol_off;
+  const size_t sxy = (size_t)g.dim[0] * g.dim[1];
+  float* vo = vol + I.vol_off + (size_t)(y - g.lo[1]) * g.dim[0] + (x - g.lo[0]);
 #pragma unroll
-  for (int k = 0; k < kB; ++k) {
-    const int z = z0 + k;
-    if (z < g.lo[2] + g.dim[2]) vo[(size_t)(z - g.lo[2]) * sxy + col] = acc[k];
+  for (int p = 0; p < kS / 2; ++p) {
+    const int z = sz + 2 * p;
+    if (z < zend) vo[(size_t)(z - g.lo[2]) * sxy] = acc[p].x;
+    if (z + 1 < zend) vo[(size_t)(z + 1 - g.lo[2]) * sxy] = acc[p].y;
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Reduce-scatter of ten per-lane values over the warp in 12 shuffles: on return lane l holds
+// in v[0] the warp sum of value index vox_rs_index(l) when vox_rs_holder(l).
+__device__ __forceinline__ void reduce_scatter10(float v[10], int lane) {
+  {
+    const bool b = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float lo = v[i], hi = v[i + 5];
+      v[i] = (b ? hi : lo) + __shfl_xor_sync(0xffffffffu, b ? lo : hi, 16);
+    }
+  }
+  {
+    const bool b = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float lo = v[i], hi = i + 3 < 5 ? v[i + 3] : 0.f;
+      v[i] = (b ? hi : lo) + __shfl_xor_sync(0xffffffffu, b ? lo : hi, 8);
+    }
+  }
+  {
+    const bool b = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float lo = v[i], hi = i + 2 < 3 ? v[i + 2] : 0.f;
+      v[i] = (b ? hi : lo) + __shfl_xor_sync(0xffffffffu, b ? lo : hi, 4);
+    }
+  }
+  {
+    const bool b = lane & 2;
+    const float lo = v[0], hi = v[1];
+    v[0] = (b ? hi : lo) + __shfl_xor_sync(0xffffffffu, b ? lo : hi, 2);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ bool vox_rs_holder(int lane) {
+  const bool b1 = lane & 2, b2 = lane & 4, b3 = lane & 8;
+  return !(lane & 1) && !(b2 && b1) && !(b3 && b2);
+}
+__device__ __forceinline__ int vox_rs_index(int lane) {
+  return ((lane & 16) ? 5 : 0) + ((lane & 8) ? 3 : 0) + ((lane & 4) ? 2 : ((lane >> 1) & 1));
+}
+
+constexpr int kMoments = 10;
+
+__global__ void __launch_bounds__(kThreads, 4)
     k_vox_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
               const float4* __restrict__ geo, const float4* __restrict__ cov0,
               const float4* __restrict__ cov1, const short4* __restrict__ lo_in,
               const short4* __restrict__ hi_in, const __grid_constant__ VBatch bt,
               const float* __restrict__ dvol_all, float4* __restrict__ vgrad,
               const gs_status* st) {
-  __shared__ float s_g[kB * kB * kB];
   __shared__ float4 s_geo[kThreads];
   __shared__ float4 s_c0[kThreads];
   __shared__ float4 s_c1[kThreads];
   __shared__ short4 s_lo[kThreads];
   __shared__ short4 s_hi[kThreads];
-  __shared__ uint32_t s_idx[kThreads];
+  __shared__ VisitCoef s_vc[kThreads];
+  __shared__ uint8_t s_zr[kWarps * kThreads];
+  __shared__ float s_mom[kThreads * kMoments];
   if (st->code != GS_OK) return;
-  const uint2 r = ranges[blockIdx.x];
+  // one CTA per (brick, sub-brick)
+  const int nsub = bt.sub * bt.sub * bt.sub;
+  const int key = (int)(blockIdx.x / nsub), sb = (int)(blockIdx.x % nsub);
+  const uint2 r = ranges[key];
   if (r.x == r.y) return;
-  const VInst& I = bt.in[inst_of_key(bt, blockIdx.x)];
+  const VInst& I = bt.in[inst_of_key(bt, key)];
   const VGrid& g = I.g;
+  int sx, sy, sz;
+  sub_origin(g, (int)(key - I.key_off), bt.brick, bt.sub, sb, sx, sy, sz);
+  const int xend = g.lo[0] + g.dim[0], yend = g.lo[1] + g.dim[1], zend = g.lo[2] + g.dim[2];
+  if (sx >= xend || sy >= yend || sz >= zend) return;  // sub-brick outside the region
   const float* dvol = dvol_all + I.vol_off;
-  const int brick = (int)(blockIdx.x - I.key_off);
-  const int bx = brick % g.nb[0], by = (brick / g.nb[0]) % g.nb[1], bz = brick / (g.nb[0] * g.nb[1]);
-  const int x0b = g.lo[0] + bx * kB, y0b = g.lo[1] + by * kB, z0b = g.lo[2] + bz * kB;
-  const size_t sx = (size_t)g.dim[0], sxy = (size_t)g.dim[0] * g.dim[1];
-  for (int p = threadIdx.x; p < kB * kB * kB; p += kThreads) {
-    const int x = x0b + p % kB, y = y0b + (p / kB) % kB, z = z0b + p / (kB * kB);
-    const bool in = x < g.lo[0] + g.dim[0] && y < g.lo[1] + g.dim[1] && z < g.lo[2] + g.dim[2];
-    s_g[p] = in ? dvol[(size_t)(z - g.lo[2]) * sxy + (size_t)(y - g.lo[1]) * sx + (x - g.lo[0])]
-                : 0.f;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float hz = g.h[2];
+  const bool holder = vox_rs_holder(lane);
+  const int mom_index = vox_rs_index(lane);
+  const int x = sx + (w & 1) * 8 + (lane & 7), y = sy + (w >> 1) * 4 + (lane >> 3);
+  const bool in_xy = x < xend && y < yend;
+  // dL/dV of this lane's column (0 outside the region)
+  float2 gv[kS / 2];
+  {
+    const size_t sxy = (size_t)g.dim[0] * g.dim[1];
+    const float* gc = dvol + (in_xy ? (size_t)(y - g.lo[1]) * g.dim[0] + (x - g.lo[0]) : 0);
+#pragma unroll
+    for (int p = 0; p < kS / 2; ++p) {
+      const int z = sz + 2 * p;
+      gv[p].x = in_xy && z < zend ? __ldg(gc + (size_t)(z - g.lo[2]) * sxy) : 0.f;
+      gv[p].y = in_xy && z + 1 < zend ? __ldg(gc + (size_t)(z + 1 - g.lo[2]) * sxy) : 0.f;
+    }
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float xc = g.o[0] + ((float)x + 0.5f) * g.h[0];
+  const float yc = g.o[1] + ((float)y + 0.5f) * g.h[1];
+  const float zc0 = g.o[2] + ((float)sz + 0.5f) * hz;
   for (uint32_t base = r.x; base < r.y; base += kThreads) {
     const int m = (int)min((uint32_t)kThreads, r.y - base);
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-      const uint32_t i = vals[base + threadIdx.x];
-      s_geo[threadIdx.x] = geo[i];
-      s_c0[threadIdx.x] = cov0[i];
-      s_c1[threadIdx.x] = cov1[i];
-      s_lo[threadIdx.x] = lo_in[i];
-      s_hi[threadIdx.x] = hi_in[i];
-      s_idx[threadIdx.x] = i;
+    __syncthreads();  // the previous batch's accumulators are flushed
+    uint32_t myI = 0;
+    if (tid < m) {
+      myI = vals[base + tid];
+      const float4 c0 = cov0[myI], c1 = cov1[myI];
+      s_geo[tid] = geo[myI];
+      s_c0[tid] = c0;
+      s_c1[tid] = c1;
+      s_lo[tid] = lo_in[myI];
+      s_hi[tid] = hi_in[myI];
+      s_vc[tid] = visit_coef(c0, c1);
+#pragma unroll
+      for (int k = 0; k < kMoments; ++k) s_mom[tid * kMoments + k] = 0.f;
     }
     __syncthreads();
-    for (int j = w; j < m; j += kThreads / 32) {
-      const short4 a = s_lo[j], b = s_hi[j];
-      const int xa = max((int)a.x, x0b), xb = min((int)b.x, x0b + kB - 1);
-      const int ya = max((int)a.y, y0b), yb = min((int)b.y, y0b + kB - 1);
-      const int za = max((int)a.z, z0b), zb = min((int)b.z, z0b + kB - 1);
-      if (xa > xb || ya > yb || za > zb) continue;
-      const float4 G = s_geo[j], c0 = s_c0[j], c1 = s_c1[j];
-      // lanes take the (x, y) columns of the box inside the brick; each walks the exact z
-      // chord of its column (closed-form roots of the exponent, widened by 1/100 voxel) and
-      // re-tests every voxel with the forward's expression and offsets
-      const int ncx = xb - xa + 1, ncols = ncx * (yb - ya + 1);
-      const float inv_ncx = 1.f / (float)ncx;
-      const float hz = g.h[2];
-      const float dz0 = (g.o[2] + ((float)z0b + 0.5f) * hz) - G.z;  // the forward's dz at z0b
-      const float inv2a = 0.5f / c1.y, inv_hz = 1.f / hz;
-      float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-      float mxx = 0.f, mxy = 0.f, mxz = 0.f, myy = 0.f, myz = 0.f, mzz = 0.f;
-      for (int ci = lane; ci < ncols; ci += 32) {
-        const int yo = (int)(((float)ci + 0.5f) * inv_ncx);
-        const int x = xa + (ci - yo * ncx), y = ya + yo;
-        const float dx = g.o[0] + ((float)x + 0.5f) * g.h[0] - G.x;
-        const float dy = g.o[1] + ((float)y + 0.5f) * g.h[1] - G.y;
+    visit_codes(g, s_geo, s_vc, s_lo, s_hi, m, sx, sy, sz, s_zr);
+    __syncthreads();
+    const uint8_t* zrw = s_zr + w * kThreads;
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      const uint8_t mine = j0 + lane < m ? zrw[j0 + lane] : kNoVisit;
+      unsigned todo = __ballot_sync(0xffffffffu, mine != kNoVisit);
+      while (todo) {
+        const int t = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int j = j0 + t;
+        const int code = __shfl_sync(0xffffffffu, (int)mine, t);
+        const float4 G = s_geo[j], c0 = s_c0[j], c1 = s_c1[j];
+        const float dx = xc - G.x, dy = yc - G.y;
         const float qxy = fmaf(fmaf(c0.y, dy, c0.x * dx), dx, c0.w * dy * dy);
         const float lin = fmaf(c0.z, dx, c1.x * dy);
-        const float disc = lin * lin - 4.f * c1.y * (qxy - c1.z);
-        if (!(disc > 0.f)) continue;
-        const float ctr = -lin * inv2a, half = -sqrtf(disc) * inv2a;
-        const int k0 = max(za - z0b, (int)ceilf((ctr - half - dz0) * inv_hz - 0.01f));
-        const int k1 = min(zb - z0b, (int)floorf((ctr + half - dz0) * inv_hz + 0.01f));
-        const float* gcol = s_g + (y - y0b) * kB + (x - x0b);
-        float q0 = 0.f, qz = 0.f, qzz = 0.f;
-        for (int k = k0; k <= k1; ++k) {
-          const float dz = fmaf((float)k, hz, dz0);
-          const float e = fmaf(fmaf(c1.y, dz, lin), dz, qxy);
-          if (e > c1.z) {
-            const float q = gcol[k * kB * kB] * ex2(e);
-            const float qd = q * dz;
-            q0 += q;
-            qz += qd;
-            qzz = fmaf(qd, dz, qzz);
-          }
+        const float dz0 = zc0 - G.z;
+        const float2 q2 = make_float2(qxy, qxy), l2 = make_float2(lin, lin);
+        const float2 c22 = make_float2(c1.y, c1.y);
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
+        // the forward's closed-form exponent over the record's exact pair range: the
+        // backward's per-pair work is long enough that skipping the pairs outside the range
+        // pays for the uniform branches
+        const int p0 = code & 15, p1 = code >> 4;  // warp-uniform
+#pragma unroll
+        for (int p = 0; p < kS / 2; ++p) {
+          if (p < p0 || p > p1) continue;
+          const float2 dz = make_float2(fmaf((float)(2 * p), hz, dz0),
+                                        fmaf((float)(2 * p + 1), hz, dz0));
+          const float2 e = __ffma2_rn(__ffma2_rn(c22, dz, l2), dz, q2);
+          const float2 val = make_float2(e.x > c1.z ? ex2(e.x) : 0.f,
+                                         e.y > c1.z ? ex2(e.y) : 0.f);
+          const float2 q = __fmul2_rn(gv[p], val);
+          const float2 qd = __fmul2_rn(q, dz);
+          s0 = __fadd2_rn(s0, q);
+          s1 = __fadd2_rn(s1, qd);
+          s2 = __ffma2_rn(qd, dz, s2);
         }
-        m0 += q0;
-        mx = fmaf(dx, q0, mx);
-        my = fmaf(dy, q0, my);
-        mz += qz;
-        mxx = fmaf(dx * dx, q0, mxx);
-        mxy = fmaf(dx * dy, q0, mxy);
-        mxz = fmaf(dx, qz, mxz);
-        myy = fmaf(dy * dy, q0, myy);
-        myz = fmaf(dy, qz, myz);
-        mzz += qzz;
+        const float q0 = s0.x + s0.y, q1 = s1.x + s1.y, qzz = s2.x + s2.y;
+        const float qx = dx * q0;
+        float v[kMoments] = {q0, qx, dy * q0, q1, dx * qx, dy * qx, dx * q1,
+                             dy * dy * q0, dy * q1, qzz};
+        reduce_scatter10(v, lane);
+        if (holder) atomicAdd(&s_mom[j * kMoments + mom_index], v[0]);
       }
-      m0 = gsd::warp_sum(m0); mx = gsd::warp_sum(mx); my = gsd::warp_sum(my);
-      mz = gsd::warp_sum(mz); mxx = gsd::warp_sum(mxx); mxy = gsd::warp_sum(mxy);
-      mxz = gsd::warp_sum(mxz); myy = gsd::warp_sum(myy); myz = gsd::warp_sum(myz);
-      mzz = gsd::warp_sum(mzz);
-      if (lane == 0) {
-        const size_t i = s_idx[j];
-        atomicAdd(&vgrad[3 * i], make_float4(m0, mx, my, mz));
-        atomicAdd(&vgrad[3 * i + 1], make_float4(mxx, mxy, mxz, myy));
-        atomicAdd(&vgrad[3 * i + 2], make_float4(myz, mzz, 0.f, 0.f));
+    }
+    __syncthreads();
+    if (tid < m) {
+      const float* mm = s_mom + tid * kMoments;
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < kMoments; ++k) any |= mm[k] != 0.f;
+      if (any) {
+        atomicAdd(&vgrad[3 * (size_t)myI], make_float4(mm[0], mm[1], mm[2], mm[3]));
+        atomicAdd(&vgrad[3 * (size_t)myI + 1], make_float4(mm[4], mm[5], mm[6], mm[7]));
+        atomicAdd(&vgrad[3 * (size_t)myI + 2], make_float4(mm[8], mm[9], 0.f, 0.f));
       }
     }
   }
@@ -623,7 +850,7 @@ int bin_bricks(const Plan& p, const Layout& L, const float* mr, const float* sc,
 
 int vox_fwd(const Plan& p, const Layout& L, const uint32_t* vals, float* vol, bool count,
             cudaStream_t s) {
-  dim3 grid((unsigned)p.n_keys), block(kThreads);
+  dim3 grid((unsigned)p.n_ctas), block(kThreads);
   if (count)
     return launch("vox_count", k_vox_fwd<true>, grid, block, 0, s, (const uint2*)L.ranges, vals,
                   (const float4*)L.geo, (const float4*)L.cov0, (const float4*)L.cov1,
@@ -727,7 +954,7 @@ int gs_voxelize_batch_backward(const float* d_mean_rho, const float* d_scale,
     GS_TRY(bin_bricks(p, L, d_mean_rho, d_scale, d_quat, s, d_ws, &k, &v));
   }
   GS_CUDA(cudaMemsetAsync(L.vgrad, 0, (size_t)p.n * 3 * sizeof(float4), s));
-  GS_TRY(launch("vox_bwd", k_vox_bwd, dim3((unsigned)p.n_keys), dim3(kThreads), 0, s,
+  GS_TRY(launch("vox_bwd", k_vox_bwd, dim3((unsigned)p.n_ctas), dim3(kThreads), 0, s,
                 (const uint2*)L.ranges, (const uint32_t*)v, (const float4*)L.geo,
                 (const float4*)L.cov0, (const float4*)L.cov1, (const short4*)L.lo,
                 (const short4*)L.hi, p.b, d_dvol, L.vgrad, (const gs_status*)L.st));

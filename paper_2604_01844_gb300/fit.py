@@ -12,13 +12,14 @@ from . import binding as B
 
 def fit_opts(alpha_ssim=0.2, lr_mean=5e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=5e-3,
              threshold_frac=0.05, density_k=0.15, data_range=0.0, init=True,
-             min_scale=1e-4, max_scale=0.5) -> B.GsFitOpts:
+             min_scale=1e-4, max_scale=0.5, brick=16) -> B.GsFitOpts:
     o = B.GsFitOpts()
     o.alpha_ssim, o.lr_mean, o.lr_rho, o.lr_scale, o.lr_quat = alpha_ssim, lr_mean, lr_rho, lr_scale, lr_quat
     o.beta1, o.beta2, o.eps = 0.9, 0.999, 1e-15
     o.min_log_scale, o.max_log_scale = math.log(min_scale), math.log(max_scale)
     o.threshold_frac, o.density_k, o.data_range, o.cut = threshold_frac, density_k, data_range, 3.0
     o.init = 1 if init else 0
+    o.brick = int(brick)
     return o
 
 
