@@ -54,6 +54,9 @@ def lib():
                 "orc_project": (ll, [i, P, i, P, i, i, d, d, d, P, i]),
                 "orc_project_pixels": (None, [i, P, i, P, i, i, d, d, d, i, P, P, i]),
                 "orc_project_ambiguity": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i]),
+                "orc_project_pixels_allow": (None, [i, P, i, P, i, i, d, d, d, d, d, i, P, P,
+                                                    P, i]),
+                "orc_voxelize_points_allow": (None, [i, P, P, d, d, d, i, P, P, P, i]),
                 "orc_project_exact": (None, [i, P, i, P, i, i, P, i]),
                 "orc_pair_flags": (None, [i, P, i, P, i, i, d, d, d, d, d, P, i, i]),
                 "orc_min_q_rect": (d, [d, d, d, d, d, d, d, d, d]),
@@ -146,6 +149,30 @@ def project_pixels(P, V, W, H, pix, opts=Opts(), nthreads=0):
     lib().orc_project_pixels(P.shape[0], _p(P), V.shape[0], _p(V), W, H, opts.cut, opts.eps,
                              opts.znear, pix.shape[0], _p(pix), _p(out), nthreads)
     return out
+
+
+def project_pixels_allow(P, V, W, H, pix, rel_band, px_band, opts=Opts(), nthreads=0):
+    """Values and guard-band allowances at the pixels pix (view, row, col): what project() and
+    project_ambiguity() give there, without whole images."""
+    pix = np.ascontiguousarray(pix, dtype=np.int32)
+    out = np.zeros(pix.shape[0])
+    allow = np.zeros(pix.shape[0])
+    lib().orc_project_pixels_allow(P.shape[0], _p(P), V.shape[0], _p(V), W, H, opts.cut,
+                                   opts.eps, opts.znear, rel_band, px_band, pix.shape[0], _p(pix),
+                                   _p(out), _p(allow), nthreads)
+    return out, allow
+
+
+def voxelize_points_allow(P, grid, idx, rel_band, idx_band, cut=3.0, nthreads=0):
+    """Values and guard-band allowances at the voxels idx (z, y, x) of the whole grid: what
+    voxelize() and voxelize_ambiguity() give there, without the whole volume."""
+    G = grid64(grid)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.zeros(idx.shape[0])
+    allow = np.zeros(idx.shape[0])
+    lib().orc_voxelize_points_allow(P.shape[0], _p(P), _p(G), cut, rel_band, idx_band,
+                                    idx.shape[0], _p(idx), _p(out), _p(allow), nthreads)
+    return out, allow
 
 
 def project_ambiguity(P, V, W, H, rel_band, px_band, opts=Opts(), nthreads=0):

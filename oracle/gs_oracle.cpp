@@ -426,6 +426,57 @@ void orc_project_pixels(int n, const double* g, int nv, const double* views, int
   }
 }
 
+// Method (B) value and guard-band allowance (the rule of orc_project_ambiguity) at a list of
+// pixels (view, row, col), for full-size checks where a whole image set would not fit: the
+// footprints of every Gaussian in a sampled view are computed once, then each sampled pixel
+// sums over the Gaussians whose clipped box holds it.  out, allow: np values each.
+void orc_project_pixels_allow(int n, const double* g, int nv, const double* views, int W, int H,
+                              double cut, double eps, double znear, double rel_band,
+                              double px_band, int np, const int* pix, double* out, double* allow,
+                              int nthreads) {
+  Opts o{cut, eps, znear};
+  set_threads(nthreads);
+  std::vector<Footprint<double>> fp(n);
+  std::vector<double> rh(n);
+  for (int k = 0; k < nv; ++k) {
+    std::vector<int> mine;
+    for (int t = 0; t < np; ++t)
+      if (pix[3 * t] == k) mine.push_back(t);
+    if (mine.empty()) continue;
+    View vw = make_view(views + 13 * k);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      double p[3], s[3], q[4], rho;
+      unpack(g + 11 * i, p, s, q, rho);
+      fp[i] = footprint(p, s, q, rho, vw, W, H, o);
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int u = 0; u < (int)mine.size(); ++u) {
+      const int t = mine[u];
+      const int y = pix[3 * t + 1], x = pix[3 * t + 2];
+      double acc = 0.0, al = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const Footprint<double>& f = fp[i];
+        if (f.culled) continue;
+        // value: inside the clipped box and the cut (orc_project_pixels)
+        const bool in_box = x >= f.ix0 && x <= f.ix1 && y >= f.iy0 && y <= f.iy1;
+        // allowance: the box grown by one pixel (orc_project_ambiguity)
+        if (x < f.ix0 - 1 || x > f.ix1 + 1 || y < f.iy0 - 1 || y > f.iy1 + 1) continue;
+        double dx = x - f.px, dy = y - f.py;
+        double qq = quad2(f, dx, dy);
+        if (in_box && qq < f.Q) acc += f.A * std::exp(-0.5 * qq);
+        bool near_cut = std::fabs(qq - f.Q) <= rel_band * f.Q;
+        bool near_box = std::fabs(x - f.lo_x) <= px_band || std::fabs(x - f.hi_x) <= px_band ||
+                        std::fabs(y - f.lo_y) <= px_band || std::fabs(y - f.hi_y) <= px_band;
+        if (near_cut || (near_box && qq < f.Q * (1.0 + rel_band)))
+          al += std::fabs(f.A) * std::exp(-0.5 * std::min(qq, f.Q));
+      }
+      out[t] = acc;
+      allow[t] = al;
+    }
+  }
+}
+
 // Per-pixel allowance for the guard band: sum of |A| exp(-q/2) over pairs whose q lies within
 // rel_band * Q of the cut (either side) or whose box edge lies within px_band of the pixel.
 void orc_project_ambiguity(int n, const double* g, int nv, const double* views, int W, int H,
@@ -816,6 +867,58 @@ void orc_voxelize_ambiguity(int n, const double* g, const double* grid, const in
             allow[id] += std::fabs(rho) * std::exp(-0.5 * std::min(qq, f.Q));
           }
         }
+  }
+}
+
+// Voxelizer value and guard-band allowance (the rule of orc_voxelize_ambiguity) at a list of
+// voxels (z, y, x) of the whole grid: each Gaussian's footprint is computed once, then each
+// sampled voxel sums over the Gaussians whose index box (grown by one for the allowance)
+// holds it.  out, allow: np values each.
+void orc_voxelize_points_allow(int n, const double* g, const double* grid, double cut,
+                               double rel_band, double idx_band, int np, const int* idx,
+                               double* out, double* allow, int nthreads) {
+  Grid gr = make_grid(grid);
+  set_threads(nthreads);
+  int lo[3] = {0, 0, 0};
+  int dim[3] = {gr.n[0], gr.n[1], gr.n[2]};
+  std::vector<VoxFoot<double>> fp(n);
+  std::vector<double> P3(3 * (size_t)n), R(n);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    double p[3], s[3], q[4], rho;
+    unpack(g + 11 * i, p, s, q, rho);
+    fp[i] = vox_footprint(p, s, q, gr, lo, dim, cut);
+    for (int k = 0; k < 3; ++k) P3[3 * (size_t)i + k] = p[k];
+    R[i] = rho;
+  }
+#pragma omp parallel for schedule(dynamic)
+  for (int t = 0; t < np; ++t) {
+    const int c[3] = {idx[3 * t + 2], idx[3 * t + 1], idx[3 * t]};  // x, y, z
+    double acc = 0.0, al = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const VoxFoot<double>& f = fp[i];
+      if (f.culled) continue;
+      bool in_box = true, near = true;
+      for (int k = 0; k < 3; ++k) {
+        in_box = in_box && c[k] >= f.lo[k] && c[k] <= f.hi[k];
+        near = near && c[k] >= f.lo[k] - 1 && c[k] <= f.hi[k] + 1;
+      }
+      if (!near) continue;
+      const double* p = &P3[3 * (size_t)i];
+      double d[3] = {gr.o[0] + (c[0] + 0.5) * gr.h[0] - p[0], gr.o[1] + (c[1] + 0.5) * gr.h[1] - p[1],
+                     gr.o[2] + (c[2] + 0.5) * gr.h[2] - p[2]};
+      double qq = quad3(f.Si, d);
+      if (in_box && qq < f.Q) acc += R[i] * std::exp(-0.5 * qq);
+      bool near_box = false;
+      for (int k = 0; k < 3; ++k)
+        near_box = near_box || std::fabs(c[k] - f.flo[k]) <= idx_band ||
+                   std::fabs(c[k] - f.fhi[k]) <= idx_band;
+      bool near_cut = std::fabs(qq - f.Q) <= rel_band * f.Q;
+      if (near_cut || (near_box && qq < f.Q * (1.0 + rel_band)))
+        al += std::fabs(R[i]) * std::exp(-0.5 * std::min(qq, f.Q));
+    }
+    out[t] = acc;
+    allow[t] = al;
   }
 }
 

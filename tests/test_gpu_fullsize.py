@@ -1,14 +1,22 @@
-"""Full-size parity on sampled outputs: the rasterizer at 75 cone views of 1024^2 with 200k
-Gaussians and of 2048^2 with 500k Gaussians, and the voxelizer at 1024^3 with 500k Gaussians,
-each against the FP64 oracle evaluated pixel by pixel (voxel by voxel)."""
+"""Full-size parity on sampled outputs, in the launch configuration the benchmark times
+(tile 16, all 75 views): the rasterizer at 75 cone views of 512^2 (50k Gaussians), 1024^2
+(200k) and 2048^2 (500k), the voxelizer at 1024^3 (500k), each against the FP64 oracle
+evaluated output by output with the same per-output guard-band allowance as the small tests
+(1e-4 of the peak plus the contributions of pairs within the band of the cut or a box edge);
+and the per-Gaussian gradient of sampled Gaussians at 512^2 and 1024^2 against the oracle's
+dual-number gradient (a Gaussian's gradient needs only its own footprint, so the oracle runs
+on the sampled Gaussians alone against the full dL/dI)."""
 import numpy as np
 import pytest
 import torch
 
 import synth
-from tests.helpers import IMG_TOL, to_dev
+from tests.helpers import IMG_TOL, REL_BAND, assert_grads_close, grads11, px_band, to_dev
 
 pytestmark = pytest.mark.gpu
+
+IDX_BAND = 2e-4
+N_SAMPLES = 1200
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +30,21 @@ def gsct():
     return g
 
 
-@pytest.mark.parametrize("side,n,median", [(1024, 200000, 0.008), (2048, 500000, 0.006)])
+def _gather(t, idx):
+    ix = [torch.from_numpy(idx[:, k]).long().to(t.device) for k in range(3)]
+    return t[ix[0], ix[1], ix[2]].cpu().numpy().astype(np.float64)
+
+
+def _check(got, want, allow, min_nonzero=0.3):
+    peak = float(np.abs(want).max())
+    assert peak > 0 and (want != 0).mean() > min_nonzero
+    bound = IMG_TOL * peak + allow
+    err = np.abs(got - want)
+    assert (err <= bound).all(), (float((err / bound).max()), int((err > bound).sum()))
+
+
+@pytest.mark.parametrize("side,n,median", [(512, 50000, 0.012), (1024, 200000, 0.008),
+                                           (2048, 500000, 0.006)])
 def test_raster_full_size_sampled(orc, gsct, side, n, median):
     mr, sc, qt = synth.gaussians(40 + side, n, radius=0.8, scale_median=median,
                                  scale_sigma_log=0.4)
@@ -30,30 +52,57 @@ def test_raster_full_size_sampled(orc, gsct, side, n, median):
     proj = gsct.Projector(views, side, side, tile=16)
     img = proj.forward(*to_dev(mr, sc, qt))
     assert proj.status().code == 0
-    pix = synth.pixel_samples(side, 75, side, side, 48)
-    got = img[torch.from_numpy(pix[:, 0]).long().cuda(), torch.from_numpy(pix[:, 1]).long().cuda(),
-              torch.from_numpy(pix[:, 2]).long().cuda()].cpu().numpy()
-    peak = float(img.abs().max())
+    pix = synth.pixel_samples(side, 75, side, side, N_SAMPLES)
+    got = _gather(img, pix)
     del img, proj
     torch.cuda.empty_cache()
     P, V = orc.params64(mr, sc, qt), orc.views64(views)
-    want = orc.project_pixels(P, V, side, side, pix)
-    assert np.all(np.abs(got - want) <= IMG_TOL * peak + 2e-3 * np.abs(want)), \
-        float(np.abs(got - want).max() / peak)
+    want, allow = orc.project_pixels_allow(P, V, side, side, pix, REL_BAND, px_band(side, side))
+    _check(got, want, allow)
 
 
 def test_voxelize_1024_sampled(orc, gsct):
     n = 500000
     mr, sc, qt = synth.gaussians(77, n, scale_median=0.004, scale_sigma_log=0.4)
     grid = synth.cube_grid(1024)
+    d = to_dev(mr, sc, qt)
     vox = gsct.Voxelizer(grid)
-    vol = vox.forward(*to_dev(mr, sc, qt))
+    vol = vox.forward(*d)
     assert vox.status().code == 0
-    idx = synth.voxel_samples(5, (1024, 1024, 1024), 64)
-    got = vol[torch.from_numpy(idx[:, 0]).long().cuda(), torch.from_numpy(idx[:, 1]).long().cuda(),
-              torch.from_numpy(idx[:, 2]).long().cuda()].cpu().numpy()
-    peak = float(vol.abs().max())
-    del vol, vox
+    idx = synth.voxel_samples(5, (1024, 1024, 1024), N_SAMPLES)
+    got = _gather(vol, idx)
+    # the 64-voxel bricks give the same volume bit for bit at full size
+    vox64 = gsct.Voxelizer(grid, brick=64)
+    assert torch.equal(vox64.forward(*d), vol)
+    del vol, vox, vox64
     torch.cuda.empty_cache()
-    want = orc.voxelize_points(orc.params64(mr, sc, qt), grid, idx)
-    assert np.all(np.abs(got - want) <= IMG_TOL * peak + 2e-3 * np.abs(want))
+    want, allow = orc.voxelize_points_allow(orc.params64(mr, sc, qt), grid, idx, REL_BAND,
+                                            IDX_BAND)
+    _check(got, want, allow, min_nonzero=0.15)
+
+
+@pytest.mark.parametrize("side,n,median", [(512, 50000, 0.012), (1024, 200000, 0.008)])
+def test_raster_gradients_full_size_sampled(orc, gsct, side, n, median):
+    mr, sc, qt = synth.gaussians(60 + side, n, radius=0.8, scale_median=median,
+                                 scale_sigma_log=0.4)
+    views = synth.cone_views(75, side, side)
+    rng = np.random.default_rng(side)
+    w = rng.standard_normal((75, side, side), dtype=np.float32)
+    proj = gsct.Projector(views, side, side, tile=16)
+    d = to_dev(mr, sc, qt)
+    proj.forward(*d)
+    got = grads11(*proj.backward(*d, torch.from_numpy(w).cuda(), reuse=True))
+    assert proj.status().code == 0
+    del proj
+    torch.cuda.empty_cache()
+    # 200 sampled Gaussians with no guard-band pair in any of the 75 views (the oracle's
+    # flags alone decide; with 75 views one Gaussian in 7 (512^2) to 55 (1024^2) has none)
+    cand = np.sort(rng.choice(n, 30000, replace=False))
+    V = orc.views64(views)
+    flags = orc.pair_flags(orc.params64(mr, sc, qt)[cand], V, side, side, REL_BAND,
+                           px_band(side, side))
+    clean = cand[~(flags != 0).any(axis=0)]
+    assert len(clean) >= 200, len(clean)
+    sel = clean[:200]
+    want = orc.project_grad(orc.params64(mr, sc, qt)[sel], V, side, side, w)
+    assert_grads_close(got[sel], want, np.ones(len(sel), dtype=bool))

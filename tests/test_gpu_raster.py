@@ -284,24 +284,6 @@ def test_autograd_function(gsct):
         assert torch.allclose(t.grad, r, rtol=1e-5, atol=1e-5 * float(r.abs().max()))
 
 
-def test_full_size_sampled_pixels(orc, gsct):
-    """75 cone views of 512x512 with 50,000 Gaussians (the reconstruction workload's launch
-    configuration): sampled pixels against the oracle computed one by one."""
-    W = H = 512
-    mr, sc, qt = synth.gaussians(17, 50000, radius=0.8, scale_median=0.012, scale_sigma_log=0.4)
-    views = synth.cone_views(75, W, H)
-    proj = gsct.Projector(views, W, H, tile=16)
-    img = proj.forward(*to_dev(mr, sc, qt)).cpu().numpy()
-    assert proj.status().code == 0
-    pix = synth.pixel_samples(3, 75, W, H, 96)
-    P, V = orc.params64(mr, sc, qt), orc.views64(views)
-    want = orc.project_pixels(P, V, W, H, pix)
-    got = img[pix[:, 0], pix[:, 1], pix[:, 2]]
-    peak = float(np.abs(img).max())
-    assert np.all(np.abs(got - want) <= IMG_TOL * peak + 2e-3 * np.abs(want)), \
-        float(np.abs(got - want).max() / peak)
-
-
 def test_view_chunking_matches_single_call(gsct, monkeypatch):
     """When the views need more pairs than one call can sort, the projector splits them into
     chunks: images are identical to the single call, gradients agree (unordered atomics)."""

@@ -427,6 +427,35 @@ def test_near_plane_culls(orc):
     assert orc.footprints(P, V, 16, 16)["why"][0, 0] == 1
 
 
+def test_pixel_list_values_and_allowances_match_full_images(orc):
+    """The sampled-pixel form used by the full-size checks gives, at every listed pixel, the
+    value of the whole-image projection and the allowance of the whole-image guard band
+    (both pinned above).  Catches a wrong box test, a missed view or a pixel index swap."""
+    W, H = 40, 32
+    P = _rand_P(31, 300, radius=0.6, median=0.04)
+    V = orc.views64(synth.cone_views(5, W, H))
+    img, _ = orc.project(P, V, W, H)
+    allow = orc.project_ambiguity(P, V, W, H, 2e-5, 1e-4 + 4e-6 * W)
+    pix = synth.pixel_samples(9, 5, W, H, 700)
+    val, al = orc.project_pixels_allow(P, V, W, H, pix, 2e-5, 1e-4 + 4e-6 * W)
+    np.testing.assert_allclose(val, img[pix[:, 0], pix[:, 1], pix[:, 2]], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(al, allow[pix[:, 0], pix[:, 1], pix[:, 2]], rtol=1e-12, atol=1e-15)
+    assert (val > 0).mean() > 0.5 and (al > 0).any()
+
+
+def test_voxel_list_values_and_allowances_match_full_volume(orc):
+    grid = synth.cube_grid(24)
+    P = _rand_P(32, 200, radius=0.6, median=0.06)
+    vol, _ = orc.voxelize(P, grid)
+    # wide bands, so that many sampled voxels carry an allowance
+    allow = orc.voxelize_ambiguity(P, grid, (0, 0, 0), (24, 24, 24), 0.2, 0.3)
+    idx = synth.voxel_samples(4, (24, 24, 24), 900)
+    val, al = orc.voxelize_points_allow(P, grid, idx, 0.2, 0.3)
+    np.testing.assert_allclose(val, vol[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(al, allow[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=1e-12, atol=1e-15)
+    assert (val > 0).mean() > 0.15 and (al > 0).any()
+
+
 def test_project_matches_box_free_evaluation(orc):
     """Brute force without any box: every pixel of the detector evaluated against every
     footprint reproduces the image, so the box never drops an in-cut pixel."""
