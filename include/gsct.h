@@ -663,6 +663,64 @@ int gs_adam_flat(float* d_p, float* d_m, float* d_v, const float* d_g, int64_t n
 int gs_colsum(const float* d_g, int rows, int cols, float* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * The per-brick MLP as one network: 4096 -> 256 -> 256 -> 256 -> 384 (352 outputs used, the
+ * rest zero), ReLU on the hidden layers, BF16 weights and activations, FP32 accumulation and
+ * FP32 master parameters.  The paper has no learned initializer; this network is an addition
+ * to its method (FDK bricks in, Gaussian parameters out, the FDK-gradient initialisation of
+ * Sec. 3.1 as the fallback).
+ *
+ * Parameter layout: ONE float array of gs_mlp_param_count() values, in this order:
+ *   W1 [256][4096], W2 [256][256], W3 [256][256], W4 [384][256]   (row-major, [out][in])
+ *   b1 [256], b2 [256], b3 [256], b4 [384]
+ * The BF16 weights (d_w16) are gs_mlp_weight_count() values: W1..W4 in the same order.  Adam
+ * moments (d_m, d_v) and gradients (d_grad) use the parameter layout.  Batches hold M bricks,
+ * M a positive multiple of 128; inputs d_x16 are M x 4096 bf16 (a brick's voxels [z][y][x]),
+ * targets M x 4096 float.  All arrays 16-byte aligned.  d_err: device int, GS_ERR_TIMEOUT if a
+ * GEMM pipeline wait gave up (the caller zeroes it).
+ * ------------------------------------------------------------------------------------- */
+#define GS_MLP_IN 4096
+#define GS_MLP_HIDDEN 256
+#define GS_MLP_OUT 352
+#define GS_MLP_OUT_PAD 384
+
+size_t gs_mlp_param_count(void);
+size_t gs_mlp_weight_count(void);
+/* Scratch bytes for batches of M bricks (activations, transposes, output gradients). */
+size_t gs_mlp_workspace_size(int M);
+
+/* d_w16 = bf16(weights of d_params). */
+int gs_mlp_sync_bf16(const float* d_params, void* d_w16, void* stream);
+
+/* Forward pass: raw outputs d_y (M x 384 float, columns 352.. are the zero padding's) from
+ * d_x16; the hidden activations stay in the workspace for gs_mlp_backward. */
+int gs_mlp_forward(const float* d_params, const void* d_w16, const void* d_x16, int M,
+                   float* d_y, void* d_ws, size_t ws_bytes, int* d_err, void* stream);
+
+/* Backward pass of the last gs_mlp_forward on the same workspace and inputs: given dL/dy
+ * (d_dy, M x 384, padding columns zero), OVERWRITES d_grad (parameter layout) with
+ * dL/d(parameters). */
+int gs_mlp_backward(const void* d_w16, const void* d_x16, int M, const float* d_dy,
+                    float* d_grad, void* d_ws, size_t ws_bytes, int* d_err, void* stream);
+
+/* One training step on a batch: forward, the brick render + L1 loss of gs_brick_loss against
+ * d_target (*d_loss INCREMENTED by the batch's mean |render - target|), backward, Adam on all
+ * parameters with the device step count *d_step (bias correction step *d_step + 1), the bf16
+ * weights refreshed, then *d_step += 1.  d_grad receives the step's gradient.  Equal, bit for
+ * bit, to the sequence gs_mlp_forward, gs_brick_loss, gs_mlp_backward, gs_adam_flat over the
+ * weights (with their bf16 copy) and over the biases, gs_step_incr. */
+int gs_mlp_train_step(float* d_params, void* d_w16, float* d_m, float* d_v, float* d_grad,
+                      int* d_step, const void* d_x16, const float* d_target, int M, float lr,
+                      float beta1, float beta2, float eps, float* d_loss, void* d_ws,
+                      size_t ws_bytes, int* d_err, void* stream);
+
+/* Inference: the Gaussians of M bricks (32 per brick, gs_brick_decode of the forward's raw
+ * outputs): d_geo float4 per brick = (origin x, y, z, voxel size), densities times amp;
+ * writes 32 M records to each of d_mean_rho, d_scale, d_quat. */
+int gs_mlp_infer(const float* d_params, const void* d_w16, const void* d_x16, int M,
+                 const float* d_geo, float amp, float* d_mean_rho, float* d_scale, float* d_quat,
+                 void* d_ws, size_t ws_bytes, int* d_err, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Binning internals exposed for testing: the sorted (key, value) lists of the last binning
  * in a workspace.  Copies min(pairs, cap) entries to host arrays (SYNCHRONOUS).  Rasterizer:
  * key = (global view << b) | tile, where the global view is the instance's first view + view,

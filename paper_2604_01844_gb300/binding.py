@@ -179,6 +179,16 @@ SIGNATURES = {
     "gs_adam_flat": (_I, [_P, _P, _P, _P, _I64, _P, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, ctypes.c_float, _P, _P]),
     "gs_step_incr": (_I, [_P, _P]),
+    "gs_mlp_param_count": (_SZ, []),
+    "gs_mlp_weight_count": (_SZ, []),
+    "gs_mlp_workspace_size": (_SZ, [_I]),
+    "gs_mlp_sync_bf16": (_I, [_P, _P, _P]),
+    "gs_mlp_forward": (_I, [_P, _P, _P, _I, _P, _P, _SZ, _P, _P]),
+    "gs_mlp_backward": (_I, [_P, _P, _I, _P, _P, _P, _SZ, _P, _P]),
+    "gs_mlp_train_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _SZ, _P,
+                               _P]),
+    "gs_mlp_infer": (_I, [_P, _P, _P, _I, _P, ctypes.c_float, _P, _P, _P, _P, _SZ, _P, _P]),
     "gs_timing_enable": (None, [_I]),
     "gs_timing_reset": (None, []),
     "gs_timing_read": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),

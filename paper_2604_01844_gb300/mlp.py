@@ -1,8 +1,9 @@
 """Per-brick MLP initializer: a 16^3 FDK brick (4096 values) -> 3 hidden layers of 256 (ReLU)
 -> 32 Gaussians x 11 raw parameters, BF16 weights and activations with FP32 accumulation on the
 library's tcgen05 GEMM.  Trained through the fused brick render + L1 kernel (gs_brick_loss), so
-that the unordered set of 32 Gaussians needs no matching.  This module only orders the library
-calls; every operation is a libgsct kernel.
+that the unordered set of 32 Gaussians needs no matching.  The network's forward, backward,
+training step and inference are single library calls (gs_mlp_*); this module allocates their
+buffers and marshals the arguments.
 """
 from __future__ import annotations
 
@@ -24,11 +25,19 @@ def _s():
 
 
 class BrickMLP:
+    """Device state of the network in the library's flat layout (gs_mlp_param_count FP32
+    parameters W1..W4, b1..b4; BF16 weights; Adam moments; gradients) and the calls of its
+    forward, backward, training step and inference."""
+
     def __init__(self, seed: int = 0, device="cuda"):
         self.device = torch.device(device)
+        L = B.lib()
+        n_par, n_w = int(L.gs_mlp_param_count()), int(L.gs_mlp_weight_count())
         rng = np.random.default_rng(seed)
         shapes = [(HIDDEN, K_IN), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN), (N_OUT_PAD, HIDDEN)]
-        self.W, self.b = [], []
+        flat = np.zeros(n_par, dtype=np.float32)
+        off = 0
+        ws, bs = [], []
         for li, (o, i) in enumerate(shapes):
             w = rng.standard_normal((o, i)) * np.sqrt(2.0 / i)
             b = np.zeros(o)
@@ -38,118 +47,98 @@ class BrickMLP:
                 # start from the lattice (offsets 0, base scales) with densities about the
                 # mean intensity of a normalised brick
                 b[:N_OUT].reshape(32, 11)[:, 10] = -0.5
-            self.W.append(torch.from_numpy(w.astype(np.float32)).to(self.device))
-            self.b.append(torch.from_numpy(b.astype(np.float32)).to(self.device))
-        self.W16 = [torch.empty(w.shape, dtype=torch.bfloat16, device=self.device) for w in self.W]
+            ws.append(w)
+            bs.append(b)
+        for w in ws:
+            flat[off:off + w.size] = w.ravel()
+            off += w.size
+        for b in bs:
+            flat[off:off + b.size] = b
+            off += b.size
+        assert off == n_par and sum(w.size for w in ws) == n_w
+        self.flat = torch.from_numpy(flat).to(self.device)
+        self.flat16 = torch.empty(n_w, dtype=torch.bfloat16, device=self.device)
+        self.flat_m = torch.zeros_like(self.flat)
+        self.flat_v = torch.zeros_like(self.flat)
+        self.flat_grad = torch.zeros_like(self.flat)
+        # per-tensor views, [out][in] weights then biases
+        self.W, self.b, self.W16, gw, gb = [], [], [], [], []
+        off = 0
+        for o, i in shapes:
+            self.W.append(self.flat[off:off + o * i].view(o, i))
+            self.W16.append(self.flat16[off:off + o * i].view(o, i))
+            gw.append(self.flat_grad[off:off + o * i].view(o, i))
+            off += o * i
+        for o, _ in shapes:
+            self.b.append(self.flat[off:off + o])
+            gb.append(self.flat_grad[off:off + o])
+            off += o
         self.params = self.W + self.b
-        self.m = [torch.zeros_like(p) for p in self.params]
-        self.v = [torch.zeros_like(p) for p in self.params]
-        self.grads = [torch.zeros_like(p) for p in self.params]
+        self.grads = gw + gb
         self.step_count = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.err = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self._ws = {}
         self._sync_bf16()
-        self._bufs = {}
 
     def _sync_bf16(self):
-        for w, w16 in zip(self.W, self.W16):
-            B.check(B.lib().gs_f32_to_bf16(B.ptr(w), B.ptr(w16), w.numel(), _s()), "f32_to_bf16")
+        B.check(B.lib().gs_mlp_sync_bf16(B.ptr(self.flat), B.ptr(self.flat16), _s()),
+                "gs_mlp_sync_bf16")
 
-    def _buf(self, name, shape, dtype):
-        t = self._bufs.get(name)
-        if t is None or tuple(t.shape) != tuple(shape) or t.dtype != dtype:
-            t = torch.empty(shape, dtype=dtype, device=self.device)
-            self._bufs[name] = t
-        return t
-
-    def _gemm(self, a, b, M, N, K, bias=None, relu=False, c32=None, c16=None, ldc=None):
-        B.check(B.lib().gs_gemm_bf16(B.ptr(a), B.ptr(b), M, N, K, B.ptr(bias), 1 if relu else 0,
-                                     B.ptr(c32), B.ptr(c16), ldc or N, B.ptr(self.err), _s()),
-                "gs_gemm_bf16")
+    def workspace(self, M: int) -> torch.Tensor:
+        ws = self._ws.get(M)
+        if ws is None:
+            nbytes = int(B.lib().gs_mlp_workspace_size(M))
+            if nbytes == 0:
+                raise ValueError("the brick batch must be a positive multiple of 128")
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._ws = {M: ws}
+        return ws
 
     # -- forward ----------------------------------------------------------------------
-    def forward(self, x16: torch.Tensor) -> torch.Tensor:
+    def forward(self, x16: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """x16: (M, 4096) bf16, M % 128 == 0 -> raw outputs (M, 384) float32."""
         M = x16.shape[0]
-        if M % 128:
-            raise ValueError("the brick batch must be a multiple of 128")
+        ws = self.workspace(M)
+        y = out if out is not None else torch.empty((M, N_OUT_PAD), dtype=torch.float32,
+                                                    device=self.device)
         self.x16 = x16
-        self.h = []
-        a = x16
-        K = K_IN
-        for li in range(3):
-            h = self._buf(f"h{li}", (M, HIDDEN), torch.bfloat16)
-            self._gemm(a, self.W16[li], M, HIDDEN, K, bias=self.b[li], relu=True, c16=h)
-            self.h.append(h)
-            a, K = h, HIDDEN
-        y = self._buf("y", (M, N_OUT_PAD), torch.float32)
-        self._gemm(a, self.W16[3], M, N_OUT_PAD, HIDDEN, bias=self.b[3], c32=y)
+        B.check(B.lib().gs_mlp_forward(B.ptr(self.flat), B.ptr(self.flat16), B.ptr(x16), M,
+                                       B.ptr(y), B.ptr(ws), ws.numel(), B.ptr(self.err), _s()),
+                "gs_mlp_forward")
         return y
 
     # -- backward ---------------------------------------------------------------------
     def backward(self, dy: torch.Tensor):
         """dy: (M, 384) float32 gradient of the raw outputs (padded columns zero); fills
         self.grads (W1..W4, b1..b4).  Uses the activations of the last forward."""
-        L = B.lib()
         M = dy.shape[0]
-        acts = [self.x16] + self.h  # inputs of layers 0..3
-        g32 = dy
-        g16 = self._buf("g16_out", (M, N_OUT_PAD), torch.bfloat16)
-        B.check(L.gs_f32_to_bf16(B.ptr(g32), B.ptr(g16), g32.numel(), _s()), "f32_to_bf16")
-        width = N_OUT_PAD
-        for li in (3, 2, 1, 0):
-            a_in = acts[li]
-            k_in = a_in.shape[1]
-            # bias gradient
-            B.check(L.gs_colsum(B.ptr(g32), M, width, B.ptr(self.grads[4 + li]), _s()), "colsum")
-            # weight gradient: dW = g^T a_in  (TN GEMM on the transposes, K = M)
-            gT = self._buf(f"gT{li}", (width, M), torch.bfloat16)
-            aT = self._buf(f"aT{li}", (k_in, M), torch.bfloat16)
-            B.check(L.gs_transpose_bf16(B.ptr(g16), M, width, B.ptr(gT), _s()), "transpose")
-            B.check(L.gs_transpose_bf16(B.ptr(a_in), M, k_in, B.ptr(aT), _s()), "transpose")
-            self._gemm(gT, aT, width, k_in, M, c32=self.grads[li])
-            if li == 0:
-                break
-            # gradient of the layer input: g W, then the ReLU of the previous layer
-            WT = self._buf(f"WT{li}", (k_in, width), torch.bfloat16)
-            B.check(L.gs_transpose_bf16(B.ptr(self.W16[li]), width, k_in, B.ptr(WT), _s()),
-                    "transpose")
-            g_prev = self._buf(f"gp{li}", (M, k_in), torch.float32)
-            self._gemm(g16, WT, M, k_in, width, c32=g_prev)
-            g16p = self._buf(f"g16_{li}", (M, k_in), torch.bfloat16)
-            B.check(L.gs_relu_mask_bf16(B.ptr(g_prev), B.ptr(self.h[li - 1]), g_prev.numel(),
-                                        B.ptr(g16p), _s()), "relu_mask")
-            g32, g16, width = g_prev, g16p, k_in
-
-    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-        L = B.lib()
-        for i, (p, m, v, g) in enumerate(zip(self.params, self.m, self.v, self.grads)):
-            p16 = self.W16[i] if i < 4 else None
-            B.check(L.gs_adam_flat(B.ptr(p), B.ptr(m), B.ptr(v), B.ptr(g), p.numel(),
-                                   B.ptr(self.step_count), lr, beta1, beta2, eps, B.ptr(p16),
-                                   _s()), "adam_flat")
-        B.check(L.gs_step_incr(B.ptr(self.step_count), _s()), "step_incr")
+        ws = self.workspace(M)
+        B.check(B.lib().gs_mlp_backward(B.ptr(self.flat16), B.ptr(self.x16), M,
+                                        B.ptr(dy.contiguous()), B.ptr(self.flat_grad),
+                                        B.ptr(ws), ws.numel(), B.ptr(self.err), _s()),
+                "gs_mlp_backward")
 
     # -- training ---------------------------------------------------------------------
-    def train_step(self, x16, target, loss, lr=1e-3):
+    def train_step(self, x16, target, loss, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         """One step on a batch: forward, brick render + L1 (loss += mean |render - target|),
-        backward, Adam."""
-        y = self.forward(x16)
+        backward, Adam (gs_mlp_train_step)."""
         M = x16.shape[0]
-        dy = self._buf("dy", (M, N_OUT_PAD), torch.float32)
-        B.check(B.lib().gs_memset(B.ptr(dy), 0, dy.numel() * 4, _s()), "memset")
-        B.check(B.lib().gs_brick_loss(B.ptr(y), N_OUT_PAD, B.ptr(target), M, B.ptr(loss),
-                                      B.ptr(dy), N_OUT_PAD, None, _s()), "gs_brick_loss")
-        self.backward(dy)
-        self.adam(lr=lr)
+        ws = self.workspace(M)
+        B.check(B.lib().gs_mlp_train_step(
+            B.ptr(self.flat), B.ptr(self.flat16), B.ptr(self.flat_m), B.ptr(self.flat_v),
+            B.ptr(self.flat_grad), B.ptr(self.step_count), B.ptr(x16), B.ptr(target), M, lr,
+            beta1, beta2, eps, B.ptr(loss), B.ptr(ws), ws.numel(), B.ptr(self.err), _s()),
+            "gs_mlp_train_step")
 
     def infer_gaussians(self, x16, geo, amp: float):
         """World-space Gaussians (32 per brick) for the bricks in x16; geo (M, 4) float32 =
-        origin and voxel size of each brick; densities times amp."""
-        y = self.forward(x16)
+        origin and voxel size of each brick; densities times amp (gs_mlp_infer)."""
         M = x16.shape[0]
+        ws = self.workspace(M)
         out = [torch.empty((M * 32, 4), dtype=torch.float32, device=self.device) for _ in range(3)]
-        B.check(B.lib().gs_brick_decode(B.ptr(y), N_OUT_PAD, B.ptr(geo), M, amp,
-                                        *[B.ptr(t) for t in out], _s()), "gs_brick_decode")
+        B.check(B.lib().gs_mlp_infer(B.ptr(self.flat), B.ptr(self.flat16), B.ptr(x16), M,
+                                     B.ptr(geo), amp, *[B.ptr(t) for t in out], B.ptr(ws),
+                                     ws.numel(), B.ptr(self.err), _s()), "gs_mlp_infer")
         return out
 
 

@@ -146,3 +146,25 @@ def test_voxel_batch_table_validation(built):
     assert L.gs_voxelize_batch_workspace_size(t, 4, ctypes.byref(o), 0) == 0
     t[2].roi_lo[1], t[2].n = 0, 0
     assert L.gs_voxelize_batch_workspace_size(t, 4, ctypes.byref(o), 0) > 0
+
+
+def test_mlp_network_layout_and_host_errors(built):
+    """The flat parameter layout's size, and the MLP entry points' argument checks (batch not
+    a multiple of 128, workspace too small) answered on the host before any launch."""
+    from paper_2604_01844_gb300 import binding as B
+
+    L = B.lib()
+    weights = 256 * 4096 + 2 * 256 * 256 + 384 * 256
+    assert L.gs_mlp_weight_count() == weights
+    assert L.gs_mlp_param_count() == weights + 3 * 256 + 384
+    assert L.gs_mlp_workspace_size(100) == 0 and L.gs_mlp_workspace_size(0) == 0
+    ws = L.gs_mlp_workspace_size(256)
+    assert ws > 256 * 4096 * 2  # holds at least the transposed input of the first layer
+    fake = 1 << 20  # never dereferenced: the checks fail first
+    rc = L.gs_mlp_forward(fake, fake, fake, 100, fake, fake, ws, fake, None)
+    assert rc == B.GS_ERR_ARG
+    rc = L.gs_mlp_forward(fake, fake, fake, 256, fake, fake, ws - 1, fake, None)
+    assert rc == B.GS_ERR_CAPACITY
+    rc = L.gs_mlp_train_step(fake, fake, fake, fake, fake, fake, fake, None, 256, 1e-3, 0.9,
+                             0.999, 1e-8, fake, fake, ws, fake, None)
+    assert rc == B.GS_ERR_ARG
