@@ -499,15 +499,24 @@ def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
 LR_FAST = dict(lr_mean=1.6e-3, lr_rho=2e-2, lr_scale=2e-2, lr_quat=2e-3)
 LR_BASE = dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)
 
-# learned start: half of the Gaussian budget from the MLP (its outputs under 5 % of the peak
-# density dropped), the rest from gradient sampling
-LEARNED_INIT = dict(mlp_share=0.5, min_rho_frac=0.05)
+# learned start: the MLP on every brick above 5 % of the FDK volume's maximum, the largest-mass
+# Gaussians up to the budget, any remainder gradient-sampled from the residual
+LEARNED_INIT = dict(frac=0.05)
 
 
-def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_steps=3000):
-    """Per-brick MLP initializer (trained here on n_train phantoms with other seeds) against
-    the FDK-gradient initialisation on the 40-ellipsoid phantom: PSNR after 10 iterations and
-    GPU time to target_db (evaluated every iteration)."""
+def _first_at(hist, target):
+    """(iteration, gpu ms) of the first evaluation at or above target, or None."""
+    return next(((it, ms) for it, ms, db in hist if db >= target), None)
+
+
+def learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=40,
+                     train_steps=3000):
+    """Per-brick MLP initializer against the FDK-gradient initialisation on the 40-ellipsoid
+    phantom (75 cone views of 512^2, 50k Gaussians, 256^3).  The MLP is trained here on the
+    voxelization of gs_fit_volume fits of n_fit phantoms with other seeds.  The plain form runs
+    ref_iters iterations; its PSNR then is the reference the learned start must reach.
+    Reported: PSNR of each start, GPU time (initialisation included) to 35 dB and to the
+    reference."""
     import numpy as np
     import torch
 
@@ -522,66 +531,85 @@ def learned_vs_plain(device, target_db=35.0, max_iters=120, n_train=40, train_st
     grid = synth.cube_grid(256)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    X, T = I.training_set([10 ** 6 + j for j in range(n_train)], views, 512, 512, grid,
-                          device=device)
+    X, T, fit_db = I.fit_training_set([10 ** 6 + j for j in range(n_fit)], views, 512, 512,
+                                      grid, 50000, fit_iters=100, device=device)
     mlp = BrickMLP(seed=0, device=device)
-    hist = I.train(mlp, X, T, steps=train_steps, batch=1024, lr=3e-4)
+    hist = I.train(mlp, X, T, steps=train_steps, batch=1024, lr=1e-3)
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
+    n_bricks = int(X.shape[0])
     del X, T
     prob = PhantomProblem(synth.ellipsoid_phantom(1, 40), views, 512, 512, grid, device=device)
     u = np.random.default_rng(7).random((50000, 4)).astype(np.float32)
     sse = torch.zeros(1, dtype=torch.float64, device=device)
     # warm the inference path once (module load, tensor-map set-up) outside the timing
     I.learned_init(mlp, fdk_volume(prob, grid), grid, 50000, u, **LEARNED_INIT)
-    out = {"train_ms": round(train_ms, 1),
+    out = {"train_ms": round(train_ms, 1), "fits": n_fit, "train_bricks": n_bricks,
+           "fit_psnr_db_min_mean": [round(min(fit_db), 2), round(float(np.mean(fit_db)), 2)],
            "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)],
            "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3",
-           "learned_init": LEARNED_INIT}
-    lr_sets = {"plain": [LR_FAST, LR_BASE], "learned": [LR_FAST, LR_BASE]}
-    for name in ("plain", "learned"):
+           "learned_init": LEARNED_INIT, "ref_iters": ref_iters, "eval_every": eval_every}
+
+    def start(kind):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         fdk = fdk_volume(prob, grid)
-        if name == "plain":
+        if kind == "plain":
             mr, sc, q = gradient_init(fdk, grid, 50000, u)
             n_mlp = 0
         else:
             mr, sc, q, n_mlp = I.learned_init(mlp, fdk, grid, 50000, u, **LEARNED_INIT)
         b.record()
         torch.cuda.synchronize()
-        init_ms = a.elapsed_time(b)
-        runs = []
-        for lrs in lr_sets[name]:
-            rec = Reconstruction(views, 512, 512, prob.proj.clone(), grid, mr.cpu().numpy(),
-                                 sc.cpu().numpy(), q.cpu().numpy(), cfg=ReconConfig(**lrs),
-                                 device=device)
-            p0 = psnr_of(rec.voxelizer.forward(*rec.act), prob.gt, prob.peak, sse)
-            h, ok = reconstruct_to_psnr(rec, prob.gt, prob.peak, max_iters, target_db, 1)
-            at10 = next((x[2] for x in h if x[0] == 10), None)
-            runs.append({"lr_mean": lrs["lr_mean"], "reached": ok, "iters": h[-1][0],
-                         "ms_optimise": round(h[-1][1], 2),
-                         "ms_total": round(h[-1][1] + init_ms, 2),
-                         "psnr_init_db": round(p0, 2),
-                         "psnr_at_10_db": round(at10, 2) if at10 else None})
-        best = min((r for r in runs if r["reached"]), key=lambda r: r["ms_total"],
-                   default=runs[0])
-        out[name] = {"init_ms": round(init_ms, 2), "gaussians_from_mlp": n_mlp, "runs": runs,
-                     "best_ms_to_target": best["ms_total"] if best["reached"] else None}
+        return (mr.cpu().numpy(), sc.cpu().numpy(), q.cpu().numpy()), a.elapsed_time(b), n_mlp
+
+    def run(params, lrs, target, iters):
+        rec = Reconstruction(views, 512, 512, prob.proj.clone(), grid, *params,
+                             cfg=ReconConfig(**lrs), device=device)
+        p0 = psnr_of(rec.voxelizer.forward(*rec.act), prob.gt, prob.peak, sse)
+        h, ok = reconstruct_to_psnr(rec, prob.gt, prob.peak, iters, target, eval_every)
+        return p0, h
+
+    params, init_ms, _ = start("plain")
+    p0, h = run(params, LR_FAST, float("inf"), ref_iters)
+    ref_db = h[-1][2]
+    at35 = _first_at(h, 35.0)
+    out["plain"] = {"init_ms": round(init_ms, 2), "psnr_start_db": round(p0, 2),
+                    "psnr_ref_db": round(ref_db, 2),
+                    "ms_to_ref": round(h[-1][1] + init_ms, 2),
+                    "ms_to_35db": round(at35[1] + init_ms, 2) if at35 else None,
+                    "iters_to_35db": at35[0] if at35 else None}
+    params, init_ms, n_mlp = start("learned")
+    runs = []
+    for lrs in (LR_FAST, LR_BASE):
+        p0, h = run(params, lrs, ref_db, max_iters)
+        at35, atref = _first_at(h, 35.0), _first_at(h, ref_db)
+        runs.append({"lr_mean": lrs["lr_mean"], "psnr_start_db": round(p0, 2),
+                     "ms_to_35db": round(at35[1] + init_ms, 2) if at35 else None,
+                     "ms_to_ref": round(atref[1] + init_ms, 2) if atref else None,
+                     "iters_to_ref": atref[0] if atref else None,
+                     "psnr_last_db": round(h[-1][2], 2)})
+    best = min(runs, key=lambda r: r["ms_to_ref"] if r["ms_to_ref"] else float("inf"))
+    out["learned"] = {"init_ms": round(init_ms, 2), "gaussians_from_mlp": n_mlp, "runs": runs,
+                      "ms_to_ref": best["ms_to_ref"]}
+    out["learned_reaches_ref_faster"] = bool(best["ms_to_ref"] and
+                                             best["ms_to_ref"] < out["plain"]["ms_to_ref"])
     return out
 
 
-def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5,
-                             n_train=48, train_steps=3000, seq_steps=5):
+def batched_learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=48,
+                             train_steps=3000, seq_steps=5):
     """16 uneven reconstructions (synth.batch_specs: volumes 128^3-384^3, 25-75 views of
-    256^2-512^2, 10k-80k Gaussians, 40-ellipsoid phantoms) advanced together: one batched
-    rasterizer and voxelizer call per pass, the whole step in one CUDA graph.  Reports the
-    graph step time against the same instances stepped one by one (each in its own graph),
-    and the GPU time until every instance reaches target_db with the per-brick MLP
-    initializer (trained here on n_train phantoms of the same size distribution, other seeds)
-    against the FDK-gradient initialisation; initialisation time included."""
+    256^2-512^2, 10k-80k Gaussians, 40-ellipsoid phantoms).  The plain single-instance form
+    (FDK-gradient start, each instance stepped alone) runs ref_iters iterations per instance;
+    each instance's PSNR then is its reference.  The batched, learned-initialised form (one
+    batched rasterizer and voxelizer call per pass, the whole step in one CUDA graph, starts
+    from the per-brick MLP trained here on gs_fit_volume fits of n_fit phantoms drawn like the
+    instances, other seeds) runs until every instance reaches its reference.  GPU times include
+    the initialisations.  Also: the graph step time against the same instances stepped one by
+    one (each in its own graph), and the batched plain form to the same references."""
     import numpy as np
     import torch
 
@@ -590,32 +618,38 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
     from paper_2604_01844_gb300.batch import BatchGraphStep, BatchReconstruction, batch_to_psnr
     from paper_2604_01844_gb300.mlp import BrickMLP
     from paper_2604_01844_gb300.recon import (GraphStep, PhantomProblem, ReconConfig,
-                                               Reconstruction, fdk_volume, gradient_init)
+                                               Reconstruction, fdk_volume, gradient_init,
+                                               reconstruct_to_psnr)
 
     def ev():
         e = torch.cuda.Event(enable_timing=True)
         e.record()
         return e
 
-    # training set: phantoms drawn like the instances (other seeds)
+    # training set: gs_fit_volume fits of phantoms drawn like the instances (other seeds)
     e0 = ev()
-    Xs, Ts = [], []
-    for sp in synth.batch_specs(seeds=[10 ** 6 + j for j in range(n_train)]):
+    Xs, Ts, fdb = [], [], []
+    for sp in synth.batch_specs(seeds=[10 ** 6 + j for j in range(n_fit)]):
         v = synth.cone_views(sp["n_views"], sp["det"], sp["det"])
-        X, T = I.training_set([sp["seed"]], v, sp["det"], sp["det"], synth.cube_grid(sp["side"]),
-                              device=device)
+        X, T, db = I.fit_training_set([sp["seed"]], v, sp["det"], sp["det"],
+                                      synth.cube_grid(sp["side"]), sp["n"], fit_iters=100,
+                                      device=device)
         Xs.append(X)
         Ts.append(T)
+        fdb += db
     X, T = torch.cat(Xs), torch.cat(Ts)
     del Xs, Ts
     mlp = BrickMLP(seed=0, device=device)
-    hist = I.train(mlp, X, T, steps=train_steps, batch=1024, lr=3e-4)
+    hist = I.train(mlp, X, T, steps=train_steps, batch=1024, lr=1e-3)
     e1 = ev()
     torch.cuda.synchronize()
     out = {"workload": "16 uneven reconstructions (seeds 100-115): volumes 128^3-384^3, "
                        "25-75 cone views of 256^2-512^2, 10k-80k Gaussians",
-           "train_ms": round(e0.elapsed_time(e1), 1), "train_bricks": int(X.shape[0]),
-           "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)]}
+           "train_ms": round(e0.elapsed_time(e1), 1), "fits": n_fit,
+           "train_bricks": int(X.shape[0]),
+           "fit_psnr_db_min_mean": [round(min(fdb), 2), round(float(np.mean(fdb)), 2)],
+           "train_loss_first_last": [round(hist[0], 5), round(hist[-1], 5)],
+           "ref_iters": ref_iters, "eval_every": eval_every}
     del X, T
     specs = synth.batch_specs()
     probs, grids, views = [], [], []
@@ -635,14 +669,17 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
     def init(kind):
         torch.cuda.synchronize()
         a = ev()
-        inst, n_mlp = [], 0
+        inst, n_mlp, ms_each = [], 0, []
         for sp, prob, g, v, u in zip(specs, probs, grids, views, us):
+            c = ev()
             fdk = fdk_volume(prob, g)
             if kind == "plain":
                 mr, sc, q = gradient_init(fdk, g, sp["n"], u)
             else:
                 mr, sc, q, nm = I.learned_init(mlp, fdk, g, sp["n"], u, **LEARNED_INIT)
                 n_mlp += nm
+            d = ev()
+            ms_each.append((c, d))
             inst.append(dict(views=v, W=sp["det"], H=sp["det"], target=prob.proj, grid=g,
                              mean_rho=mr, scale=sc, quat=q))
         b = ev()
@@ -650,12 +687,11 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
         for x in inst:
             for key in ("mean_rho", "scale", "quat"):
                 x[key] = x[key].cpu().numpy()
-        return inst, a.elapsed_time(b), n_mlp
+        return inst, a.elapsed_time(b), n_mlp, [c.elapsed_time(d) for c, d in ms_each]
 
-    plain_lr = LR_FAST
     # step time: batched graph vs the same instances one by one (each its own graph)
-    inst, _, _ = init("plain")
-    rec = BatchReconstruction(inst, cfg=ReconConfig(**plain_lr), device=device)
+    inst, _, _, _ = init("plain")
+    rec = BatchReconstruction(inst, cfg=ReconConfig(**LR_FAST), device=device)
     g = BatchGraphStep(rec, warmup=1)
     g()
     torch.cuda.synchronize()
@@ -664,13 +700,13 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
         g()
     b = ev()
     torch.cuda.synchronize()
-    batched_ms = a.elapsed_time(b) / seq_steps
-    pairs = int(rec.projector.capacity)
+    out["step_ms_batched_graph"] = round(a.elapsed_time(b) / seq_steps, 3)
+    out["pair_capacity"] = int(rec.projector.capacity)
     del rec, g
     seq_ms = 0.0
     for x in inst:
         r = Reconstruction(x["views"], x["W"], x["H"], x["target"], x["grid"], x["mean_rho"],
-                           x["scale"], x["quat"], cfg=ReconConfig(**plain_lr), device=device)
+                           x["scale"], x["quat"], cfg=ReconConfig(**LR_FAST), device=device)
         gs = GraphStep(r, warmup=1)
         gs()
         torch.cuda.synchronize()
@@ -681,26 +717,42 @@ def batched_learned_vs_plain(device, target_db=35.0, max_iters=300, eval_every=5
         torch.cuda.synchronize()
         seq_ms += a.elapsed_time(b) / seq_steps
         del r, gs
-    out["step_ms_batched_graph"] = round(batched_ms, 3)
     out["step_ms_one_by_one_graphs"] = round(seq_ms, 3)
-    out["pair_capacity"] = pairs
-    for kind, lr_sets in (("plain", [LR_FAST, LR_BASE]), ("learned", [LR_FAST, LR_BASE])):
-        inst, init_ms, n_mlp = init(kind)
+
+    # the plain single-instance form, instance after instance: its references
+    refs, plain_ms, plain35 = [], 0.0, 0.0
+    for x, init_k, gt, pk in zip(inst, init("plain")[3], gts, peaks):
+        r = Reconstruction(x["views"], x["W"], x["H"], x["target"], x["grid"], x["mean_rho"],
+                           x["scale"], x["quat"], cfg=ReconConfig(**LR_FAST), device=device)
+        h, _ = reconstruct_to_psnr(r, gt, pk, ref_iters, float("inf"), eval_every)
+        refs.append(h[-1][2])
+        plain_ms += h[-1][1] + init_k
+        at35 = _first_at(h, 35.0)
+        plain35 = plain35 + at35[1] + init_k if (at35 and plain35 is not None) else None
+        del r
+    out["plain_one_by_one"] = {"ms_to_ref": round(plain_ms, 1),
+                               "ms_to_35db": round(plain35, 1) if plain35 else None,
+                               "psnr_ref_db": [round(x, 2) for x in refs]}
+    init("learned")  # first use of the learned start's buffers, outside the timing
+    for kind, lr_sets in (("learned", [LR_FAST, LR_BASE]), ("plain", [LR_FAST])):
+        inst, init_ms, n_mlp, _ = init(kind)
         runs = []
         for lrs in lr_sets:
             rec = BatchReconstruction(inst, cfg=ReconConfig(**lrs), device=device)
-            reached, last, iters, ms = batch_to_psnr(rec, gts, peaks, max_iters, target_db,
+            reached, last, iters, ms = batch_to_psnr(rec, gts, peaks, max_iters, refs,
                                                      eval_every)
             ok = all(r is not None for r in reached)
             runs.append({"lr_mean": lrs["lr_mean"], "all_reached": ok, "iters": iters,
-                         "ms_optimise": round(ms, 1), "ms_total": round(ms + init_ms, 1),
+                         "ms_to_ref": round(ms + init_ms, 1) if ok else None,
                          "iters_per_instance": [r[0] if r else None for r in reached],
-                         "psnr_final_min": round(min(last), 2)})
+                         "psnr_last_min_margin_db": round(min(l - t for l, t in
+                                                              zip(last, refs)), 2)})
             del rec
-        best = min((r for r in runs if r["all_reached"]), key=lambda r: r["ms_total"],
-                   default=None)
-        out[kind] = {"init_ms": round(init_ms, 1), "gaussians_from_mlp": n_mlp, "runs": runs,
-                     "best_ms_to_target": best["ms_total"] if best else None}
+        best = min(runs, key=lambda r: r["ms_to_ref"] if r["ms_to_ref"] else float("inf"))
+        out["batched_" + kind] = {"init_ms": round(init_ms, 1), "gaussians_from_mlp": n_mlp,
+                                  "runs": runs, "ms_to_ref": best["ms_to_ref"]}
+    bl = out["batched_learned"]["ms_to_ref"]
+    out["batched_learned_reaches_refs_faster"] = bool(bl and bl < plain_ms)
     return out
 
 

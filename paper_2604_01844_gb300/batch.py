@@ -185,10 +185,10 @@ class BatchGraphStep:
         return self.rec.loss
 
 
-def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_psnr: float,
+def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_psnr,
                   eval_every: int = 5, graph: bool = True):
-    """Steps the batch until every instance's voxelized volume reaches target_psnr against its
-    ground truth.  Returns (per-instance [(iter, gpu ms)] of first reaching the target or None,
+    """Steps the batch until every instance's voxelized volume reaches target_psnr (one value
+    for all, or one per instance) against its ground truth.  Returns (per-instance [(iter, gpu ms)] of first reaching the target or None,
     per-instance final PSNR, iterations run, total gpu ms).  A step that ran out of pair
     capacity is detected at the evaluation points; the workspaces are then re-planned (and the
     graph captured again)."""
@@ -196,6 +196,7 @@ def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_p
     stepper = BatchGraphStep(rec, warmup=0) if graph else rec.step
     start = torch.cuda.Event(enable_timing=True)
     start.record()
+    targets = list(target_psnr) if hasattr(target_psnr, "__len__") else [target_psnr] * rec.K
     reached = [None] * rec.K
     last = [float("-inf")] * rec.K
     it = 0
@@ -216,7 +217,7 @@ def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_p
             last[k] = psnr_of(vols[k], gts[k], peaks[k], sse)
         ms = start.elapsed_time(ev)
         for k in range(rec.K):
-            if reached[k] is None and last[k] >= target_psnr:
+            if reached[k] is None and last[k] >= targets[k]:
                 reached[k] = (it, ms)
         if all(r is not None for r in reached):
             break

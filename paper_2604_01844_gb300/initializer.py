@@ -1,7 +1,8 @@
-"""Learned initialisation with the per-brick MLP: training set from seeded phantoms (FDK bricks
-as inputs, ground-truth bricks as targets, both scaled by 1 / max(FDK)), training, and the
-inference that turns the FDK of a new scan into Gaussians (32 per non-empty 16^3 brick),
-topped up by gradient sampling when the budget is not filled."""
+"""Learned initialisation with the per-brick MLP: training sets from seeded phantoms (FDK
+bricks as inputs; as targets the voxelization of a gs_fit_volume fit of the phantom, or the
+ground-truth bricks themselves; both scaled by 1 / max(FDK)), training, and the inference that
+turns the FDK of a new scan into Gaussians (32 per non-empty 16^3 brick), topped up by gradient
+sampling when the budget is not filled."""
 from __future__ import annotations
 
 import numpy as np
@@ -38,6 +39,39 @@ def training_set(seeds, views, W, H, grid, n_ell=(20, 60), device="cuda"):
     return torch.cat(xs), torch.cat(ts)
 
 
+def fit_training_set(seeds, views, W, H, grid, n_gauss: int, fit_iters: int = 100,
+                     n_ell=(20, 60), device="cuda"):
+    """Training bricks whose targets come from gs_fit_volume: for every seeded phantom the
+    ground-truth volume is fitted with n_gauss Gaussians (gradient initialisation, then
+    fit_iters iterations of Eq. 6) and the fitted set is voxelized; inputs are the FDK bricks
+    of the phantom's projections.  Returns (x16 (n, 4096) bf16, target (n, 4096) f32, fit
+    PSNRs) over the non-empty bricks; one fit per seed."""
+    from .fit import VolumeFit, fit_opts
+    from .recon import psnr_of
+    from .voxelizer import Voxelizer
+
+    xs, ts, fit_db = [], [], []
+    fit = VolumeFit(grid, n_gauss, device=device)
+    vox = Voxelizer(grid, device=device)
+    sse = torch.zeros(1, dtype=torch.float64, device=device)
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        ell = synth.ellipsoid_phantom(s, int(rng.integers(n_ell[0], n_ell[1] + 1)))
+        prob = PhantomProblem(ell, views, W, H, grid, device=device)
+        fdk = fdk_volume(prob, grid)
+        u = torch.from_numpy(rng.random((n_gauss, 4)).astype(np.float32)).to(device)
+        fit.run(prob.gt, fit_iters, fit_opts(data_range=prob.peak), u)
+        fitted = vox.forward(*fit.params)
+        fit_db.append(psnr_of(fitted, prob.gt, prob.peak, sse))
+        scale = 1.0 / max(float(fdk.max()), 1e-6)
+        nz, ny, nx = fdk.shape
+        keep = _nonempty(fdk, 0.05)
+        ids = torch.from_numpy(brick_ids((nx // 16, ny // 16, nz // 16), keep)).to(device)
+        xs.append(extract(fdk, ids, scale, True))
+        ts.append(extract(fitted, ids, scale, False))
+    return torch.cat(xs), torch.cat(ts), fit_db
+
+
 def train(mlp: BrickMLP, x16, target, steps=1500, batch=1024, lr=1e-3, seed=0):
     """Adam on random batches; returns the loss of every 100th step (synchronising there)."""
     n = x16.shape[0]
@@ -56,34 +90,44 @@ def train(mlp: BrickMLP, x16, target, steps=1500, batch=1024, lr=1e-3, seed=0):
 
 
 def learned_init(mlp: BrickMLP, fdk: torch.Tensor, grid, budget: int, uniforms: np.ndarray,
-                 frac=0.05, mlp_share: float = 1.0, min_rho_frac: float = 0.0):
-    """Gaussians for a new scan: MLP on the non-empty bricks of its FDK volume (the
-    `mlp_share * budget / 32` brightest bricks if there are more), dropping MLP Gaussians whose
-    density is below `min_rho_frac` of the largest, topped up by gradient sampling."""
+                 frac: float = 0.05, mlp_share: float = 1.0, vox=None):
+    """Gaussians for a new scan from its FDK volume: the MLP's 32 Gaussians for every 16^3
+    brick whose maximum exceeds `frac` of the volume's (the brick list padded with the next
+    brightest bricks to the GEMM's 128-row tile).  Over mlp_share of the budget, the Gaussians
+    of largest mass (rho sx sy sz) are kept; the rest of the budget is sampled by the gradient
+    initialisation from the residual max(FDK - voxelized MLP set, 0), so that it goes where the
+    MLP's set falls short.  vox: a Voxelizer of `grid` to reuse for the residual.  Returns
+    (mean_rho, scale, quat, Gaussians from the MLP)."""
+    from .voxelizer import Voxelizer
+
     dev = fdk.device
     nz, ny, nx = fdk.shape
     fmax = max(float(fdk.max()), 1e-6)
     nb = (nx // 16, ny // 16, nz // 16)
     vmax = fdk.reshape(nz // 16, 16, ny // 16, 16, nx // 16, 16).amax(dim=(1, 3, 5)).reshape(-1)
+    if vmax.numel() < 128:
+        raise ValueError("the learned start needs a volume of at least 128 bricks of 16^3")
     order = torch.argsort(vmax, descending=True).cpu().numpy()
-    keep_n = int(min((vmax > frac * fmax).sum().item(), int(budget * mlp_share) // 32))
-    keep_n -= keep_n % 128  # the GEMM tiles 128 rows
-    keep_n = max(keep_n, 128)
+    n_sel = int((vmax > frac * fmax).sum().item())
+    n_sel = min(max(128, -(-n_sel // 128) * 128), vmax.numel() - vmax.numel() % 128)
     sel = np.zeros(vmax.numel(), dtype=bool)
-    sel[order[:keep_n]] = True
+    sel[order[:n_sel]] = True
     ids_np = brick_ids(nb, sel)
-    ids = torch.from_numpy(ids_np).to(dev)
-    x16 = extract(fdk, ids, 1.0 / fmax, True)
+    x16 = extract(fdk, torch.from_numpy(ids_np).to(dev), 1.0 / fmax, True)
     o = np.asarray(grid["origin"], dtype=np.float32).ravel()
     h = float(np.asarray(grid["voxel"]).ravel()[0])
     geo = np.stack([o[0] + ids_np[:, 0] * 16 * h, o[1] + ids_np[:, 1] * 16 * h,
                     o[2] + ids_np[:, 2] * 16 * h, np.full(len(ids_np), h)], 1).astype(np.float32)
     mr, sc, q = mlp.infer_gaussians(x16, torch.from_numpy(geo).to(dev), amp=fmax)
-    if min_rho_frac > 0.0:
-        keep = mr[:, 3] > min_rho_frac * mr[:, 3].max()
+    cap = int(budget * mlp_share)
+    if mr.shape[0] > cap:
+        mass = mr[:, 3] * sc[:, 0] * sc[:, 1] * sc[:, 2]
+        keep = torch.topk(mass, cap).indices.sort().values
         mr, sc, q = mr[keep], sc[keep], q[keep]
-    n_mlp = mr.shape[0]
+    n_mlp = int(mr.shape[0])
     if n_mlp < budget:
-        extra = gradient_init(fdk, grid, budget - n_mlp, uniforms[: budget - n_mlp])
+        vox = vox if vox is not None else Voxelizer(grid, device=dev)
+        resid = (fdk - vox.forward(mr.contiguous(), sc.contiguous(), q.contiguous())).clamp_min(0)
+        extra = gradient_init(resid, grid, budget - n_mlp, uniforms[: budget - n_mlp])
         mr, sc, q = (torch.cat([a, b]) for a, b in zip((mr, sc, q), extra))
-    return mr[:budget].contiguous(), sc[:budget].contiguous(), q[:budget].contiguous(), n_mlp
+    return mr.contiguous(), sc.contiguous(), q.contiguous(), n_mlp
