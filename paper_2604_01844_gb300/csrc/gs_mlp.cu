@@ -23,11 +23,20 @@
 namespace gs {
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64;
+constexpr int kBM = 128, kBN = 128, kBK = 64;  // kBN: the narrower tile (N % 128 == 0)
 constexpr int kStages = 4;
 constexpr int kGemmThreads = 128;
-constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KiB per operand slice
-constexpr uint32_t kSmemBytes = kStages * 2 * kTileBytes + 1024 + 256;
+constexpr uint32_t kTileBytes = kBM * kBK * 2;  // 16 KiB per 128-row operand slice
+// Tile N = BN (128, or 256 when N allows): A slice 128 x 64, B slice BN x 64 per stage.
+template <int BN>
+struct GemmTile {
+  static constexpr uint32_t kBBytes = BN * kBK * 2;
+  static constexpr uint32_t kStageBytes = kTileBytes + kBBytes;
+  static constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+  // instruction descriptor of kind::f16: D f32, A/B bf16, both K-major, M = 128, N = BN
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+};
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -81,15 +90,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor of kind::f16: D f32, A/B bf16, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
+template <int BN>
 __global__ void __launch_bounds__(kGemmThreads)
     k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int M, int N, int K, const float* __restrict__ bias, int relu,
-              float* __restrict__ C32, __nv_bfloat16* __restrict__ C16, int ldc,
+              float* __restrict__ C32, __nv_bfloat16* __restrict__ C16, int ldc, int vec_out,
               int* __restrict__ err) {
+  using TT = GemmTile<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -98,7 +105,7 @@ __global__ void __launch_bounds__(kGemmThreads)
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
   const int ktiles = K / kBK;
 
   if (threadIdx.x == 0) {
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(kGemmThreads)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"(kBN));
+                 "r"(BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -131,9 +138,9 @@ __global__ void __launch_bounds__(kGemmThreads)
         break;
       }
       if (abort_flag) break;
-      mbar_expect_tx(&full[s], 2 * kTileBytes);
+      mbar_expect_tx(&full[s], TT::kStageBytes);
       tma_load_2d(&tmA, &full[s], sA + s * kTileBytes, kt * kBK, m0);
-      tma_load_2d(&tmB, &full[s], sB + s * kTileBytes, kt * kBK, n0);
+      tma_load_2d(&tmB, &full[s], sB + s * TT::kBBytes, kt * kBK, n0);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(kGemmThreads)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * TT::kBBytes);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
         const uint64_t ad = smem_desc(a0 + kk * 32), bd = smem_desc(b0 + kk * 32);
@@ -152,7 +159,7 @@ __global__ void __launch_bounds__(kGemmThreads)
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+            "l"(ad), "l"(bd), "r"(TT::kIdesc), "r"(acc));
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(kGemmThreads)
   } else {
     const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       uint32_t r[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -191,7 +198,37 @@ __global__ void __launch_bounds__(kGemmThreads)
             "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+      if (row < M && vec_out) {
+        // the lane's 32 consecutive columns of its row as 16-byte stores (ldc % 8 == 0 and
+        // 16-byte aligned outputs; N % 128 == 0, so the 32 columns are all inside)
+        const int col0 = n0 + c0;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float x = __uint_as_float(r[j]);
+          if (bias) x += __ldg(bias + col0 + j);
+          v[j] = relu ? fmaxf(x, 0.f) : x;
+        }
+        if (C32) {
+          float4* o = reinterpret_cast<float4*>(C32 + (size_t)row * ldc + col0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        if (C16) {
+          uint4* o = reinterpret_cast<uint4*>(C16 + (size_t)row * ldc + col0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * j + 2 * k], v[8 * j + 2 * k + 1]);
+              w[k] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            o[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      } else if (row < M) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
@@ -209,7 +246,7 @@ __global__ void __launch_bounds__(kGemmThreads)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
 }
 
@@ -235,13 +272,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x cols bf16 row-major (cols contiguous), box kBK x 128 with the 128-byte swizzle
-int make_map(CUtensorMap* map, const void* base, int rows, int cols) {
+// rows x cols bf16 row-major (cols contiguous), box kBK x box_rows with the 128-byte swizzle
+int make_map(CUtensorMap* map, const void* base, int rows, int cols, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return GS_ERR_CUDA;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, 128u};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -309,19 +346,36 @@ int gs_gemm_bf16(const void* d_a, const void* d_b, int M, int N, int K, const fl
   if (M < 1 || N < 1 || K < kBK || K % kBK != 0 || M % kBM != 0 || N % kBN != 0 || ldc < N)
     return GS_ERR_ARG;
   if (((uintptr_t)d_a & 15u) || ((uintptr_t)d_b & 15u)) return GS_ERR_ARG;
+  // 128 x 256 tiles when N allows (A read once per pair of 128-column tiles) and the grid
+  // still covers the SMs, else 128 x 128
+  const int bn = (N % 256 == 0 && (int64_t)(N / 256) * (M / kBM) >= num_sms()) ? 256 : kBN;
+  const int vec = (ldc % 8 == 0 && ((uintptr_t)d_c32 & 15u) == 0 && ((uintptr_t)d_c16 & 15u) == 0)
+                      ? 1 : 0;
   CUtensorMap ma, mb;
-  GS_TRY(make_map(&ma, d_a, M, K));
-  GS_TRY(make_map(&mb, d_b, N, K));
-  static bool attr_set = false;
-  if (!attr_set) {
-    GS_CUDA(cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes));
-    attr_set = true;
+  GS_TRY(make_map(&ma, d_a, M, K, kBM));
+  GS_TRY(make_map(&mb, d_b, N, K, bn));
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  static bool attr_set[2][64] = {};
+  const int which = bn == 256 ? 1 : 0;
+  if (dev < 0 || dev >= 64) return GS_ERR_ARG;
+  if (!attr_set[which][dev]) {
+    if (bn == 256)
+      GS_CUDA(cudaFuncSetAttribute(k_gemm_tn<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)GemmTile<256>::kSmemBytes));
+    else
+      GS_CUDA(cudaFuncSetAttribute(k_gemm_tn<kBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)GemmTile<kBN>::kSmemBytes));
+    attr_set[which][dev] = true;
   }
-  dim3 grid(N / kBN, M / kBM);
-  return launch("gemm_bf16", k_gemm_tn, grid, dim3(kGemmThreads), kSmemBytes,
+  dim3 grid(N / bn, M / kBM);
+  if (bn == 256)
+    return launch("gemm_bf16", k_gemm_tn<256>, grid, dim3(kGemmThreads),
+                  GemmTile<256>::kSmemBytes, (cudaStream_t)stream, ma, mb, M, N, K, d_bias, relu,
+                  d_c32, (__nv_bfloat16*)d_c16, ldc, vec, d_err);
+  return launch("gemm_bf16", k_gemm_tn<kBN>, grid, dim3(kGemmThreads), GemmTile<kBN>::kSmemBytes,
                 (cudaStream_t)stream, ma, mb, M, N, K, d_bias, relu, d_c32,
-                (__nv_bfloat16*)d_c16, ldc, d_err);
+                (__nv_bfloat16*)d_c16, ldc, vec, d_err);
 }
 
 int gs_f32_to_bf16(const float* d_x, void* d_y, int64_t n, void* stream) {

@@ -21,9 +21,11 @@ def _bf16(a):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 128, 256), (384, 256, 4096),
-                                   (1024, 384, 256)])
+                                   (1024, 384, 256), (256, 512, 192), (128, 4096, 128),
+                                   (19456, 256, 128), (9728, 512, 256)])
 @pytest.mark.parametrize("relu", [0, 1])
 def test_gemm_matches_float64(B, M, N, K, relu):
+    """The last two shapes fill the GPU's SMs with 128 x 256 tiles, the others use 128 x 128."""
     rng = np.random.default_rng(M + N + K)
     a = _bf16(rng.standard_normal((M, K)))
     b = _bf16(rng.standard_normal((N, K)))
@@ -53,3 +55,28 @@ def test_gemm_rejects_bad_shapes(B):
     rc = B.lib().gs_gemm_bf16(B.ptr(x), B.ptr(x), 100, 128, 64, None, 0, B.ptr(x), None, 128,
                               B.ptr(err), torch.cuda.current_stream().cuda_stream)
     assert rc == B.GS_ERR_ARG
+
+
+@pytest.mark.parametrize("ldc", [260, 264])
+def test_gemm_row_stride(B, ldc):
+    """Outputs with a row stride wider than N: ldc % 8 == 0 takes the 16-byte store epilogue,
+    other strides the per-element one; both leave the padding columns untouched."""
+    M, N, K = 256, 256, 128
+    rng = np.random.default_rng(ldc)
+    a = _bf16(rng.standard_normal((M, K)))
+    b = _bf16(rng.standard_normal((N, K)))
+    want = a.double() @ b.double().T
+    c32 = torch.full((M, ldc), 7.0, device="cuda")
+    c16 = torch.full((M, ldc), 7.0, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    da, db = a.cuda(), b.cuda()  # held: the library reads them after the call returns
+    B.check(B.lib().gs_gemm_bf16(B.ptr(da), B.ptr(db), M, N, K, None, 0, B.ptr(c32),
+                                 B.ptr(c16), ldc, B.ptr(err),
+                                 torch.cuda.current_stream().cuda_stream), "gemm")
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = c32[:, :N].cpu().double()
+    bound = 2e-6 * K ** 0.5 * (a.double().abs() @ b.double().abs().T) + 1e-6
+    assert bool(((got - want).abs() <= bound).all())
+    assert torch.allclose(c16[:, :N].cpu().double(), got, rtol=1e-2, atol=1e-2)
+    assert bool((c32[:, N:] == 7.0).all()) and bool((c16[:, N:] == 7.0).all())
