@@ -3,12 +3,15 @@
 //
 // gemm_tn:  C[M, N] = A[M, K] . B[N, K]^T (+ bias[N]) (ReLU), A and B bf16 row-major with K
 // contiguous ("K-major"), FP32 accumulation in tensor memory, outputs FP32 and/or BF16.
-// One CTA computes a 128 x 128 tile with 128 threads:
+// One CTA computes a 128 x BN tile with 128 threads, BN = 256 when N is a multiple of 256 and
+// the grid still covers the SMs (A is then streamed once for both halves), else 128:
 //   warp 0 / lane 0  TMA producer: 64-wide K slices of A and B (128-byte swizzle) into a
 //                    4-stage shared-memory ring guarded by mbarriers (full / empty);
-//   warp 1 / lane 0  MMA issuer: 4 x tcgen05.mma (128 x 128 x 16, kind::f16) per slice into a
-//                    128-column TMEM accumulator; tcgen05.commit frees the slice;
-//   all 4 warps      epilogue: tcgen05.ld of their 32 TMEM lanes (rows), bias, ReLU, stores.
+//   warp 1 / lane 0  MMA issuer: 4 x tcgen05.mma (128 x BN x 16, kind::f16) per slice into a
+//                    BN-column TMEM accumulator; tcgen05.commit frees the slice;
+//   all 4 warps      epilogue: tcgen05.ld of their 32 TMEM lanes (rows), bias, ReLU, and each
+//                    lane's 32 consecutive outputs stored as 16-byte vectors (per element
+//                    when the row stride is not a multiple of 8).
 // Every mbarrier wait is bounded; on timeout the kernel records GS_ERR_TIMEOUT in a status word,
 // stops issuing work, still releases its tensor memory, and returns.
 #include <cuda.h>
