@@ -284,6 +284,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     t_end = time.time()
     clk = clocks.stop((t_start, t_end))
+    if rec.overflowed():
+        raise RuntimeError("a workspace of the step ran out of pair capacity during the timed "
+                           "steps: the timing would credit work that was skipped")
     launches = B.launch_count() - launches0
     ms = R.slowest(e0.elapsed_time(e1) / args.steps, device)
     loss = float(rec.loss.item())
@@ -514,7 +517,7 @@ def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
     init_ms = e0.elapsed_time(e1)
     sse = torch.zeros(1, dtype=torch.float64, device=device)
     fdk_db = psnr_of(fdk, prob.gt, prob.peak, sse)
-    cfg = ReconConfig(**LR_FAST)
+    cfg = ReconConfig(**LR_FAST, headroom=LONG_RUN_HEADROOM)
     rec = Reconstruction(views, 512, 512, prob.proj.clone(), grid, mr.cpu().numpy(),
                          sc.cpu().numpy(), q.cpu().numpy(), cfg=cfg, device=device)
     init_db = psnr_of(rec.voxelizer.forward(*rec.act), prob.gt, prob.peak, sse)
@@ -523,7 +526,7 @@ def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
     return {"target_db": target_db, "reached": ok, "iters": it, "ms_optimise": round(ms, 2),
             "ms_fdk_and_init": round(init_ms, 2), "ms_total": round(ms + init_ms, 2),
             "psnr_fdk_db": round(fdk_db, 2), "psnr_init_db": round(init_db, 2),
-            "psnr_final_db": round(db, 2), "eval_every": eval_every,
+            "psnr_final_db": round(db, 2), "eval_every": eval_every, "replans": rec.replans,
             "workload": "40-ellipsoid phantom, 75 cone views x 512^2, 50k Gaussians, 256^3",
             "note": "plain single-instance form; PSNR = 10 log10(max(V_gt)^2 / MSE) on 256^3"}
 
@@ -533,6 +536,11 @@ def time_to_psnr(device, target_db=35.0, max_iters=400, eval_every=5):
 # and plain starts are run with both and the faster is reported for each.
 LR_FAST = dict(lr_mean=1.6e-3, lr_rho=2e-2, lr_scale=2e-2, lr_quat=2e-3)
 LR_BASE = dict(lr_mean=4e-4, lr_rho=2e-2, lr_scale=1e-2, lr_quat=2e-3)
+
+# pair capacity of the long reconstructions, as a multiple of the starting pair counts: the
+# Gaussians grow as they are optimised, and a step that ran out of capacity does incomplete
+# work (the runs count the re-plans they needed)
+LONG_RUN_HEADROOM = 3.0
 
 # learned start: the MLP on every brick above 5 % of the FDK volume's maximum, the largest-mass
 # Gaussians up to the budget, any remainder gradient-sampled from the residual
@@ -602,10 +610,13 @@ def learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=4
 
     def run(params, lrs, target, iters):
         rec = Reconstruction(views, 512, 512, prob.proj.clone(), grid, *params,
-                             cfg=ReconConfig(**lrs), device=device)
+                             cfg=ReconConfig(**lrs, headroom=LONG_RUN_HEADROOM), device=device)
         p0 = psnr_of(rec.voxelizer.forward(*rec.act), prob.gt, prob.peak, sse)
         h, ok = reconstruct_to_psnr(rec, prob.gt, prob.peak, iters, target, eval_every)
+        replans.append(rec.replans)
         return p0, h
+
+    replans = []
 
     params, init_ms, _ = start("plain")
     p0, h = run(params, LR_FAST, float("inf"), ref_iters)
@@ -631,6 +642,7 @@ def learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=4
                       "ms_to_ref": best["ms_to_ref"]}
     out["learned_reaches_ref_faster"] = bool(best["ms_to_ref"] and
                                              best["ms_to_ref"] < out["plain"]["ms_to_ref"])
+    out["replans"] = replans  # pair-capacity overflows met by the runs (0: every step complete)
     return out
 
 
@@ -755,11 +767,13 @@ def batched_learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5,
     out["step_ms_one_by_one_graphs"] = round(seq_ms, 3)
 
     # the plain single-instance form, instance after instance: its references
-    refs, plain_ms, plain35 = [], 0.0, 0.0
+    refs, plain_ms, plain35, plain_replans = [], 0.0, 0.0, 0
     for x, init_k, gt, pk in zip(inst, init("plain")[3], gts, peaks):
         r = Reconstruction(x["views"], x["W"], x["H"], x["target"], x["grid"], x["mean_rho"],
-                           x["scale"], x["quat"], cfg=ReconConfig(**LR_FAST), device=device)
+                           x["scale"], x["quat"],
+                           cfg=ReconConfig(**LR_FAST, headroom=LONG_RUN_HEADROOM), device=device)
         h, _ = reconstruct_to_psnr(r, gt, pk, ref_iters, float("inf"), eval_every)
+        plain_replans += r.replans
         refs.append(h[-1][2])
         plain_ms += h[-1][1] + init_k
         at35 = _first_at(h, 35.0)
@@ -767,13 +781,15 @@ def batched_learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5,
         del r
     out["plain_one_by_one"] = {"ms_to_ref": round(plain_ms, 1),
                                "ms_to_35db": round(plain35, 1) if plain35 else None,
-                               "psnr_ref_db": [round(x, 2) for x in refs]}
+                               "psnr_ref_db": [round(x, 2) for x in refs],
+                               "replans": plain_replans}
     init("learned")  # first use of the learned start's buffers, outside the timing
     for kind, lr_sets in (("learned", [LR_FAST, LR_BASE]), ("plain", [LR_FAST])):
         inst, init_ms, n_mlp, _ = init(kind)
         runs = []
         for lrs in lr_sets:
-            rec = BatchReconstruction(inst, cfg=ReconConfig(**lrs), device=device)
+            rec = BatchReconstruction(inst, cfg=ReconConfig(**lrs, headroom=LONG_RUN_HEADROOM),
+                                      device=device)
             reached, last, iters, ms = batch_to_psnr(rec, gts, peaks, max_iters, refs,
                                                      eval_every)
             ok = all(r is not None for r in reached)
@@ -781,7 +797,8 @@ def batched_learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5,
                          "ms_to_ref": round(ms + init_ms, 1) if ok else None,
                          "iters_per_instance": [r[0] if r else None for r in reached],
                          "psnr_last_min_margin_db": round(min(l - t for l, t in
-                                                              zip(last, refs)), 2)})
+                                                              zip(last, refs)), 2),
+                         "replans": rec.replans})
             del rec
         best = min(runs, key=lambda r: r["ms_to_ref"] if r["ms_to_ref"] else float("inf"))
         out["batched_" + kind] = {"init_ms": round(init_ms, 1), "gaussians_from_mlp": n_mlp,

@@ -56,10 +56,12 @@ class BatchReconstruction:
         views = [x["views"] if isinstance(x["views"], torch.Tensor)
                  else views_to_device(x["views"], dev) for x in instances]
         self.projector = BatchProjector([(v, x["W"], x["H"]) for v, x in zip(views, instances)],
-                                        cut=cfg.cut, tile=cfg.tile, device=dev)
+                                        cut=cfg.cut, tile=cfg.tile, device=dev,
+                                        headroom=cfg.headroom)
         self.grids = [x["grid"] for x in instances]
         self.voxelizer = BatchVoxelizer([(g, (0, 0, 0), None) for g in self.grids], cut=cfg.cut,
-                                        device=dev)
+                                        device=dev, headroom=cfg.headroom)
+        self.replans = 0  # workspaces re-planned after a pair-capacity overflow
         self.img = torch.zeros(self.projector.img_numel, dtype=torch.float32, device=dev)
         self.dimg = torch.zeros_like(self.img)
         self.target = torch.zeros_like(self.img)
@@ -208,6 +210,7 @@ def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_p
             continue
         if rec.overflowed():
             rec.plan()
+            rec.replans += 1
             if graph:
                 stepper = BatchGraphStep(rec, warmup=0)
         vols = rec.volumes()

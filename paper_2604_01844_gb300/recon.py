@@ -38,6 +38,7 @@ class ReconConfig:
     recompute_lists: bool = False  # backward rebuilds the sorted lists instead of reusing them
     overlap_tv: bool = True  # the TV branch runs on a second stream beside the projection
     view_streams: int = 2  # the views split into this many chunks, each on its own stream
+    headroom: float = 1.5  # pair capacity planned as this multiple of the current pair counts
 
 
 def inverse_softplus(x: np.ndarray) -> np.ndarray:
@@ -69,18 +70,22 @@ class Reconstruction:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.target = target.contiguous()
         self.W, self.H = int(W), int(H)
-        self.projector = Projector(views, W, H, cut=cfg.cut, tile=cfg.tile, device=dev)
+        self.projector = Projector(views, W, H, cut=cfg.cut, tile=cfg.tile, device=dev,
+                                   headroom=cfg.headroom)
+        self.replans = 0  # workspaces re-planned after a pair-capacity overflow
         # view chunks of the pipelined step: (v0, v1, projector of those views)
         nv = int(self.target.shape[0])
         k = max(1, min(int(cfg.view_streams), nv))
         bounds = [round(i * nv / k) for i in range(k + 1)]
         self.vchunks = [] if k == 1 else [
             (a, b, Projector(self.projector.views[a:b], W, H, cut=cfg.cut, tile=cfg.tile,
-                             device=dev)) for a, b in zip(bounds[:-1], bounds[1:])]
+                             device=dev, headroom=cfg.headroom))
+            for a, b in zip(bounds[:-1], bounds[1:])]
         if cfg.tv_roi is None:
-            self.voxelizer = Voxelizer(grid, cut=cfg.cut, device=dev)
+            self.voxelizer = Voxelizer(grid, cut=cfg.cut, device=dev, headroom=cfg.headroom)
         else:
-            self.voxelizer = Voxelizer(grid, cfg.tv_roi[0], cfg.tv_roi[1], cut=cfg.cut, device=dev)
+            self.voxelizer = Voxelizer(grid, cfg.tv_roi[0], cfg.tv_roi[1], cut=cfg.cut, device=dev,
+                                       headroom=cfg.headroom)
         self.img = torch.empty_like(self.target)
         self.dimg = torch.empty_like(self.target)
         self.vol = torch.empty(self.voxelizer.shape, dtype=torch.float32, device=dev)
@@ -331,7 +336,11 @@ def psnr_of(vol: torch.Tensor, gt: torch.Tensor, peak: float, sse: torch.Tensor)
 def reconstruct_to_psnr(rec: "Reconstruction", gt: torch.Tensor, peak: float, max_iters: int,
                         target_psnr: float, eval_every: int = 25):
     """Runs rec.step() until the PSNR of its voxelized volume (the TV volume, which covers the
-    ground-truth grid) reaches target_psnr.  Returns (history [(iter, gpu ms, psnr)], reached)."""
+    ground-truth grid) reaches target_psnr.  Returns (history [(iter, gpu ms, psnr)], reached).
+    At every evaluation the workspaces' status is read: when the growing Gaussians have run a
+    step out of pair capacity, the workspaces are re-planned (rec.replans counts it; the steps
+    since the last evaluation did incomplete work, so plan with enough cfg.headroom that this
+    does not happen)."""
     sse = torch.zeros(1, dtype=torch.float64, device=gt.device)
     start = torch.cuda.Event(enable_timing=True)
     start.record()
@@ -341,6 +350,9 @@ def reconstruct_to_psnr(rec: "Reconstruction", gt: torch.Tensor, peak: float, ma
         if it % eval_every == 0 or it == max_iters:
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()
+            if rec.overflowed():
+                rec.plan()
+                rec.replans += 1
             p = psnr_of(rec.vol, gt, peak, sse)
             hist.append((it, start.elapsed_time(ev), p))
             if p >= target_psnr:

@@ -19,18 +19,26 @@ HELD_OUT = [500, 501]
 
 
 @pytest.fixture(scope="module")
-def trained():
+def training_set():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2604_01844_gb300 import build
 
     build.build()
     from paper_2604_01844_gb300 import initializer as I
-    from paper_2604_01844_gb300.mlp import BrickMLP
 
     views = synth.cone_views(NV, DET, DET)
     grid = synth.cube_grid(SIDE)
     X, T, fit_db = I.fit_training_set(TRAIN_SEEDS, views, DET, DET, grid, BUDGET, fit_iters=100)
+    return views, grid, X, T, fit_db
+
+
+@pytest.fixture(scope="module")
+def trained(training_set):
+    from paper_2604_01844_gb300 import initializer as I
+    from paper_2604_01844_gb300.mlp import BrickMLP
+
+    views, grid, X, T, fit_db = training_set
     mlp = BrickMLP(seed=0)
     hist = I.train(mlp, X, T, steps=3000, batch=1024, lr=1e-3)
     torch.cuda.synchronize()
@@ -49,7 +57,26 @@ def _oracle_psnr(orc, params, ell, grid):
 def test_fits_are_good_targets(trained):
     _, _, _, fit_db, hist = trained
     assert min(fit_db) > 30.0, fit_db
-    assert hist[-1] < 0.5 * hist[0], hist
+    # summed L1 of 100 steps: about 0.33 once trained; a run that stalls stays near 1.3, the
+    # loss of rendering nothing
+    assert hist[-1] < 0.6, hist
+
+
+def test_training_survives_last_bit_changes_of_the_targets(training_set):
+    """The fits' atomic sums make the targets differ between processes in their last bits.
+    Training must converge for every such variant: at lr = 1e-3 without the warm-up ramp, half
+    of these variants stalled within 100 steps at the loss of rendering nothing."""
+    from paper_2604_01844_gb300 import initializer as I
+    from paper_2604_01844_gb300.mlp import BrickMLP
+
+    _, _, X, T, _ = training_set
+    last = []
+    for p in range(6):
+        gen = torch.Generator(device=T.device).manual_seed(100 + p)
+        Tp = T * (1 + 1e-6 * torch.randn(T.shape, generator=gen, device=T.device))
+        hist = I.train(BrickMLP(seed=0), X, Tp, steps=400, batch=1024, lr=1e-3)
+        last.append(hist[-1])
+    assert max(last) < 0.9, last
 
 
 @pytest.mark.parametrize("seed", HELD_OUT)
