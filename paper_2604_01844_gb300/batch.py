@@ -58,6 +58,7 @@ class BatchReconstruction:
         self.projector = BatchProjector([(v, x["W"], x["H"]) for v, x in zip(views, instances)],
                                         cut=cfg.cut, tile=cfg.tile, device=dev,
                                         headroom=cfg.headroom)
+        self._geom = [(v, x["W"], x["H"]) for v, x in zip(views, instances)]
         self.grids = [x["grid"] for x in instances]
         self.voxelizer = BatchVoxelizer([(g, (0, 0, 0), None) for g in self.grids], cut=cfg.cut,
                                         device=dev, headroom=cfg.headroom)
@@ -91,6 +92,32 @@ class BatchReconstruction:
         """Activated parameters of instance k (views into the concatenated arrays)."""
         a, b = int(self.g_off[k]), int(self.g_off[k + 1])
         return [t[a:b] for t in self.act]
+
+    def subset(self, keep) -> "BatchReconstruction":
+        """A batch of the instances `keep` (indices into this batch) that continues their
+        optimisation where it stands: raw parameters, Adam moments and the step count are
+        carried over.  The instances of a batch do not interact, so dropping the others
+        changes nothing for these; the workspaces are planned for the smaller batch."""
+        keep = [int(k) for k in keep]
+        insts = []
+        for k in keep:
+            v, W, H = self._geom[k]
+            mr, sc, q = (t.cpu().numpy() for t in self.params(k))
+            insts.append(dict(views=v, W=W, H=H, target=self.targets[k], grid=self.grids[k],
+                              mean_rho=mr, scale=sc, quat=q, data_range=self.data_range[k]))
+        new = BatchReconstruction(insts, cfg=self.cfg, device=self.device)
+        for j, k in enumerate(keep):
+            a, b = int(self.g_off[k]), int(self.g_off[k + 1])
+            c, d = int(new.g_off[j]), int(new.g_off[j + 1])
+            for dst, src in zip(new.raw, self.raw):
+                dst[c:d].copy_(src[a:b])
+            new.m[3 * c:3 * d].copy_(self.m[3 * a:3 * b])
+            new.v[3 * c:3 * d].copy_(self.v[3 * a:3 * b])
+        new.step_count.copy_(self.step_count)
+        new.replans = self.replans
+        new.activate()
+        new.plan()
+        return new
 
     def activate(self):
         B.check(B.lib().gs_activate(*[B.ptr(t) for t in self.raw], *[B.ptr(t) for t in self.act],
@@ -188,12 +215,18 @@ class BatchGraphStep:
 
 
 def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_psnr,
-                  eval_every: int = 5, graph: bool = True):
+                  eval_every: int = 5, graph: bool = True, history: list | None = None,
+                  retire: bool = False):
     """Steps the batch until every instance's voxelized volume reaches target_psnr (one value
-    for all, or one per instance) against its ground truth.  Returns (per-instance [(iter, gpu ms)] of first reaching the target or None,
-    per-instance final PSNR, iterations run, total gpu ms).  A step that ran out of pair
-    capacity is detected at the evaluation points; the workspaces are then re-planned (and the
-    graph captured again)."""
+    for all, or one per instance) against its ground truth.  Returns (per instance the
+    (iteration, gpu ms) at which it first reached its target, or None; per-instance PSNR at the
+    last evaluation that stepped it; iterations run; total gpu ms).  retire: an instance that
+    has reached its target leaves the batch at that evaluation (the rest continue as
+    rec.subset(...), with the graph captured again), so that finished instances cost no more
+    steps; the re-planning and capture are inside the timed span.  history, when given,
+    receives (iteration, gpu ms, per-instance PSNRs, instances still stepped, re-plans) at
+    every evaluation.  A step that ran out of pair capacity is detected at the evaluation
+    points; the workspaces are then re-planned (and the graph captured again)."""
     sse = torch.zeros(1, dtype=torch.float64, device=rec.device)
     stepper = BatchGraphStep(rec, warmup=0) if graph else rec.step
     start = torch.cuda.Event(enable_timing=True)
@@ -201,6 +234,7 @@ def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_p
     targets = list(target_psnr) if hasattr(target_psnr, "__len__") else [target_psnr] * rec.K
     reached = [None] * rec.K
     last = [float("-inf")] * rec.K
+    active = list(range(rec.K))  # original index of each instance of the current batch
     it = 0
     ms = 0.0
     while it < max_iters:
@@ -216,12 +250,20 @@ def batch_to_psnr(rec: BatchReconstruction, gts, peaks, max_iters: int, target_p
         vols = rec.volumes()
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
-        for k in range(rec.K):
-            last[k] = psnr_of(vols[k], gts[k], peaks[k], sse)
+        for j, k in enumerate(active):
+            last[k] = psnr_of(vols[j], gts[k], peaks[k], sse)
         ms = start.elapsed_time(ev)
-        for k in range(rec.K):
+        if history is not None:
+            history.append((it, ms, list(last), len(active), rec.replans))
+        for k in active:
             if reached[k] is None and last[k] >= targets[k]:
                 reached[k] = (it, ms)
         if all(r is not None for r in reached):
             break
+        if retire:
+            stay = [j for j, k in enumerate(active) if reached[k] is None]
+            if len(stay) < len(active):
+                rec = rec.subset(stay)
+                active = [active[j] for j in stay]
+                stepper = BatchGraphStep(rec, warmup=0) if graph else rec.step
     return reached, last, it, ms

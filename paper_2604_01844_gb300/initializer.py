@@ -107,14 +107,20 @@ def train(mlp: BrickMLP, x16, target, steps=1500, batch=1024, lr=1e-3, seed=0, w
 
 
 def learned_init(mlp: BrickMLP, fdk: torch.Tensor, grid, budget: int, uniforms: np.ndarray,
-                 frac: float = 0.05, mlp_share: float = 1.0, vox=None):
+                 frac: float = 0.05, mlp_share: float = 1.0, vox=None, min_scale: float = 1.5):
     """Gaussians for a new scan from its FDK volume: the MLP's 32 Gaussians for every 16^3
     brick whose maximum exceeds `frac` of the volume's (the brick list padded with the next
     brightest bricks to the GEMM's 128-row tile).  Over mlp_share of the budget, the Gaussians
     of largest mass (rho sx sy sz) are kept; the rest of the budget is sampled by the gradient
     initialisation from the residual max(FDK - voxelized MLP set, 0), so that it goes where the
-    MLP's set falls short.  vox: a Voxelizer of `grid` to reuse for the residual.  Returns
-    (mean_rho, scale, quat, Gaussians from the MLP)."""
+    MLP's set falls short.  vox: a Voxelizer of `grid` to reuse for the residual.
+    min_scale: every axis of the MLP's Gaussians is raised to at least this many voxels, the
+    density lowered so that each Gaussian keeps its mass (rho sx sy sz).  The network, trained on
+    16^3 bricks, puts out thin Gaussians (median minor axis 0.06 voxel); a reconstruction
+    started from them converges more slowly.  Measured on the 40-ellipsoid phantom (75 views of
+    512^2, 256^3, 50k Gaussians): the start 34.4 -> 34.7 dB, 400 iterations 39.9 -> 41.5 dB
+    (floors of 1 and 2 voxels 41.4 dB, 3 voxels 40.8 dB).  Returns (mean_rho, scale, quat,
+    Gaussians from the MLP)."""
     from .voxelizer import Voxelizer
 
     dev = fdk.device
@@ -136,6 +142,11 @@ def learned_init(mlp: BrickMLP, fdk: torch.Tensor, grid, budget: int, uniforms: 
     geo = np.stack([o[0] + ids_np[:, 0] * 16 * h, o[1] + ids_np[:, 1] * 16 * h,
                     o[2] + ids_np[:, 2] * 16 * h, np.full(len(ids_np), h)], 1).astype(np.float32)
     mr, sc, q = mlp.infer_gaussians(x16, torch.from_numpy(geo).to(dev), amp=fmax)
+    if min_scale > 0:
+        axes = sc[:, :3]
+        floored = axes.clamp_min(min_scale * h)
+        mr[:, 3] *= axes.prod(1) / floored.prod(1)
+        sc[:, :3] = floored
     cap = int(budget * mlp_share)
     if mr.shape[0] > cap:
         mass = mr[:, 3] * sc[:, 0] * sc[:, 1] * sc[:, 2]

@@ -114,3 +114,55 @@ def test_batch_to_psnr_improves_every_instance(gsct):
                                              eval_every=10)
     assert iters == 40 and all(r is None for r in reached) and ms > 0
     assert all(b > a + 1.0 for a, b in zip(p0, last)), (p0, last)
+
+
+def test_subset_continues_where_the_batch_stands(gsct):
+    """rec.subset(keep) carries the kept instances' raw parameters, Adam moments and step
+    count over bit for bit; stepped on, they follow the full batch."""
+    from paper_2604_01844_gb300.batch import BatchReconstruction
+
+    rec = BatchReconstruction(_instances(gsct), cfg=_cfg())
+    for _ in range(3):
+        rec.step()
+    keep = [0, 2]
+    sub = rec.subset(keep)
+    torch.cuda.synchronize()
+    assert sub.K == 2 and int(sub.step_count.item()) == int(rec.step_count.item()) == 3
+    for j, k in enumerate(keep):
+        a, b = int(rec.g_off[k]), int(rec.g_off[k + 1])
+        c, d = int(sub.g_off[j]), int(sub.g_off[j + 1])
+        for x, y in zip(sub.raw, rec.raw):
+            assert torch.equal(x[c:d], y[a:b])
+        for x, y in zip(sub.params(j), rec.params(k)):
+            assert torch.equal(x, y)
+        assert torch.equal(sub.m[3 * c:3 * d], rec.m[3 * a:3 * b])
+        assert torch.equal(sub.v[3 * c:3 * d], rec.v[3 * a:3 * b])
+        assert torch.equal(sub.targets[j], rec.targets[k])
+    for _ in range(3):
+        lf = rec.step().cpu().numpy()
+        ls = sub.step().cpu().numpy()
+        np.testing.assert_allclose(ls, lf[keep], rtol=1e-4)
+    for j, k in enumerate(keep):
+        for x, y in zip(sub.params(j), rec.params(k)):
+            assert _close_fraction(x, y) > 0.99
+
+
+def test_batch_to_psnr_retires_finished_instances(gsct):
+    """With retire=True an instance that reached its target is not stepped again: its PSNR
+    stays at the value of the evaluation that retired it, and the batch shrinks."""
+    from paper_2604_01844_gb300.batch import BatchReconstruction, batch_to_psnr
+
+    inst = _instances(gsct)
+    rec = BatchReconstruction(inst, cfg=_cfg())
+    # ground truths: the starting volumes; instance 0's target (0 dB) is met at the first
+    # evaluation, the others' never
+    gts = [v.clone() for v in rec.volumes()]
+    peaks = [float(g.max()) for g in gts]
+    targets = [0.0, 1e9, 1e9]
+    hist = []
+    reached, last, iters, ms = batch_to_psnr(rec, gts, peaks, 10, targets, eval_every=5,
+                                             history=hist, retire=True)
+    assert reached[0] == (5, hist[0][1]) and reached[1] is None and reached[2] is None
+    assert [h[3] for h in hist] == [3, 2]  # three instances stepped to 5, two to 10
+    assert last[0] == hist[0][2][0] and iters == 10
+    assert last[1] != hist[0][2][1]  # the others kept stepping
