@@ -1155,6 +1155,8 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
     nvox = side ** 3
     hbm = (measured_peaks() or {}).get("hbm_gbs")
     bytes_per_voxel = {
+        "ssim3d_fwd": 20,     # fused streaming forward: X, Y in; three maps out
+        "ssim3d_bwd": 24,     # fused streaming backward: three maps, X and Y in; the gradient out
         "ssim3d_z_fwd": 28,   # X, Y in; five moments out
         "ssim3d_z_bwd": 24,   # three maps in; three filtered maps out
         "ssim3d_xy_fwd": 32,  # five moments in; three maps out
@@ -1168,6 +1170,18 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
             gbs = bpv * nvox / (per_kernel[k] * 1e-3) / 1e9
             hbm_roofs[k] = {"bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),
                             "peak_gbs": hbm, "frac": round(gbs / hbm, 3)}
+    # the fused 3D SSIM kernels are bound by shared memory, not HBM: per output voxel they move
+    # the TMA-staged boxes in, the y pass's loads and stores and the x pass's 11 float4 loads
+    # (forward 287 B, backward 348 B) through the SM's 128 B/clock shared-memory pipe
+    sms_ = torch.cuda.get_device_properties(device).multi_processor_count
+    fmax_ = (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
+    smem_peak = 128.0 * sms_ * fmax_ * 1e6 / 1e9  # GB/s
+    smem_roofs = {}
+    for k, bpv in {"ssim3d_fwd": 287, "ssim3d_bwd": 348}.items():
+        if k in per_kernel and per_kernel[k] > 0:
+            gbs = bpv * nvox / (per_kernel[k] * 1e-3) / 1e9
+            smem_roofs[k] = {"smem_bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),
+                             "peak_gbs": round(smem_peak, 1), "frac": round(gbs / smem_peak, 3)}
     # the voxel passes against their binding roofline: the larger of the HBM floor (the volume
     # or dL/dV streamed once, 4 B per voxel) and the ALU floor (in-cut evaluations at the
     # evaluation rate of the FP32 / ex2 unit counts at the maximum SM clock, with the scope's
@@ -1194,7 +1208,7 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
             "value": evals / (ms * 1e-3), "unit": "Gaussian-voxel evals/s",
             "status": int(st.code), "loss_last": float(loss[-1].item()),
             "kernels_ms_per_iter": per_kernel,
-            "hbm_rooflines": hbm_roofs, "vox_rooflines": vox_roofs,
+            "hbm_rooflines": hbm_roofs, "smem_rooflines": smem_roofs, "vox_rooflines": vox_roofs,
             "hbm_note": "achieved = algorithmic bytes per voxel x voxels / kernel ms; the voxel "
                         "passes' frac is their binding floor (HBM or ALU) over their time"}
 

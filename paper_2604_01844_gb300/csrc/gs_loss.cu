@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "gs_internal.cuh"
+#include "gs_tma.cuh"
 
 namespace gs {
 namespace {
@@ -255,8 +256,9 @@ __global__ void __launch_bounds__(kThreads)
 
 // xy filtering and completion of a tile of one slice (an image of a 2D batch or a z-plane of a
 // volume; slice = blockIdx.z, nx x ny elements, channels cstride elements apart).
-//   MODE 0  2D forward: X, Y -> moments (x, y), (x^2, y^2) and x y -> SSIM, maps, loss (plus
-//           l1g * sum |x - y| over the tile when fused with an L1 term)
+//   MODE 0  2D forward: X, Y -> moments (x, y) and (x^2 + y^2, x y) -> SSIM, maps, loss (plus
+//           l1g * sum |x - y| over the tile when fused with an L1 term); SSIM needs the second
+//           moments of x and y only through sigma_x^2 + sigma_y^2
 //   MODE 1  3D forward: the five z-filtered moments -> SSIM, maps, loss
 //   MODE 2  backward (2D, or 3D after the z pass): maps m1, m2, m3 (filtered in z for 3D)
 //           -> dL/dx = w * m1 + 2 x (w * m2) + y (w * m3) (+ l1g sign(x - y) when fused
@@ -268,7 +270,8 @@ struct XyShape {
   static constexpr int NPI = MODE == 1 ? 2 : 1;  // staged channel pairs
   static constexpr int NSI = MODE == 0 ? 0 : 1;  // staged single channels
   static constexpr int NPO = MODE == 2 ? 1 : 2;  // filtered pairs
-  static constexpr int NSO = 1;                  // filtered singles
+  static constexpr int NSO = MODE == 0 ? 0 : 1;  // filtered singles
+  static constexpr int NSOA = NSO ? NSO : 1;     // their array extent
   // shared memory: rows of odd stride (in elements), so that a warp reading 32 consecutive
   // rows of one column hits distinct banks
   static constexpr size_t in2 = (size_t)NPI * kIn2 * (kIn2 + 1) * sizeof(float2);
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(kSsimThreads)
   for (int p = tid; p < kIn2 * (kT2 / kG); p += kSsimThreads) {
     const int r = p % kIn2, c0 = (p / kIn2) * kG;
     float2 a2[NPO][kG];
-    float a1[NSO][kG];
+    float a1[S::NSOA][kG];
 #pragma unroll
     for (int j = 0; j < kG; ++j) {
 #pragma unroll
@@ -352,12 +355,12 @@ __global__ void __launch_bounds__(kSsimThreads)
 #pragma unroll
     for (int i = 0; i < kG + 2 * kR; ++i) {
       float2 u2[NPO];
-      float u1[NSO];
+      float u1[S::NSOA];
       if (MODE == 0) {
         const float2 xy = in2[0][r][c0 + i];
         u2[0] = xy;
-        u2[NPO - 1] = __fmul2_rn(xy, xy);
-        u1[0] = xy.x * xy.y;
+        // second moments as (x^2 + y^2, x y): SSIM needs sigma_x^2 + sigma_y^2 only
+        u2[NPO - 1] = make_float2(fmaf(xy.x, xy.x, xy.y * xy.y), xy.x * xy.y);
       } else {
 #pragma unroll
         for (int m = 0; m < NPO; ++m) u2[m] = in2[m][r][c0 + i];
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kSsimThreads)
   // ---- vertical pass: column tx, rows ty0 .. ty0 + 3
   const int tx = tid % kT2, ty0 = (tid / kT2) * kG;
   float2 f2[NPO][kG];
-  float f1[NSO][kG];
+  float f1[S::NSOA][kG];
 #pragma unroll
   for (int j = 0; j < kG; ++j) {
 #pragma unroll
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(kSsimThreads)
 #pragma unroll
   for (int i = 0; i < kG + 2 * kR; ++i) {
     float2 u2[NPO];
-    float u1[NSO];
+    float u1[S::NSOA];
 #pragma unroll
     for (int m = 0; m < NPO; ++m) u2[m] = h2[m][ty0 + i][tx];
 #pragma unroll
@@ -431,10 +434,17 @@ __global__ void __launch_bounds__(kSsimThreads)
       grad[o] = accumulate ? grad[o] + g : g;
     } else {
       const float mx = f2[0][j].x, my = f2[0][j].y;
-      const float sxx = f2[NPO - 1][j].x - mx * mx, syy = f2[NPO - 1][j].y - my * my;
-      const float sxy = f1[0][j] - mx * my;
+      float sxy, D;  // sigma_xy and sigma_x^2 + sigma_y^2 + C2
+      if (MODE == 0) {  // filtered (x^2 + y^2, x y)
+        sxy = f2[1][j].y - mx * my;
+        D = (f2[1][j].x - mx * mx - my * my) + C2;
+      } else {  // filtered (x^2, y^2) and x y
+        const float sxx = f2[NPO - 1][j].x - mx * mx, syy = f2[NPO - 1][j].y - my * my;
+        sxy = f1[0][j] - mx * my;
+        D = sxx + syy + C2;
+      }
       const float Am = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
-      const float C = mx * mx + my * my + C1, D = sxx + syy + C2;
+      const float C = mx * mx + my * my + C1;
       const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
       const float Sv = (Am * Bn) * inv;
       const float dmu = (2.f * my * Bn) * inv - Sv * (2.f * mx) * (D * inv);
@@ -457,6 +467,408 @@ int ssim_xy_attributes() {
                                              (int)XyShape<1>::smem);
   if (e != cudaSuccess) {
     set_last_error("ssim_xy attributes", e);
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// SSIM 3D, fused: one kernel for the forward (X, Y -> SSIM, loss and the three derivative
+// maps) and one for the backward (maps -> dL/dX), each streaming its volume along z once.
+// A CTA owns a 32 x 8 tile of (x, y) columns (a thread per column; two CTAs per SM) and a
+// range of z.  Per input plane it
+//   1. receives the plane's 48 x 18 box of every input channel by TMA, four planes in flight
+//      (zero fill outside the volume; the box starts 8 columns left of the tile, so that its x
+//      coordinate stays 16-byte aligned, and 5 rows above it),
+//   2. filters the box along y: items of one halo column and two output rows share the 12
+//      inputs they need (register blocking), results in shared memory as one float4 of
+//      channels per column,
+//   3. filters along x for its own column, which leaves the thread the plane's xy-filtered
+//      channels of its column,
+//   4. keeps them in a register ring of the last 12 planes and, once 11 planes are in,
+//      filters along z for the plane 5 behind and completes that voxel: SSIM, the loss term
+//      and the maps in the forward, the gradient in the backward.
+// Planes go through these steps in pairs (six planes in flight), so that each barrier covers
+// two planes and every thread has two independent chains of work in each step.
+// The forward filters four channels, x, y, x^2 + y^2 and x y: SSIM depends on the second
+// moments of x and y only through sigma_x^2 + sigma_y^2.  The backward filters the maps m1,
+// m2, m3; its stage also brings the tile's X and Y at the output plane.  The ring slots of
+// each pair are fixed at compile time by a switch over the 6 pair positions, so the ring stays
+// in registers without unrolling the whole loop.  Filtering is zero-padded 'same' in all three
+// directions, as in the separable kernels above (the y, x, z
+// order and the summed channel only change FP32 rounding).  Traffic: forward X, Y in and three
+// maps out (20 bytes per voxel); backward the maps, X and Y in and the gradient out (24).
+// ------------------------------------------------------------------------------------------
+constexpr int kFX = 32, kFY = 8;                       // output tile (x, y)
+constexpr int kFThreads = kFX * kFY;                   // a thread per column
+constexpr int kBoxX = kFX + 16, kBoxY = kFY + 2 * kR;  // staged box 48 x 18
+constexpr int kHaloX = kFX + 2 * kR;                   // 42 y-filtered columns
+constexpr int kFStages = 6;                            // planes in flight (3 pairs)
+constexpr int kYItems = kHaloX * (kFY / 2);            // 168 y-pass items
+constexpr uint32_t kBox4 = kBoxX * kBoxY * 4;          // bytes of a 4-byte channel box (3456)
+constexpr uint32_t kBox8 = 2 * kBox4;                  // of an 8-byte (pair) box
+constexpr uint32_t kTile4 = kFX * kFY * 4;             // of a 4-byte output tile (1024)
+static_assert(kBox4 % 128 == 0 && kTile4 % 128 == 0, "TMA destinations stay 128-byte aligned");
+static_assert(kFY % 2 == 0 && kFThreads % 32 == 0, "y items take row pairs; whole warps");
+
+// Stage layout and filtered channels of the two directions.
+//   forward (BWD = false): X box | Y box; NP = 2 filtered pairs (x, y), (x^2 + y^2, x y)
+//   backward (BWD = true): (m1, m2) box | m3 box | X tile | Y tile; NP = 1 pair + 1 single
+template <bool BWD>
+struct FusedShape {
+  static constexpr int NP = BWD ? 1 : 2, NS = BWD ? 1 : 0;
+  static constexpr uint32_t offB = BWD ? kBox8 : kBox4;
+  static constexpr uint32_t offX = kBox8 + kBox4, offY = offX + kTile4;  // backward only
+  static constexpr uint32_t stage = BWD ? offY + kTile4 : 2 * kBox4;
+  static constexpr uint32_t txbytes = BWD ? kBox8 + kBox4 + 2 * kTile4 : 2 * kBox4;
+  static constexpr uint32_t hbuf = sizeof(float4) * kFY * kHaloX;  // y-filtered channels
+  static constexpr size_t smem = 128 + kFStages * stage + 4 * hbuf;  // h: 2 planes x 2
+};
+
+// The ring holds the last 12 planes' xy-filtered channels; planes arrive in pairs, the pair
+// of iteration i in slots 2K and 2K + 1 (K = i % 6).  The z filter of the pair's first plane
+// reads the 11 slots ending at 2K, that of the second the 11 ending at 2K + 1.
+constexpr int kRing = 12;
+template <int K, int NP, int NS>
+__device__ __forceinline__ void ring_z2(float2 (&rp)[NP][kRing], float (&rs)[NS ? NS : 1][kRing],
+                                        const float2 (&vp)[2][NP],
+                                        const float (&vs)[2][NS ? NS : 1],
+                                        const float2 (&w2)[2 * kR + 1], float2 (&fp)[2][NP],
+                                        float (&fs)[2][NS ? NS : 1]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      rp[m][2 * K + h] = vp[h][m];
+      fp[h][m] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      rs[m][2 * K + h] = vs[h][m];
+      fs[h][m] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int t = 0; t <= 2 * kR; ++t) {
+      const int sl = (2 * K + h + kRing - 2 * kR + t) % kRing;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) fp[h][m] = __ffma2_rn(w2[t], rp[m][sl], fp[h][m]);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) fs[h][m] = fmaf(w2[t].x, rs[m][sl], fs[h][m]);
+    }
+}
+
+template <int NP, int NS>
+__device__ __forceinline__ void ring_push2(int k, float2 (&rp)[NP][kRing],
+                                           float (&rs)[NS ? NS : 1][kRing],
+                                           const float2 (&vp)[2][NP],
+                                           const float (&vs)[2][NS ? NS : 1],
+                                           const float2 (&w2)[2 * kR + 1], float2 (&fp)[2][NP],
+                                           float (&fs)[2][NS ? NS : 1]) {
+  switch (k) {
+    case 0: ring_z2<0, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 1: ring_z2<1, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 2: ring_z2<2, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 3: ring_z2<3, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 4: ring_z2<4, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    default: ring_z2<5, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+  }
+}
+
+// Shared streaming skeleton: two input planes per iteration (twice the independent work
+// between barriers).  `on_stage(sb, p, h)` reads what the thread needs from plane p's stage
+// (h = p % 2) before the stage is released; `finish(z, h, fp, fs)` completes the voxel of the
+// thread's column at output plane z = z0 + p - 10.  Returns false if a TMA wait timed out: every thread then leaves the loop
+// at the same iteration, and the copies still in flight have been waited for.
+template <bool BWD, typename Finish, typename OnStage>
+__device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                             const CUtensorMap* tmX, const CUtensorMap* tmY,
+                                             const Win& W, int z0, int z1, Finish finish,
+                                             OnStage on_stage) {
+  using S = FusedShape<BWD>;
+  constexpr int NP = S::NP, NS = S::NS, NSA = NS ? NS : 1;
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  // 128-byte aligned start, derived from the shared array itself (shared-space addressing)
+  unsigned char* base = dyn_raw + ((128u - (smem_u32(dyn_raw) & 127u)) & 127u);
+  float4* h4 = reinterpret_cast<float4*>(base + kFStages * S::stage);  // [2][2][kFY][kHaloX]
+  __shared__ __align__(8) uint64_t bar[kFStages];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int bx0 = blockIdx.x * kFX, by0 = blockIdx.y * kFY;
+  // planes p = 0 .. 2 * iters - 1 enter at z = z0 - kR + p (one past the range if odd)
+  const int planes = (z1 - z0) + 2 * kR, iters = (planes + 1) / 2, total = 2 * iters;
+  int issued = 0;
+  auto issue = [&](int p) {
+    const int st = p % kFStages;
+    unsigned char* dst = base + st * S::stage;
+    const int zi = z0 - kR + p;
+    mbar_expect_tx(&bar[st], S::txbytes);
+    tma_load_3d(tmA, &bar[st], dst, bx0 - 8, by0 - kR, zi);
+    tma_load_3d(tmB, &bar[st], dst + S::offB, bx0 - 8, by0 - kR, zi);
+    if constexpr (BWD) {  // the output plane's X and Y tiles
+      tma_load_3d(tmX, &bar[st], dst + S::offX, bx0, by0, zi - kR);
+      tma_load_3d(tmY, &bar[st], dst + S::offY, bx0, by0, zi - kR);
+    }
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < kFStages; ++st) mbar_init(&bar[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (; issued < kFStages && issued < total; ++issued) issue(issued);
+  }
+  __syncthreads();
+  float2 w2[2 * kR + 1];
+#pragma unroll
+  for (int t = 0; t <= 2 * kR; ++t) w2[t] = make_float2(W.w[t], W.w[t]);
+  float2 rp[NP][kRing];
+  float rs[NSA][kRing];
+#pragma unroll
+  for (int t = 0; t < kRing; ++t) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) rp[m][t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < NSA; ++m) rs[m][t] = 0.f;
+  }
+  int k = 0;  // ring pair position of iteration i: i % 6
+  bool failed = false;
+  for (int i = 0; i < iters; ++i) {
+    const int p0 = 2 * i;
+    // a wait that gives up raises the flag; the planes are still walked (on whatever the
+    // buffers hold) so that every thread reaches the barrier, after which all leave together
+    if (!mbar_wait(&bar[p0 % kFStages], (uint32_t)(p0 / kFStages) & 1u)) abort_flag = 1;
+    if (!mbar_wait(&bar[(p0 + 1) % kFStages], (uint32_t)((p0 + 1) / kFStages) & 1u))
+      abort_flag = 1;
+    float4* hb = h4 + (i & 1) * 2 * kFY * kHaloX;
+    // ---- y pass of both planes: item (halo column c, output rows 2j and 2j + 1), inputs at
+    // box column c + 3
+    if (tid < kYItems) {
+      const int c = tid % kHaloX, j = tid / kHaloX;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned char* sb = base + ((p0 + h) % kFStages) * S::stage;
+        float2 a0[NP], a1[NP];
+        float c0 = 0.f, c1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) a0[m] = a1[m] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r <= 2 * kR + 1; ++r) {
+          const int e = (2 * j + r) * kBoxX + c + 3;
+          float2 u[NP];
+          float us = 0.f;
+          if constexpr (!BWD) {  // X, Y -> (x, y), (x^2 + y^2, x y)
+            const float xv = reinterpret_cast<const float*>(sb)[e];
+            const float yv = reinterpret_cast<const float*>(sb + S::offB)[e];
+            u[0] = make_float2(xv, yv);
+            u[NP - 1] = make_float2(fmaf(xv, xv, yv * yv), xv * yv);
+          } else {  // (m1, m2), m3
+            u[0] = reinterpret_cast<const float2*>(sb)[e];
+            us = reinterpret_cast<const float*>(sb + S::offB)[e];
+          }
+          if (r <= 2 * kR) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) a0[m] = __ffma2_rn(w2[r], u[m], a0[m]);
+            if (NS) c0 = fmaf(w2[r].x, us, c0);
+          }
+          if (r >= 1) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) a1[m] = __ffma2_rn(w2[r - 1], u[m], a1[m]);
+            if (NS) c1 = fmaf(w2[r - 1].x, us, c1);
+          }
+        }
+        // channels of a column as one float4: forward (x, y, x^2 + y^2, x y), backward
+        // (m1, m2, m3, unused)
+        float4* hh = hb + h * kFY * kHaloX;
+        if constexpr (NP == 2) {
+          hh[(2 * j) * kHaloX + c] = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
+          hh[(2 * j + 1) * kHaloX + c] = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
+        } else {
+          hh[(2 * j) * kHaloX + c] = make_float4(a0[0].x, a0[0].y, c0, 0.f);
+          hh[(2 * j + 1) * kHaloX + c] = make_float4(a1[0].x, a1[0].y, c1, 0.f);
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) on_stage(base + ((p0 + h) % kFStages) * S::stage, p0 + h, h);
+    __syncthreads();
+    if (abort_flag) {
+      failed = true;
+      break;
+    }
+    if (tid == 0)  // refill the two stages just read
+      for (int n = 0; n < 2 && issued < total; ++n) issue(issued++);
+    // ---- x pass of both planes for the thread's column
+    float2 vp[2][NP];
+    float vs[2][NSA];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int m = 0; m < NP; ++m) vp[h][m] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < NSA; ++m) vs[h][m] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t <= 2 * kR; ++t) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 q = hb[(h * kFY + ty) * kHaloX + tx + t];
+        vp[h][0] = __ffma2_rn(w2[t], make_float2(q.x, q.y), vp[h][0]);
+        if constexpr (NP == 2)
+          vp[h][NP - 1] = __ffma2_rn(w2[t], make_float2(q.z, q.w), vp[h][NP - 1]);
+        else
+          vs[h][0] = fmaf(w2[t].x, q.z, vs[h][0]);
+      }
+    }
+    // ---- ring, z filter, completion of output planes z0 + p0 - 2 kR and the next
+    float2 fp[2][NP];
+    float fs[2][NSA];
+    ring_push2<NP, NS>(k, rp, rs, vp, vs, w2, fp, fs);
+    k = k == kRing / 2 - 1 ? 0 : k + 1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int z = z0 + p0 + h - 2 * kR;
+      if (z >= z0 && z < z1) finish(z, h, fp[h], fs[h]);
+    }
+  }
+  if (failed && tid == 0) {
+    // wait (bounded) for the copies still in flight before the CTA's shared memory goes away
+    for (int j = issued - kFStages; j < issued; ++j)
+      if (j >= 0) mbar_wait(&bar[j % kFStages], (uint32_t)(j / kFStages) & 1u);
+  }
+  return !failed;
+}
+
+template <bool MAPS>
+__global__ void __launch_bounds__(kFThreads, 2)
+    k_ssim3d_fwd_fused(const __grid_constant__ CUtensorMap tmX,
+                       const __grid_constant__ CUtensorMap tmY, const __grid_constant__ Win W,
+                       int nx, int ny, int nz, int zc, float C1, float C2, float gscale,
+                       float l1s, float* __restrict__ loss, float2* __restrict__ m12,
+                       float* __restrict__ m3, int* __restrict__ err) {
+  const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x = blockIdx.x * kFX + tx, y = blockIdx.y * kFY + ty;
+  const bool own = x < nx && y < ny;
+  float contrib = 0.f, l1 = 0.f;
+  auto finish = [&](int z, int, const float2 (&fp)[2], const float (&)[1]) {
+    if (!own) return;
+    const float mx = fp[0].x, my = fp[0].y;
+    const float sxy = fp[1].y - mx * my;
+    const float Am = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
+    const float C = mx * mx + my * my + C1;
+    const float D = (fp[1].x - mx * mx - my * my) + C2;  // sigma_x^2 + sigma_y^2 + C2
+    const float inv = 1.f / (C * D);
+    const float Sv = (Am * Bn) * inv;
+    contrib += 1.f - Sv;
+    if (MAPS) {
+      const float dmu = (2.f * my * Bn) * inv - Sv * (2.f * mx) * (D * inv);
+      const float dsxx = -Sv * (C * inv);
+      const float dsxy = 2.f * Am * inv;
+      const size_t o = ((size_t)z * ny + y) * nx + x;
+      m12[o] = make_float2(gscale * (dmu - 2.f * mx * dsxx - my * dsxy), gscale * dsxx);
+      m3[o] = gscale * dsxy;
+    }
+  };
+  auto on_stage = [&](const unsigned char* sb, int p, int) {
+    // the L1 term: |X - Y| of the thread's own voxel of the staged plane (zero outside)
+    if (l1s != 0.f && own) {
+      const int e = (ty + kR) * kBoxX + tx + 8;
+      const int zi = z0 - kR + p;
+      if (zi >= z0 && zi < z1)
+        l1 += fabsf(reinterpret_cast<const float*>(sb)[e] -
+                    reinterpret_cast<const float*>(sb + kBox4)[e]);
+    }
+  };
+  const bool ok = fused_stream<false>(&tmX, &tmY, nullptr, nullptr, W, z0, z1, finish, on_stage);
+  if (!ok) {  // a tile copy never arrived: report it and poison the loss
+    if (threadIdx.x == 0) {
+      atomicExch(err, GS_ERR_TIMEOUT);
+      if (loss) atomicExch(loss, __int_as_float(0x7fc00000));
+    }
+    return;
+  }
+  if (loss) block_add(contrib * (-gscale) + l1 * l1s, loss);
+}
+
+__global__ void __launch_bounds__(kFThreads, 2)
+    k_ssim3d_bwd_fused(const __grid_constant__ CUtensorMap tmM12,
+                       const __grid_constant__ CUtensorMap tmM3,
+                       const __grid_constant__ CUtensorMap tmXt,
+                       const __grid_constant__ CUtensorMap tmYt, const __grid_constant__ Win W,
+                       int nx, int ny, int nz, int zc, float* __restrict__ grad, int accumulate,
+                       float l1g, int* __restrict__ err) {
+  using S = FusedShape<true>;
+  const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x = blockIdx.x * kFX + tx, y = blockIdx.y * kFY + ty;
+  const bool own = x < nx && y < ny;
+  float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f};  // X, Y of the two voxels finished next
+  auto on_stage = [&](const unsigned char* sb, int, int h) {
+    xv[h] = reinterpret_cast<const float*>(sb + S::offX)[ty * kFX + tx];
+    yv[h] = reinterpret_cast<const float*>(sb + S::offY)[ty * kFX + tx];
+  };
+  auto finish = [&](int z, int h, const float2 (&fp)[1], const float (&fs)[1]) {
+    if (!own) return;
+    const size_t o = ((size_t)z * ny + y) * nx + x;
+    const float xh = xv[h], yh = yv[h];
+    float g = fp[0].x + 2.f * xh * fp[0].y + yh * fs[0];
+    if (l1g != 0.f) g = l1g * sgnf(xh - yh) + g;  // fused L1 term
+    grad[o] = accumulate ? grad[o] + g : g;
+  };
+  const bool ok = fused_stream<true>(&tmM12, &tmM3, &tmXt, &tmYt, W, z0, z1, finish, on_stage);
+  if (!ok) {  // a tile copy never arrived: report it and poison the tile's gradient
+    if (threadIdx.x == 0) atomicExch(err, GS_ERR_TIMEOUT);
+    if (own)
+      for (int z = z0; z < z1; ++z) grad[((size_t)z * ny + y) * nx + x] = __int_as_float(0x7fc00000);
+  }
+}
+
+// 3D tensor map over an nx x ny x nz volume of elem-byte elements (elem 4: FP32, 8: FP32
+// pairs), box bx x by x 1, zero fill outside
+int volume_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int elem, int bx,
+               int by) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_last_error_msg("cuTensorMapEncodeTiled is not available");
+    return GS_ERR_CUDA;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * elem, (cuuint64_t)nx * ny * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r =
+      fn(map, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error_msg("cuTensorMapEncodeTiled failed for a 3D SSIM volume");
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}
+
+// Whether the fused 3D SSIM applies: TMA wants 16-byte aligned bases and row strides (nx a
+// multiple of 4), and the volume at least one box wide and high.
+bool ssim3d_fused_ok(const void* a, const void* b, int nx, int ny) {
+  return nx % 4 == 0 && nx >= kBoxX && ny >= kBoxY && ((uintptr_t)a & 15u) == 0 &&
+         ((uintptr_t)b & 15u) == 0;
+}
+
+int ssim3d_fused_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_ssim3d_fwd_fused<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)FusedShape<false>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ssim3d_fwd_fused<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FusedShape<false>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ssim3d_bwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FusedShape<true>::smem);
+  if (e != cudaSuccess) {
+    set_last_error("ssim3d fused attributes", e);
     return GS_ERR_CUDA;
   }
   return GS_OK;
@@ -762,6 +1174,37 @@ int ssim3d(const float* d_x, const float* d_y, int nx, int ny, int nz, float dat
   const int64_t cols = (int64_t)nx * ny;
   const dim3 gz((unsigned)((cols + kThreads - 1) / kThreads)), bz(kThreads);
   const float l1s = l1_weight / (float)plane;
+  if (ssim3d_fused_ok(d_x, d_y, nx, ny)) {
+    // fused streaming kernels; tmp's first word is the TMA timeout status
+    int* err = (int*)tmp;
+    CUtensorMap tmX, tmY;
+    GS_TRY(volume_map(&tmX, d_x, nx, ny, nz, 4, kBoxX, kBoxY));
+    GS_TRY(volume_map(&tmY, d_y, nx, ny, nz, 4, kBoxX, kBoxY));
+    GS_TRY(ssim3d_fused_attributes());
+    // z chunks so that the grid fills the SMs (two CTAs each) about twice; at least 32
+    // planes per chunk
+    const int tiles = ((nx + kFX - 1) / kFX) * ((ny + kFY - 1) / kFY);
+    const int want = (4 * num_sms() + tiles - 1) / tiles;
+    const int nch = std::max(1, std::min(want, nz / 32));
+    const int zc = (nz + nch - 1) / nch;
+    const dim3 gf((nx + kFX - 1) / kFX, (ny + kFY - 1) / kFY, (nz + zc - 1) / zc);
+    float2* m12 = reinterpret_cast<float2*>(maps);
+    float* m3 = maps + 2 * plane;
+    if (!d_grad)
+      return launch("ssim3d_fwd", k_ssim3d_fwd_fused<false>, gf, dim3(kFThreads),
+                    FusedShape<false>::smem, s, tmX, tmY, W, nx, ny, nz, zc, C1, C2, gscale,
+                    l1s, d_loss, m12, m3, err);
+    GS_TRY(launch("ssim3d_fwd", k_ssim3d_fwd_fused<true>, gf, dim3(kFThreads),
+                  FusedShape<false>::smem, s, tmX, tmY, W, nx, ny, nz, zc, C1, C2, gscale, l1s,
+                  d_loss, m12, m3, err));
+    CUtensorMap tmM12, tmM3, tmXt, tmYt;
+    GS_TRY(volume_map(&tmM12, m12, nx, ny, nz, 8, kBoxX, kBoxY));
+    GS_TRY(volume_map(&tmM3, m3, nx, ny, nz, 4, kBoxX, kBoxY));
+    GS_TRY(volume_map(&tmXt, d_x, nx, ny, nz, 4, kFX, kFY));
+    GS_TRY(volume_map(&tmYt, d_y, nx, ny, nz, 4, kFX, kFY));
+    return launch("ssim3d_bwd", k_ssim3d_bwd_fused, gf, dim3(kFThreads), FusedShape<true>::smem,
+                  s, tmM12, tmM3, tmXt, tmYt, W, nx, ny, nz, zc, d_grad, accumulate, l1s, err);
+  }
   GS_TRY(launch("ssim3d_z_fwd", k_ssim3d_z<2>, gz, bz, 0, s, W, d_x, d_y, nx, ny, nz, plane,
                 tmp, l1s, d_loss));
   GS_TRY(launch("ssim3d_xy_fwd", k_ssim_xy<1>, gxy, bxy, XyShape<1>::smem, s, W,

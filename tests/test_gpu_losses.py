@@ -131,6 +131,38 @@ def test_ssim3d(B, shape):
     assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
 
 
+@pytest.mark.parametrize("shape", [(37, 45, 52), (70, 26, 48), (16, 33, 96)])
+def test_ssim3d_streaming(B, shape):
+    """Volumes the fused streaming kernels take (x a multiple of 4, at least 48 x 26 columns):
+    several 32 x 16 column tiles with ragged edges, z in one or more chunks (70 planes run as
+    two chunks of 35), against the FP64 oracle; then accumulation onto a non-zero gradient and
+    the value-only call."""
+    rng = np.random.default_rng(5)
+    y = _x32(rng.random(shape))
+    x = _x32(np.clip(y + 0.1 * rng.standard_normal(shape), 0, None))
+    L = float(y.max())
+    val, g = _run_loss(B, "ssim3d", x, y, L, weight=0.5)
+    want, gw = OL.value_and_grad(lambda a, b: 0.5 * (1 - OL.ssim3d(a, b, L)), x, y)
+    assert abs(val - want) <= 2e-5 * max(1.0, abs(want)), (val, want)
+    scale = np.abs(gw).max()
+    assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
+    base = _x32(rng.standard_normal(shape))
+    val2, g2 = _run_loss(B, "ssim3d", x, y, L, weight=0.5, accumulate_into=base)
+    assert abs(val2 - val) <= 1e-6 * abs(val)  # block sums meet in atomic order
+    assert np.abs(g2 - (gw + base)).max() <= 1e-3 * scale + 1e-6 * np.abs(base).max()
+    # value only: no gradient pointer
+    Lb = B.lib()
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    yd = torch.from_numpy(y.astype(np.float32)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(Lb.gs_ssim3d_workspace_size(xd.numel()), dtype=torch.uint8, device="cuda")
+    dz, dy, dx = shape
+    B.check(Lb.gs_ssim3d_loss(B.ptr(xd), B.ptr(yd), dx, dy, dz, L, 0.5, B.ptr(loss), None, 0,
+                              B.ptr(ws), ws.numel(), _s()), "ssim3d value")
+    torch.cuda.synchronize()
+    assert abs(float(loss.item()) - val) <= 1e-6 * abs(val)
+
+
 def test_adam_matches_oracle(B):
     rng = np.random.default_rng(4)
     n = 1000
