@@ -481,8 +481,8 @@ int ssim_xy_attributes() {
 //      (zero fill outside the volume; the box starts 8 columns left of the tile, so that its x
 //      coordinate stays 16-byte aligned, and 5 rows above it),
 //   2. filters the box along y: items of one halo column and two output rows share the 12
-//      inputs they need (register blocking), results in shared memory as one float4 of
-//      channels per column,
+//      inputs they need (register blocking), results in shared memory (forward one float4
+//      of channels per column, backward a float2 and a float),
 //   3. filters along x for its own column, which leaves the thread the plane's xy-filtered
 //      channels of its column,
 //   4. keeps them in a register ring of the last 12 planes and, once 11 planes are in,
@@ -521,7 +521,9 @@ struct FusedShape {
   static constexpr uint32_t offX = kBox8 + kBox4, offY = offX + kTile4;  // backward only
   static constexpr uint32_t stage = BWD ? offY + kTile4 : 2 * kBox4;
   static constexpr uint32_t txbytes = BWD ? kBox8 + kBox4 + 2 * kTile4 : 2 * kBox4;
-  static constexpr uint32_t hbuf = sizeof(float4) * kFY * kHaloX;  // y-filtered channels
+  // y-filtered channels of one plane: forward one float4 per column, backward a float2 plane
+  // (m1, m2) and a float plane (m3)
+  static constexpr uint32_t hbuf = (BWD ? 12 : 16) * kFY * kHaloX;
   static constexpr size_t smem = 128 + kFStages * stage + 4 * hbuf;  // h: 2 planes x 2
 };
 
@@ -592,7 +594,11 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   // 128-byte aligned start, derived from the shared array itself (shared-space addressing)
   unsigned char* base = dyn_raw + ((128u - (smem_u32(dyn_raw) & 127u)) & 127u);
-  float4* h4 = reinterpret_cast<float4*>(base + kFStages * S::stage);  // [2][2][kFY][kHaloX]
+  // y-filtered planes [2 buffers][2 planes][kFY][kHaloX]: forward float4; backward float2
+  // (m1, m2), then float m3
+  float4* h4 = reinterpret_cast<float4*>(base + kFStages * S::stage);
+  float2* h2 = reinterpret_cast<float2*>(base + kFStages * S::stage);
+  float* h1 = reinterpret_cast<float*>(h2 + 4 * kFY * kHaloX);
   __shared__ __align__(8) uint64_t bar[kFStages];
   __shared__ int abort_flag;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -640,7 +646,7 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
     if (!mbar_wait(&bar[p0 % kFStages], (uint32_t)(p0 / kFStages) & 1u)) abort_flag = 1;
     if (!mbar_wait(&bar[(p0 + 1) % kFStages], (uint32_t)((p0 + 1) / kFStages) & 1u))
       abort_flag = 1;
-    float4* hb = h4 + (i & 1) * 2 * kFY * kHaloX;
+    const int hoff = (i & 1) * 2 * kFY * kHaloX;  // this iteration's buffer
     // ---- y pass of both planes: item (halo column c, output rows 2j and 2j + 1), inputs at
     // box column c + 3
     if (tid < kYItems) {
@@ -677,15 +683,15 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
             if (NS) c1 = fmaf(w2[r - 1].x, us, c1);
           }
         }
-        // channels of a column as one float4: forward (x, y, x^2 + y^2, x y), backward
-        // (m1, m2, m3, unused)
-        float4* hh = hb + h * kFY * kHaloX;
-        if constexpr (NP == 2) {
-          hh[(2 * j) * kHaloX + c] = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
-          hh[(2 * j + 1) * kHaloX + c] = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
+        const int o0 = hoff + (h * kFY + 2 * j) * kHaloX + c, o1 = o0 + kHaloX;
+        if constexpr (NP == 2) {  // (x, y, x^2 + y^2, x y) of a column as one float4
+          h4[o0] = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
+          h4[o1] = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
         } else {
-          hh[(2 * j) * kHaloX + c] = make_float4(a0[0].x, a0[0].y, c0, 0.f);
-          hh[(2 * j + 1) * kHaloX + c] = make_float4(a1[0].x, a1[0].y, c1, 0.f);
+          h2[o0] = a0[0];
+          h2[o1] = a1[0];
+          h1[o0] = c0;
+          h1[o1] = c1;
         }
       }
     }
@@ -712,12 +718,15 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
     for (int t = 0; t <= 2 * kR; ++t) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float4 q = hb[(h * kFY + ty) * kHaloX + tx + t];
-        vp[h][0] = __ffma2_rn(w2[t], make_float2(q.x, q.y), vp[h][0]);
-        if constexpr (NP == 2)
+        const int o = hoff + (h * kFY + ty) * kHaloX + tx + t;
+        if constexpr (NP == 2) {
+          const float4 q = h4[o];
+          vp[h][0] = __ffma2_rn(w2[t], make_float2(q.x, q.y), vp[h][0]);
           vp[h][NP - 1] = __ffma2_rn(w2[t], make_float2(q.z, q.w), vp[h][NP - 1]);
-        else
-          vs[h][0] = fmaf(w2[t].x, q.z, vs[h][0]);
+        } else {
+          vp[h][0] = __ffma2_rn(w2[t], h2[o], vp[h][0]);
+          vs[h][0] = fmaf(w2[t].x, h1[o], vs[h][0]);
+        }
       }
     }
     // ---- ring, z filter, completion of output planes z0 + p0 - 2 kR and the next
