@@ -474,6 +474,7 @@ def run_ours(args, ws, rank, local):
             "adaptive_control": lambda: adaptive_control(device),
             "compression": lambda: compression(device),
             "gemm": lambda: gemm_rate(device),
+            "batched_small": lambda: batched_small_step(device),
         }
         chosen = list(legs) if args.extras == "all" else args.extras.split(",")
         for name in chosen:
@@ -644,6 +645,65 @@ def learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=4
                                              best["ms_to_ref"] < out["plain"]["ms_to_ref"])
     out["replans"] = replans  # pair-capacity overflows met by the runs (0: every step complete)
     return out
+
+
+def batched_small_step(device, n_inst=16, seq_steps=20):
+    """Where batching pays: n_inst small reconstructions (volumes 64^3-128^3, 16-32 cone views
+    of 128^2-192^2, 2k-6k Gaussians, FDK-gradient starts), one optimisation step each.  Times
+    the batched step (one rasterizer and voxelizer launch per pass over all instances, the
+    whole step in one CUDA graph) against the same instances stepped one by one, each in its
+    own graph: a single small step leaves most SMs idle between its short launches."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2604_01844_gb300.batch import BatchGraphStep, BatchReconstruction
+    from paper_2604_01844_gb300.recon import (GraphStep, PhantomProblem, ReconConfig,
+                                               Reconstruction, fdk_volume, gradient_init)
+
+    specs = synth.batch_specs(seeds=range(200, 200 + n_inst), sides=(64, 96, 128),
+                              detectors=(128, 160, 192), views=(16, 32), gaussians=(2000, 6000))
+    inst = []
+    for sp in specs:
+        v = synth.cone_views(sp["n_views"], sp["det"], sp["det"])
+        g = synth.cube_grid(sp["side"])
+        prob = PhantomProblem(synth.ellipsoid_phantom(sp["seed"], sp["n_ellipsoids"]), v,
+                              sp["det"], sp["det"], g, device=device)
+        u = np.random.default_rng(sp["seed"]).random((sp["n"], 4)).astype(np.float32)
+        mr, sc, q = gradient_init(fdk_volume(prob, g), g, sp["n"], u)
+        inst.append(dict(views=v, W=sp["det"], H=sp["det"], target=prob.proj, grid=g,
+                         mean_rho=mr.cpu().numpy(), scale=sc.cpu().numpy(),
+                         quat=q.cpu().numpy()))
+    cfg = ReconConfig(**LR_FAST)
+
+    def timed(step):
+        step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(seq_steps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / seq_steps
+
+    rec = BatchReconstruction(inst, cfg=cfg, device=device)
+    batched = timed(BatchGraphStep(rec, warmup=1))
+    del rec
+    one_by_one = 0.0
+    for x in inst:
+        r = Reconstruction(x["views"], x["W"], x["H"], x["target"], x["grid"], x["mean_rho"],
+                           x["scale"], x["quat"], cfg=cfg, device=device)
+        one_by_one += timed(GraphStep(r, warmup=1))
+        del r
+    return {"workload": f"{n_inst} small reconstructions (seeds 200-{199 + n_inst}): volumes "
+                        "64^3-128^3, 16-32 cone views of 128^2-192^2, 2k-6k Gaussians",
+            "views_total": int(sum(sp["n_views"] for sp in specs)),
+            "gaussians_total": int(sum(sp["n"] for sp in specs)),
+            "step_ms_batched_graph": round(batched, 3),
+            "step_ms_one_by_one_graphs": round(one_by_one, 3),
+            "speedup": round(one_by_one / batched, 2)}
 
 
 def batched_learned_vs_plain(device, ref_iters=200, max_iters=400, eval_every=5, n_fit=48,
@@ -1375,7 +1435,8 @@ def main():
     ap.add_argument("--extras", default="all",
                     help="comma-separated study legs to run after the headline step "
                          "(time_to_psnr, learned_init, batched, fit_volume, scale_up, "
-                         "warm_start, adaptive_control, compression, gemm) or 'all'")
+                         "warm_start, adaptive_control, compression, gemm, batched_small) "
+                         "or 'all'")
     ap.add_argument("--fit-side", type=int, default=1024)
     ap.add_argument("--fit-gaussians", type=int, default=500000)
     ap.add_argument("--warm-side", type=int, default=512)
