@@ -381,8 +381,9 @@ int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float
 size_t gs_ssim_workspace_size(int64_t n_elems);
 
 /* Scratch bytes of gs_ssim3d_loss for n_voxels voxels: the 3 derivative maps plus 5 volumes
- * of z-filtered moments (the 3D filter runs as a streaming z pass and an xy pass per plane),
- * each stored as float2 pairs plus one float volume. */
+ * of z-filtered moments, each stored as float2 pairs plus one float volume.  The fused
+ * streaming kernels (see gs_ssim3d_loss) use only the maps and one status word; the moment
+ * volumes serve the separable z + xy passes of the other volumes. */
 size_t gs_ssim3d_workspace_size(int64_t n_voxels);
 
 /* D-SSIM term of Eq. 5: weight * (1 - mean SSIM(x, y)) over n_img images of H x W, SSIM of
@@ -430,7 +431,13 @@ int gs_ssim2d_loss_noalloc(const float* d_x, const float* d_y, int n_img, int H,
  * 11 x 11 x 11 Gaussian window (sigma 1.5), zero-padded, constants as in 2D; gradient w.r.t.
  * x written (accumulate = 0) or added; d_grad = NULL evaluates the value only (d_loss then
  * required).  d_ws: gs_ssim3d_workspace_size(nx ny nz) bytes, else GS_ERR_CAPACITY;
- * nz <= 65535. */
+ * nz <= 65535.
+ * Volumes with nx a multiple of 4, nx >= 48, ny >= 18 and 16-byte aligned d_x, d_y run as two
+ * fused kernels that stream the volume along z once each, with tiles staged by TMA; others run
+ * as separable z and xy passes.  The fused kernels' tile copies are waited for with bounded
+ * waits: a copy that never arrives (a hardware fault, not expected) leaves GS_ERR_TIMEOUT in
+ * the workspace's status word (the int after the maps), a NaN loss and, in the backward, a
+ * NaN gradient over the affected tile, instead of a hung kernel. */
 int gs_ssim3d_loss(const float* d_x, const float* d_y, int nx, int ny, int nz, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);

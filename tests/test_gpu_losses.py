@@ -133,8 +133,8 @@ def test_ssim3d(B, shape):
 
 @pytest.mark.parametrize("shape", [(37, 45, 52), (70, 26, 48), (16, 33, 96)])
 def test_ssim3d_streaming(B, shape):
-    """Volumes the fused streaming kernels take (x a multiple of 4, at least 48 x 26 columns):
-    several 32 x 16 column tiles with ragged edges, z in one or more chunks (70 planes run as
+    """Volumes the fused streaming kernels take (x a multiple of 4, at least 48 x 18 columns):
+    several 32 x 8 column tiles with ragged edges, z in one or more chunks (70 planes run as
     two chunks of 35), against the FP64 oracle; then accumulation onto a non-zero gradient and
     the value-only call."""
     rng = np.random.default_rng(5)
