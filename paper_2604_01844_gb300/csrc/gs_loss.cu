@@ -300,6 +300,20 @@ __global__ void __launch_bounds__(kSsimThreads)
   const int x0 = blockIdx.x * kT2 - kR, y0 = blockIdx.y * kT2 - kR;
   const size_t slice = (size_t)blockIdx.z * nx * ny;
   const int tid = threadIdx.x;
+  // backward: the output pixels' x, y (and the gradient to accumulate onto) are requested
+  // first, so that their latency overlaps the staging instead of following the filter passes
+  float xo[kG], yo[kG], go[kG];
+  if constexpr (MODE == 2) {
+    const int xq = blockIdx.x * kT2 + tid % kT2, yq = blockIdx.y * kT2 + (tid / kT2) * kG;
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const bool in = xq < nx && yq + j < ny;
+      const size_t o = slice + (size_t)(yq + j) * nx + xq;
+      xo[j] = in ? X[o] : 0.f;
+      yo[j] = in ? Y[o] : 0.f;
+      go[j] = in && accumulate ? grad[o] : 0.f;
+    }
+  }
   // ---- stage the halo tile (zero outside the slice); every load before the first store
   {
     constexpr int NC = 2 * NPI + NSI;
@@ -428,10 +442,10 @@ __global__ void __launch_bounds__(kSsimThreads)
       l1 += fabsf(xy.x - xy.y);
     }
     if (MODE == 2) {
-      const float xv = X[o], yv = Y[o];
+      const float xv = xo[j], yv = yo[j];
       float g = f2[0][j].x + 2.f * xv * f2[0][j].y + yv * f1[0][j];
       if (l1g != 0.f) g = l1g * sgnf(xv - yv) + g;  // fused L1 term
-      grad[o] = accumulate ? grad[o] + g : g;
+      grad[o] = accumulate ? go[j] + g : g;
     } else {
       const float mx = f2[0][j].x, my = f2[0][j].y;
       float sxy, D;  // sigma_xy and sigma_x^2 + sigma_y^2 + C2

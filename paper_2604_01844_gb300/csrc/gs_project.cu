@@ -245,8 +245,9 @@ __global__ void __launch_bounds__(kThreads)
   uint32_t cnt = 0;
   if (idx < items) {
     const Inst& I = b.in[inst_of_item(b, idx)];
-    const int64_t local = idx - I.item_off;
-    const int v = (int)(local / I.n), i = (int)(local - (int64_t)v * I.n);
+    // items per instance fit in 32 bits (the plan caps the total below 2^31)
+    const uint32_t local = (uint32_t)(idx - I.item_off);
+    const int v = (int)(local / (uint32_t)I.n), i = (int)(local - (uint32_t)v * (uint32_t)I.n);
     const int gi = I.g_off + i;
     const ViewFrame f = frames[I.v_off + v];
     Fwd o;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kThreads)
   short4 r = make_short4(0, 0, 0, 0);
   if (cnt > 0) {
     const Inst& I = b.in[inst_of_item(b, idx)];
-    const int v = (int)((idx - I.item_off) / I.n);
+    const int v = (int)((uint32_t)(idx - I.item_off) / (uint32_t)I.n);
     r = rect[idx];
     TW = I.TW;
     kbase = (uint32_t)(I.v_off + v) << b.tbits;
