@@ -373,7 +373,8 @@ int gs_l1_loss(const float* d_a, const float* d_b, int64_t n, float weight, floa
 int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* stream);
 
 /* 3D total variation of Eq. 5: weight * (sum of |forward differences| along x, y and z where
- * the neighbour exists) / (nx ny nz), volume [z][y][x]; sub-gradient with sign(0) = 0. */
+ * the neighbour exists) / (nx ny nz), volume [z][y][x]; sub-gradient with sign(0) = 0.
+ * ny nz must stay below 2^31 (GS_ERR_ARG otherwise). */
 int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,
                  float* d_grad, int accumulate, void* stream);
 

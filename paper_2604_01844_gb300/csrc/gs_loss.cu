@@ -86,12 +86,13 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_tv3d(const float* __restrict__ v, int nx, int ny, int nz, float scale,
            float* __restrict__ loss, float* __restrict__ grad, int accumulate) {
-  // blocks stride over the (y, z) rows, threads over x: one index division per row
-  const int64_t rows = (int64_t)ny * nz;
+  // blocks stride over the (y, z) rows, threads over x: one 32-bit index division per row
+  // (the entry point keeps ny nz below 2^31)
+  const uint32_t rows = (uint32_t)ny * (uint32_t)nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny;
   float s = 0.f;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int y = (int)(row % ny), z = (int)(row / ny);
+  for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int z = (int)(row / (uint32_t)ny), y = (int)(row - (uint32_t)z * (uint32_t)ny);
     const int64_t r0 = row * nx;
     for (int x = threadIdx.x; x < nx; x += kThreads) {
       const int64_t i = r0 + x;
@@ -1063,6 +1064,7 @@ int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float
   if (!d_vol || nx < 1 || ny < 1 || nz < 1) return GS_ERR_ARG;
   const int64_t total = (int64_t)nx * ny * nz;
   const int64_t rows = (int64_t)ny * nz;
+  if (rows >= ((int64_t)1 << 31)) return GS_ERR_ARG;
   const int blocks = (int)std::min<int64_t>(rows, 8 * (int64_t)num_sms());
   return launch("tv3d_loss", k_tv3d, dim3(blocks), dim3(kThreads), 0,
                 (cudaStream_t)stream, d_vol, nx, ny, nz, weight / (float)total, d_loss, d_grad,
