@@ -1231,13 +1231,14 @@ def fit_volume_rate(device, side=1024, n=500000, iters=4, warmup=2):
             hbm_roofs[k] = {"bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),
                             "peak_gbs": hbm, "frac": round(gbs / hbm, 3)}
     # the fused 3D SSIM kernels are bound by shared memory, not HBM: per output voxel they move
-    # the TMA-staged boxes in, the y pass's loads and stores and the x pass's 11 float4 loads
-    # (forward 287 B, backward 304 B) through the SM's 128 B/clock shared-memory pipe
+    # the TMA-staged boxes in, the y pass's loads and stores, the x pass's 11 loads of the
+    # column's channels and the fused L1 term's x, y (forward 269 B, backward 259 B) through
+    # the SM's 128 B/clock shared-memory pipe
     sms_ = torch.cuda.get_device_properties(device).multi_processor_count
     fmax_ = (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
     smem_peak = 128.0 * sms_ * fmax_ * 1e6 / 1e9  # GB/s
     smem_roofs = {}
-    for k, bpv in {"ssim3d_fwd": 287, "ssim3d_bwd": 304}.items():
+    for k, bpv in {"ssim3d_fwd": 269, "ssim3d_bwd": 259}.items():
         if k in per_kernel and per_kernel[k] > 0:
             gbs = bpv * nvox / (per_kernel[k] * 1e-3) / 1e9
             smem_roofs[k] = {"smem_bytes_per_voxel": bpv, "achieved_gbs": round(gbs, 1),

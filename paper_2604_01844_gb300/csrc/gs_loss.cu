@@ -495,7 +495,7 @@ int ssim_xy_attributes() {
 //   1. receives the plane's 48 x 18 box of every input channel by TMA, four planes in flight
 //      (zero fill outside the volume; the box starts 8 columns left of the tile, so that its x
 //      coordinate stays 16-byte aligned, and 5 rows above it),
-//   2. filters the box along y: items of one halo column and two output rows share the 12
+//   2. filters the box along y: items of one halo column and four output rows share the 14
 //      inputs they need (register blocking), results in shared memory (forward one float4
 //      of channels per column, backward a float2 and a float),
 //   3. filters along x for its own column, which leaves the thread the plane's xy-filtered
@@ -519,12 +519,13 @@ constexpr int kFThreads = kFX * kFY;                   // a thread per column
 constexpr int kBoxX = kFX + 16, kBoxY = kFY + 2 * kR;  // staged box 48 x 18
 constexpr int kHaloX = kFX + 2 * kR;                   // 42 y-filtered columns
 constexpr int kFStages = 6;                            // planes in flight (3 pairs)
-constexpr int kYItems = kHaloX * (kFY / 2);            // 168 y-pass items
+constexpr int kYItems = 2 * kHaloX * (kFY / 4);        // 168 y-pass items (2 planes)
 constexpr uint32_t kBox4 = kBoxX * kBoxY * 4;          // bytes of a 4-byte channel box (3456)
 constexpr uint32_t kBox8 = 2 * kBox4;                  // of an 8-byte (pair) box
 constexpr uint32_t kTile4 = kFX * kFY * 4;             // of a 4-byte output tile (1024)
 static_assert(kBox4 % 128 == 0 && kTile4 % 128 == 0, "TMA destinations stay 128-byte aligned");
-static_assert(kFY % 2 == 0 && kFThreads % 32 == 0, "y items take row pairs; whole warps");
+static_assert(kFY % 4 == 0 && kFThreads % 32 == 0 && kYItems <= kFThreads,
+              "y items take four rows; whole warps");
 
 // Stage layout and filtered channels of the two directions.
 //   forward (BWD = false): X box | Y box; NP = 2 filtered pairs (x, y), (x^2 + y^2, x y)
@@ -662,51 +663,50 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
     if (!mbar_wait(&bar[(p0 + 1) % kFStages], (uint32_t)((p0 + 1) / kFStages) & 1u))
       abort_flag = 1;
     const int hoff = (i & 1) * 2 * kFY * kHaloX;  // this iteration's buffer
-    // ---- y pass of both planes: item (halo column c, output rows 2j and 2j + 1), inputs at
-    // box column c + 3
+    // ---- y pass of both planes: item (plane h, halo column c, output rows 4q .. 4q + 3), the
+    // 14 box rows from 4q on at box column c + 3
     if (tid < kYItems) {
-      const int c = tid % kHaloX, j = tid / kHaloX;
+      const int c = tid % kHaloX, hq = tid / kHaloX, h = hq / (kFY / 4), q = hq % (kFY / 4);
+      const unsigned char* sb = base + ((p0 + h) % kFStages) * S::stage;
+      float2 a[4][NP];
+      float cs[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const unsigned char* sb = base + ((p0 + h) % kFStages) * S::stage;
-        float2 a0[NP], a1[NP];
-        float c0 = 0.f, c1 = 0.f;
+      for (int o = 0; o < 4; ++o) {
 #pragma unroll
-        for (int m = 0; m < NP; ++m) a0[m] = a1[m] = make_float2(0.f, 0.f);
+        for (int m = 0; m < NP; ++m) a[o][m] = make_float2(0.f, 0.f);
+        cs[o] = 0.f;
+      }
 #pragma unroll
-        for (int r = 0; r <= 2 * kR + 1; ++r) {
-          const int e = (2 * j + r) * kBoxX + c + 3;
-          float2 u[NP];
-          float us = 0.f;
-          if constexpr (!BWD) {  // X, Y -> (x, y), (x^2 + y^2, x y)
-            const float xv = reinterpret_cast<const float*>(sb)[e];
-            const float yv = reinterpret_cast<const float*>(sb + S::offB)[e];
-            u[0] = make_float2(xv, yv);
-            u[NP - 1] = make_float2(fmaf(xv, xv, yv * yv), xv * yv);
-          } else {  // (m1, m2), m3
-            u[0] = reinterpret_cast<const float2*>(sb)[e];
-            us = reinterpret_cast<const float*>(sb + S::offB)[e];
-          }
-          if (r <= 2 * kR) {
-#pragma unroll
-            for (int m = 0; m < NP; ++m) a0[m] = __ffma2_rn(w2[r], u[m], a0[m]);
-            if (NS) c0 = fmaf(w2[r].x, us, c0);
-          }
-          if (r >= 1) {
-#pragma unroll
-            for (int m = 0; m < NP; ++m) a1[m] = __ffma2_rn(w2[r - 1], u[m], a1[m]);
-            if (NS) c1 = fmaf(w2[r - 1].x, us, c1);
-          }
+      for (int r = 0; r < 4 + 2 * kR; ++r) {
+        const int e = (4 * q + r) * kBoxX + c + 3;
+        float2 u[NP];
+        float us = 0.f;
+        if constexpr (!BWD) {  // X, Y -> (x, y), (x^2 + y^2, x y)
+          const float xv = reinterpret_cast<const float*>(sb)[e];
+          const float yv = reinterpret_cast<const float*>(sb + S::offB)[e];
+          u[0] = make_float2(xv, yv);
+          u[NP - 1] = make_float2(fmaf(xv, xv, yv * yv), xv * yv);
+        } else {  // (m1, m2), m3
+          u[0] = reinterpret_cast<const float2*>(sb)[e];
+          us = reinterpret_cast<const float*>(sb + S::offB)[e];
         }
-        const int o0 = hoff + (h * kFY + 2 * j) * kHaloX + c, o1 = o0 + kHaloX;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int k = r - o;  // tap of box row 4q + r for output row 4q + o
+          if (k < 0 || k > 2 * kR) continue;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) a[o][m] = __ffma2_rn(w2[k], u[m], a[o][m]);
+          if (NS) cs[o] = fmaf(w2[k].x, us, cs[o]);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int oo = hoff + (h * kFY + 4 * q + o) * kHaloX + c;
         if constexpr (NP == 2) {  // (x, y, x^2 + y^2, x y) of a column as one float4
-          h4[o0] = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
-          h4[o1] = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
+          h4[oo] = make_float4(a[o][0].x, a[o][0].y, a[o][1].x, a[o][1].y);
         } else {
-          h2[o0] = a0[0];
-          h2[o1] = a1[0];
-          h1[o0] = c0;
-          h1[o1] = c1;
+          h2[oo] = a[o][0];
+          h1[oo] = cs[o];
         }
       }
     }

@@ -97,6 +97,9 @@ def test_argument_errors_are_host_side(built):
     assert rc == binding.GS_ERR_ARG
     rc = L.gs_l1_ssim2d_loss(16, 16, 1, 8, 8, 1.0, 1.0, 0.2, 16, 16, 0, 16, 64, None)
     assert rc == binding.GS_ERR_CAPACITY
+    # TV: more than 2^31 - 1 (y, z) rows is refused before any launch
+    rc = L.gs_tv3d_loss(16, 4, 65536, 32768, 1.0, 16, 16, 0, None)
+    assert rc == binding.GS_ERR_ARG
 
 
 def test_batch_table_validation(built):
