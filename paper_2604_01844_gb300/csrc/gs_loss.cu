@@ -503,13 +503,14 @@ int ssim_xy_attributes() {
 //   4. keeps them in a register ring of the last 12 planes and, once 11 planes are in,
 //      filters along z for the plane 5 behind and completes that voxel: SSIM, the loss term
 //      and the maps in the forward, the gradient in the backward.
-// Planes go through these steps in pairs (six planes in flight), so that each barrier covers
-// two planes and every thread has two independent chains of work in each step.
+// Planes go through these steps three at a time (six planes in flight), so that each barrier
+// covers three planes, the y pass has an item for nearly every thread and every thread has
+// three independent chains of work in the other steps.
 // The forward filters four channels, x, y, x^2 + y^2 and x y: SSIM depends on the second
 // moments of x and y only through sigma_x^2 + sigma_y^2.  The backward filters the maps m1,
 // m2, m3; its stage also brings the tile's X and Y at the output plane.  The ring slots of
-// each pair are fixed at compile time by a switch over the 6 pair positions, so the ring stays
-// in registers without unrolling the whole loop.  Filtering is zero-padded 'same' in all three
+// each iteration are fixed at compile time by a switch over the 4 ring positions, so the ring
+// stays in registers without unrolling the whole loop.  Filtering is zero-padded 'same' in all three
 // directions, as in the separable kernels above (the y, x, z
 // order and the summed channel only change FP32 rounding).  Traffic: forward X, Y in and three
 // maps out (20 bytes per voxel); backward the maps, X and Y in and the gradient out (24).
@@ -518,8 +519,9 @@ constexpr int kFX = 32, kFY = 8;                       // output tile (x, y)
 constexpr int kFThreads = kFX * kFY;                   // a thread per column
 constexpr int kBoxX = kFX + 16, kBoxY = kFY + 2 * kR;  // staged box 48 x 18
 constexpr int kHaloX = kFX + 2 * kR;                   // 42 y-filtered columns
-constexpr int kFStages = 6;                            // planes in flight (3 pairs)
-constexpr int kYItems = 2 * kHaloX * (kFY / 4);        // 168 y-pass items (2 planes)
+constexpr int kPP = 3;                                 // planes per iteration
+constexpr int kFStages = 2 * kPP;                      // planes in flight (2 iterations)
+constexpr int kYItems = kPP * kHaloX * (kFY / 4);      // 252 y-pass items (3 planes)
 constexpr uint32_t kBox4 = kBoxX * kBoxY * 4;          // bytes of a 4-byte channel box (3456)
 constexpr uint32_t kBox8 = 2 * kBox4;                  // of an 8-byte (pair) box
 constexpr uint32_t kTile4 = kFX * kFY * 4;             // of a 4-byte output tile (1024)
@@ -540,65 +542,65 @@ struct FusedShape {
   // y-filtered channels of one plane: forward one float4 per column, backward a float2 plane
   // (m1, m2) and a float plane (m3)
   static constexpr uint32_t hbuf = (BWD ? 12 : 16) * kFY * kHaloX;
-  static constexpr size_t smem = 128 + kFStages * stage + 4 * hbuf;  // h: 2 planes x 2
+  static constexpr size_t smem = 128 + kFStages * stage + 2 * kPP * hbuf;  // h: 2 x kPP
 };
 
-// The ring holds the last 12 planes' xy-filtered channels; planes arrive in pairs, the pair
-// of iteration i in slots 2K and 2K + 1 (K = i % 6).  The z filter of the pair's first plane
-// reads the 11 slots ending at 2K, that of the second the 11 ending at 2K + 1.
+// The ring holds the last 12 planes' xy-filtered channels; planes arrive kPP at a time, those
+// of iteration i in slots kPP K .. kPP K + kPP - 1 (K = i % (12 / kPP)).  The z filter of the
+// iteration's plane h reads the 11 slots ending at kPP K + h.
 constexpr int kRing = 12;
+static_assert(kRing % kPP == 0 && kRing >= 2 * kR + 1, "ring holds every window");
 template <int K, int NP, int NS>
-__device__ __forceinline__ void ring_z2(float2 (&rp)[NP][kRing], float (&rs)[NS ? NS : 1][kRing],
-                                        const float2 (&vp)[2][NP],
-                                        const float (&vs)[2][NS ? NS : 1],
-                                        const float2 (&w2)[2 * kR + 1], float2 (&fp)[2][NP],
-                                        float (&fs)[2][NS ? NS : 1]) {
+__device__ __forceinline__ void ring_zp(float2 (&rp)[NP][kRing], float (&rs)[NS ? NS : 1][kRing],
+                                        const float2 (&vp)[kPP][NP],
+                                        const float (&vs)[kPP][NS ? NS : 1],
+                                        const float2 (&w2)[2 * kR + 1], float2 (&fp)[kPP][NP],
+                                        float (&fs)[kPP][NS ? NS : 1]) {
+  // plane by plane: each insert overwrites the plane 12 behind, which no later window needs
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kPP; ++h) {
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-      rp[m][2 * K + h] = vp[h][m];
+      rp[m][kPP * K + h] = vp[h][m];
       fp[h][m] = make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
-      rs[m][2 * K + h] = vs[h][m];
+      rs[m][kPP * K + h] = vs[h][m];
       fs[h][m] = 0.f;
     }
-  }
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int t = 0; t <= 2 * kR; ++t) {
-      const int sl = (2 * K + h + kRing - 2 * kR + t) % kRing;
+      const int sl = (kPP * K + h + kRing - 2 * kR + t) % kRing;
 #pragma unroll
       for (int m = 0; m < NP; ++m) fp[h][m] = __ffma2_rn(w2[t], rp[m][sl], fp[h][m]);
 #pragma unroll
       for (int m = 0; m < NS; ++m) fs[h][m] = fmaf(w2[t].x, rs[m][sl], fs[h][m]);
     }
-}
-
-template <int NP, int NS>
-__device__ __forceinline__ void ring_push2(int k, float2 (&rp)[NP][kRing],
-                                           float (&rs)[NS ? NS : 1][kRing],
-                                           const float2 (&vp)[2][NP],
-                                           const float (&vs)[2][NS ? NS : 1],
-                                           const float2 (&w2)[2 * kR + 1], float2 (&fp)[2][NP],
-                                           float (&fs)[2][NS ? NS : 1]) {
-  switch (k) {
-    case 0: ring_z2<0, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
-    case 1: ring_z2<1, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
-    case 2: ring_z2<2, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
-    case 3: ring_z2<3, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
-    case 4: ring_z2<4, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
-    default: ring_z2<5, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
   }
 }
 
-// Shared streaming skeleton: two input planes per iteration (twice the independent work
-// between barriers).  `on_stage(sb, p, h)` reads what the thread needs from plane p's stage
-// (h = p % 2) before the stage is released; `finish(z, h, fp, fs)` completes the voxel of the
-// thread's column at output plane z = z0 + p - 10.  Returns false if a TMA wait timed out: every thread then leaves the loop
+template <int NP, int NS>
+__device__ __forceinline__ void ring_push(int k, float2 (&rp)[NP][kRing],
+                                          float (&rs)[NS ? NS : 1][kRing],
+                                          const float2 (&vp)[kPP][NP],
+                                          const float (&vs)[kPP][NS ? NS : 1],
+                                          const float2 (&w2)[2 * kR + 1], float2 (&fp)[kPP][NP],
+                                          float (&fs)[kPP][NS ? NS : 1]) {
+  static_assert(kRing / kPP == 4, "one case per ring position");
+  switch (k) {
+    case 0: ring_zp<0, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 1: ring_zp<1, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    case 2: ring_zp<2, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+    default: ring_zp<3, NP, NS>(rp, rs, vp, vs, w2, fp, fs); break;
+  }
+}
+
+// Shared streaming skeleton: kPP input planes per iteration (kPP times the independent work
+// between barriers, and y-pass items for nearly every thread).  `on_stage(sb, p, h)` reads
+// what the thread needs from plane p's stage (h = p % kPP) before the stage is released;
+// `finish(z, h, fp, fs)` completes the voxel of the thread's column at output plane
+// z = z0 + p - 10.  Returns false if a TMA wait timed out: every thread then leaves the loop
 // at the same iteration, and the copies still in flight have been waited for.
 template <bool BWD, typename Finish, typename OnStage>
 __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUtensorMap* tmB,
@@ -614,13 +616,13 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
   // (m1, m2), then float m3
   float4* h4 = reinterpret_cast<float4*>(base + kFStages * S::stage);
   float2* h2 = reinterpret_cast<float2*>(base + kFStages * S::stage);
-  float* h1 = reinterpret_cast<float*>(h2 + 4 * kFY * kHaloX);
+  float* h1 = reinterpret_cast<float*>(h2 + 2 * kPP * kFY * kHaloX);
   __shared__ __align__(8) uint64_t bar[kFStages];
   __shared__ int abort_flag;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int bx0 = blockIdx.x * kFX, by0 = blockIdx.y * kFY;
-  // planes p = 0 .. 2 * iters - 1 enter at z = z0 - kR + p (one past the range if odd)
-  const int planes = (z1 - z0) + 2 * kR, iters = (planes + 1) / 2, total = 2 * iters;
+  // planes p = 0 .. kPP iters - 1 enter at z = z0 - kR + p (up to kPP - 1 past the range)
+  const int planes = (z1 - z0) + 2 * kR, iters = (planes + kPP - 1) / kPP, total = kPP * iters;
   int issued = 0;
   auto issue = [&](int p) {
     const int st = p % kFStages;
@@ -653,18 +655,19 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
 #pragma unroll
     for (int m = 0; m < NSA; ++m) rs[m][t] = 0.f;
   }
-  int k = 0;  // ring pair position of iteration i: i % 6
+  int k = 0;  // ring position of iteration i: i % (kRing / kPP)
   bool failed = false;
   for (int i = 0; i < iters; ++i) {
-    const int p0 = 2 * i;
+    const int p0 = kPP * i;
     // a wait that gives up raises the flag; the planes are still walked (on whatever the
     // buffers hold) so that every thread reaches the barrier, after which all leave together
-    if (!mbar_wait(&bar[p0 % kFStages], (uint32_t)(p0 / kFStages) & 1u)) abort_flag = 1;
-    if (!mbar_wait(&bar[(p0 + 1) % kFStages], (uint32_t)((p0 + 1) / kFStages) & 1u))
-      abort_flag = 1;
-    const int hoff = (i & 1) * 2 * kFY * kHaloX;  // this iteration's buffer
-    // ---- y pass of both planes: item (plane h, halo column c, output rows 4q .. 4q + 3), the
-    // 14 box rows from 4q on at box column c + 3
+#pragma unroll
+    for (int h = 0; h < kPP; ++h)
+      if (!mbar_wait(&bar[(p0 + h) % kFStages], (uint32_t)((p0 + h) / kFStages) & 1u))
+        abort_flag = 1;
+    const int hoff = (i & 1) * kPP * kFY * kHaloX;  // this iteration's buffer
+    // ---- y pass of the iteration's planes: item (plane h, halo column c, output rows 4q ..
+    // 4q + 3), the 14 box rows from 4q on at box column c + 3
     if (tid < kYItems) {
       const int c = tid % kHaloX, hq = tid / kHaloX, h = hq / (kFY / 4), q = hq % (kFY / 4);
       const unsigned char* sb = base + ((p0 + h) % kFStages) * S::stage;
@@ -711,19 +714,19 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) on_stage(base + ((p0 + h) % kFStages) * S::stage, p0 + h, h);
+    for (int h = 0; h < kPP; ++h) on_stage(base + ((p0 + h) % kFStages) * S::stage, p0 + h, h);
     __syncthreads();
     if (abort_flag) {
       failed = true;
       break;
     }
-    if (tid == 0)  // refill the two stages just read
-      for (int n = 0; n < 2 && issued < total; ++n) issue(issued++);
-    // ---- x pass of both planes for the thread's column
-    float2 vp[2][NP];
-    float vs[2][NSA];
+    if (tid == 0)  // refill the stages just read
+      for (int n = 0; n < kPP && issued < total; ++n) issue(issued++);
+    // ---- x pass of the iteration's planes for the thread's column
+    float2 vp[kPP][NP];
+    float vs[kPP][NSA];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kPP; ++h) {
 #pragma unroll
       for (int m = 0; m < NP; ++m) vp[h][m] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -732,7 +735,7 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
 #pragma unroll
     for (int t = 0; t <= 2 * kR; ++t) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < kPP; ++h) {
         const int o = hoff + (h * kFY + ty) * kHaloX + tx + t;
         if constexpr (NP == 2) {
           const float4 q = h4[o];
@@ -744,13 +747,13 @@ __device__ __forceinline__ bool fused_stream(const CUtensorMap* tmA, const CUten
         }
       }
     }
-    // ---- ring, z filter, completion of output planes z0 + p0 - 2 kR and the next
-    float2 fp[2][NP];
-    float fs[2][NSA];
-    ring_push2<NP, NS>(k, rp, rs, vp, vs, w2, fp, fs);
-    k = k == kRing / 2 - 1 ? 0 : k + 1;
+    // ---- ring, z filter, completion of output planes z0 + p0 - 2 kR and the next ones
+    float2 fp[kPP][NP];
+    float fs[kPP][NSA];
+    ring_push<NP, NS>(k, rp, rs, vp, vs, w2, fp, fs);
+    k = k == kRing / kPP - 1 ? 0 : k + 1;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kPP; ++h) {
       const int z = z0 + p0 + h - 2 * kR;
       if (z >= z0 && z < z1) finish(z, h, fp[h], fs[h]);
     }
@@ -827,7 +830,7 @@ __global__ void __launch_bounds__(kFThreads, 2)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x = blockIdx.x * kFX + tx, y = blockIdx.y * kFY + ty;
   const bool own = x < nx && y < ny;
-  float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f};  // X, Y of the two voxels finished next
+  float xv[kPP], yv[kPP];  // X, Y of the voxels this iteration finishes
   auto on_stage = [&](const unsigned char* sb, int, int h) {
     xv[h] = reinterpret_cast<const float*>(sb + S::offX)[ty * kFX + tx];
     yv[h] = reinterpret_cast<const float*>(sb + S::offY)[ty * kFX + tx];
