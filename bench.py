@@ -39,11 +39,12 @@ UNIT = "evals/s"
 
 # The evaluation kernels' work per in-cut evaluation: one ex2 on the special-function unit and
 # this many FP32 lane operations (raster_fwd: offset, two fma for the exponent, the
-# accumulating fma; raster_bwd: two fma, G = g e, G dx, three moment updates -- the y moments
-# are folded per row; vox_fwd: the z offset fma, two fma, the accumulating fma; vox_bwd: the
-# same offset and exponent, q = g e, q dz, three moment updates).  Their roofline is the
-# slower of the two units at the rates the probe kernels measure.
-FP32_OPS_PER_EVAL = {"raster_fwd": 4, "raster_bwd": 7, "vox_fwd": 4, "vox_bwd": 8}
+# accumulating fma; raster_bwd: two fma, G = g e, and three moment updates against the block's
+# compile-time column offsets -- the y moments are folded per row; vox_fwd: the z offset fma,
+# two fma, the accumulating fma; vox_bwd: the same offset and exponent, q = g e, q dz, three
+# moment updates).  Their roofline is the slower of the two units at the rates the probe
+# kernels measure.
+FP32_OPS_PER_EVAL = {"raster_fwd": 4, "raster_bwd": 6, "vox_fwd": 4, "vox_bwd": 8}
 # The per-evaluation figures of the hot-path scope's measurement plan, which count every FP32
 # operation of an unpacked, unfolded evaluation: forward 2 adds (the pixel offset), 3 fma/mul
 # (the quadratic form), 1 compare/select (the cut) and 1 fma (the accumulation) besides the

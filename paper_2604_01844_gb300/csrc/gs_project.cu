@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
 #pragma unroll
       for (int p = 0; p < HP; ++p)
         dx[p] = make_float2(fx0 + (float)(2 * p) - g.x, fx0 + (float)(2 * p + 1) - g.x);
-      const float2 ca = make_float2(c.x, c.x), A2 = make_float2(g.z, g.z);
+      const float2 ca = make_float2(c.x, c.x);
 #pragma unroll
       for (int ry = 0; ry < 4; ++ry) {
         const float dy = (fy0 + (float)ry) - g.y;
@@ -598,9 +598,11 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
             cnt_eval += (e.x > cut && x < W && y < H) ? 1u : 0u;
             cnt_eval += (e.y > cut && x + 1 < W && y < H) ? 1u : 0u;
           } else {
-            const float2 val =
-                make_float2(e.x > cut ? ex2(e.x) : 0.f, e.y > cut ? ex2(e.y) : 0.f);
-            acc[ry * HP + p] = __ffma2_rn(A2, val, acc[ry * HP + p]);
+            // the cut as a predicate on the accumulating FMA (no select): each component rounds
+            // like the packed FMA with a zero value would leave it, so sums are unchanged
+            const float vx = ex2(e.x), vy = ex2(e.y);
+            if (e.x > cut) acc[ry * HP + p].x = fmaf(g.z, vx, acc[ry * HP + p].x);
+            if (e.y > cut) acc[ry * HP + p].y = fmaf(g.z, vy, acc[ry * HP + p].y);
           }
         }
       }
@@ -655,9 +657,11 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
 // them 32 at a time, one per lane.  Every lane walks the block's 4 x BW pixels in the same
 // fully unrolled order, so the warp never diverges: dL/dI comes from shared memory as a
 // broadcast, the cut is decided exactly as in the forward (same offsets, same expression), and
-// the six moments of g exp(-q/2) stay in the lane's registers (row sums folded with dy).  A
-// lane then adds its six sums to the record's shared accumulators; after the batch one thread
-// per record adds them to the record's moments (two float4 atomics).
+// the six moments of g exp(-q/2) stay in the lane's registers (row sums folded with dy; the x
+// moments taken about the block's centre column, whose offsets are compile-time constants,
+// and moved to the record's centre once per visit).  A lane then adds its six sums to the
+// record's shared accumulators; after the batch one thread per record adds them to the
+// record's moments (two float4 atomics).
 // ------------------------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBlocks<T>::NT)
@@ -750,10 +754,12 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
             const float2 gg = (p & 1) ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
             const float2 val = make_float2(e.x > cut ? ex2(e.x) : 0.f, e.y > cut ? ex2(e.y) : 0.f);
             const float2 G = __fmul2_rn(gg, val);
-            const float2 Gx = __fmul2_rn(G, dx[p]);
+            // x moments about the block's centre: X = x - (x_block + (BW - 1) / 2) is a
+            // compile-time half-integer, so G X and G X^2 cost one packed FMA each
+            const float Xa = (float)(2 * p) - 0.5f * (float)(BW - 1), Xb = Xa + 1.f;
             r0 = __fadd2_rn(r0, G);
-            rx = __fadd2_rn(rx, Gx);
-            rxx = __ffma2_rn(Gx, dx[p], rxx);
+            rx = __ffma2_rn(G, make_float2(Xa, Xb), rx);
+            rxx = __ffma2_rn(G, make_float2(Xa * Xa, Xb * Xb), rxx);
           }
           const float r0s = r0.x + r0.y, rxs = rx.x + rx.y;
           s0 += r0s;
@@ -762,6 +768,12 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
           sy = fmaf(dy, r0s, sy);
           sxy = fmaf(dy, rxs, sxy);
           syy = fmaf(dy * dy, r0s, syy);
+        }
+        {  // back to moments about the record's centre: dx = X + o
+          const float o = ((float)(tx0 + bxl) + 0.5f * (float)(BW - 1)) - g.x;
+          sxx = fmaf(o, fmaf(2.f, sx, o * s0), sxx);
+          sxy = fmaf(o, sy, sxy);
+          sx = fmaf(o, s0, sx);
         }
         if (s0 != 0.f || sx != 0.f || sy != 0.f || sxx != 0.f || sxy != 0.f || syy != 0.f) {
           atomicAdd(&s_acc[0][j], s0);
