@@ -307,9 +307,9 @@ __global__ void __launch_bounds__(kThreads)
     st->reserved[2] = b.in[b.count - 1].key_off +
                       (int64_t)b.in[b.count - 1].nv * b.in[b.count - 1].TW * b.in[b.count - 1].TH;
   }
-  if (st->code != GS_OK) return;
   const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const uint32_t cnt = idx < items ? counts[idx] : 0u;
+  const uint32_t cnt = idx < items ? counts[idx] : 0u;  // requested with the status word
+  if (st->code != GS_OK) return;
   const uint32_t incl = gsd::warp_inclusive_scan(cnt);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 31) warp_pre[w] = incl;
@@ -535,14 +535,14 @@ __global__ void __launch_bounds__(FwdBlocks<T>::NT, T == 32 ? 1 : 512 / FwdBlock
   __shared__ uint32_t s_mask[S::SB];
   __shared__ uint16_t s_list[S::NW][S::SB];
   __shared__ unsigned long long s_cnt;
-  if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
+  const uint2 r = ranges[key];  // requested together with the status word, not after it
+  if (st->code != GS_OK) return;
   const Inst& I = b.in[inst_of_key(b, key)];
   const int64_t lk = key - I.key_off;
   const int v = (int)(lk / (I.TW * I.TH)), tile = (int)(lk - (int64_t)v * I.TW * I.TH);
   const int W = I.W, H = I.H;
   const int tx0 = (tile % I.TW) * T, ty0 = (tile / I.TW) * T;
-  const uint2 r = ranges[key];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int bxl = (w % S::NBX) * BW, byl = (w / S::NBX) * 4;  // the warp's block in the tile
   const float fx0 = (float)(tx0 + bxl), fy0 = (float)(ty0 + byl);
@@ -680,9 +680,9 @@ __global__ void __launch_bounds__(BwdBlocks<T>::NT, T == 32 ? 3 : 1024 / BwdBloc
   __shared__ uint32_t s_mask[SB];
   __shared__ float s_acc[6][SB];
   __shared__ uint16_t s_list[S::NW][SB];
-  if (st->code != GS_OK) return;
   const int64_t key = blockIdx.x;
-  const uint2 r = ranges[key];
+  const uint2 r = ranges[key];  // requested together with the status word, not after it
+  if (st->code != GS_OK) return;
   if (r.x == r.y) return;
   const Inst& I = b.in[inst_of_key(b, key)];
   const int64_t lk = key - I.key_off;

@@ -439,10 +439,11 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ VisitCoef s_vc[kThreads];
   __shared__ uint8_t s_zr[kWarps * kThreads];
   __shared__ unsigned long long s_cnt;
-  if (st->code != GS_OK) return;
   // one CTA per (brick, sub-brick)
   const int nsub = bt.sub * bt.sub * bt.sub;
   const int key = (int)(blockIdx.x / nsub), sb = (int)(blockIdx.x % nsub);
+  const uint2 r = ranges[key];  // requested together with the status word, not after it
+  if (st->code != GS_OK) return;
   const VInst& I = bt.in[inst_of_key(bt, key)];
   const VGrid& g = I.g;
   int sx, sy, sz;
@@ -450,7 +451,6 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int xend = g.lo[0] + g.dim[0], yend = g.lo[1] + g.dim[1], zend = g.lo[2] + g.dim[2];
   if (sx >= xend || sy >= yend || sz >= zend) return;  // sub-brick outside the region
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint2 r = ranges[key];
   const float hz = g.h[2];
   if (COUNT && tid == 0) s_cnt = 0ull;
   uint32_t cnt = 0;
@@ -493,20 +493,22 @@ __global__ void __launch_bounds__(kThreads, 4)
         const float lin = fmaf(c0.z, dx, c1.x * dy);
         const float dz0 = zc0 - G.z;
         const float2 q2 = make_float2(qxy, qxy), l2 = make_float2(lin, lin);
-        const float2 c22 = make_float2(c1.y, c1.y), r2 = make_float2(G.w, G.w);
+        const float2 c22 = make_float2(c1.y, c1.y), hz2 = make_float2(hz, hz);
+        const float2 dz02 = make_float2(dz0, dz0);
         // closed-form exponent per voxel pair: the pairs are independent, so the unrolled walk
-        // interleaves them
+        // interleaves them.  dz of both voxels in one packed FMA (each component rounds like
+        // the scalar fmaf); the cut is a predicate on the accumulating FMA (sums unchanged).
         auto pair = [&](int p) {
-          const float2 dz = make_float2(fmaf((float)(2 * p), hz, dz0),
-                                        fmaf((float)(2 * p + 1), hz, dz0));
+          const float2 dz =
+              __ffma2_rn(make_float2((float)(2 * p), (float)(2 * p + 1)), hz2, dz02);
           const float2 e = __ffma2_rn(__ffma2_rn(c22, dz, l2), dz, q2);
           if (COUNT) {
             cnt += (e.x > c1.z && sz + 2 * p < zend) ? 1u : 0u;
             cnt += (e.y > c1.z && sz + 2 * p + 1 < zend) ? 1u : 0u;
           } else {
-            const float2 val = make_float2(e.x > c1.z ? ex2(e.x) : 0.f,
-                                           e.y > c1.z ? ex2(e.y) : 0.f);
-            acc[p] = __ffma2_rn(r2, val, acc[p]);
+            const float vx = ex2(e.x), vy = ex2(e.y);
+            if (e.x > c1.z) acc[p].x = fmaf(G.w, vx, acc[p].x);
+            if (e.y > c1.z) acc[p].y = fmaf(G.w, vy, acc[p].y);
           }
         };
         switch (walk_window(code & 15, code >> 4)) {  // warp-uniform
@@ -608,11 +610,11 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ VisitCoef s_vc[kThreads];
   __shared__ uint8_t s_zr[kWarps * kThreads];
   __shared__ float s_mom[kThreads * kMoments];
-  if (st->code != GS_OK) return;
   // one CTA per (brick, sub-brick)
   const int nsub = bt.sub * bt.sub * bt.sub;
   const int key = (int)(blockIdx.x / nsub), sb = (int)(blockIdx.x % nsub);
-  const uint2 r = ranges[key];
+  const uint2 r = ranges[key];  // requested together with the status word, not after it
+  if (st->code != GS_OK) return;
   if (r.x == r.y) return;
   const VInst& I = bt.in[inst_of_key(bt, key)];
   const VGrid& g = I.g;
@@ -676,17 +678,18 @@ __global__ void __launch_bounds__(kThreads, 4)
         const float lin = fmaf(c0.z, dx, c1.x * dy);
         const float dz0 = zc0 - G.z;
         const float2 q2 = make_float2(qxy, qxy), l2 = make_float2(lin, lin);
-        const float2 c22 = make_float2(c1.y, c1.y);
+        const float2 c22 = make_float2(c1.y, c1.y), hz2 = make_float2(hz, hz);
+        const float2 dz02 = make_float2(dz0, dz0);
         float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
         // the forward's closed-form exponent over the record's exact pair range: the
         // backward's per-pair work is long enough that skipping the pairs outside the range
-        // pays for the uniform branches
+        // pays for the uniform branches (dz of both voxels in one packed FMA, as the forward)
         const int p0 = code & 15, p1 = code >> 4;  // warp-uniform
 #pragma unroll
         for (int p = 0; p < kS / 2; ++p) {
           if (p < p0 || p > p1) continue;
-          const float2 dz = make_float2(fmaf((float)(2 * p), hz, dz0),
-                                        fmaf((float)(2 * p + 1), hz, dz0));
+          const float2 dz =
+              __ffma2_rn(make_float2((float)(2 * p), (float)(2 * p + 1)), hz2, dz02);
           const float2 e = __ffma2_rn(__ffma2_rn(c22, dz, l2), dz, q2);
           const float2 val = make_float2(e.x > c1.z ? ex2(e.x) : 0.f,
                                          e.y > c1.z ? ex2(e.y) : 0.f);
