@@ -308,7 +308,13 @@ __global__ void __launch_bounds__(kThreads)
                       (int64_t)b.in[b.count - 1].nv * b.in[b.count - 1].TW * b.in[b.count - 1].TH;
   }
   const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const uint32_t cnt = idx < items ? counts[idx] : 0u;  // requested with the status word
+  // every input of the thread is requested up front, with the status word, so that the
+  // emission waits for one round trip instead of a chain of them
+  const bool in = idx < items;
+  const uint32_t cnt = in ? counts[idx] : 0u;
+  const short4 r_in = in ? rect[idx] : make_short4(0, 0, 0, 0);
+  const uint32_t tm_in = in ? tmask[idx] : 0u;
+  const uint32_t boff = block_offs[blockIdx.x];
   if (st->code != GS_OK) return;
   const uint32_t incl = gsd::warp_inclusive_scan(cnt);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   __syncthreads();
-  const uint32_t wbase = block_offs[blockIdx.x] + warp_pre[w];  // the warp's first pair
+  const uint32_t wbase = boff + warp_pre[w];  // the warp's first pair
   const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
   if (wtotal == 0) return;
   // this lane's record (meaningful where cnt > 0)
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(kThreads)
   if (cnt > 0) {
     const Inst& I = b.in[inst_of_item(b, idx)];
     const int v = (int)((uint32_t)(idx - I.item_off) / (uint32_t)I.n);
-    r = rect[idx];
+    r = r_in;
     TW = I.TW;
     kbase = (uint32_t)(I.v_off + v) << b.tbits;
     tx0i = r.x / T;
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(kThreads)
     ntx = r.z / T - tx0i + 1;
     const int nty = r.w / T - ty0i + 1;
     small = ntx * nty <= kMaskTiles;
-    tm = tmask[idx];
+    tm = tm_in;
   }
   // records with at most 32 box tiles: the warp writes its contiguous range of pairs
   // cooperatively, pair p going to lane p % 32, which finds the owning record by a binary

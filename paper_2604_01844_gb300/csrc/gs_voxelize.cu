@@ -290,9 +290,14 @@ __global__ void __launch_bounds__(kThreads)
     st->reserved[1] = sorted_vals_off;
     st->reserved[2] = n_keys;
   }
-  if (st->code != GS_OK) return;
   const int i = blockIdx.x * kThreads + threadIdx.x;
-  const uint32_t cnt = i < n ? counts[i] : 0u;
+  // every input of the thread is requested up front, with the status word
+  const bool in = i < n;
+  const uint32_t cnt = in ? counts[i] : 0u;
+  const short4 a = in ? lo_in[i] : make_short4(0, 0, 0, 0);
+  const short4 b = in ? hi_in[i] : make_short4(0, 0, 0, 0);
+  const uint32_t boff = block_offs[blockIdx.x];
+  if (st->code != GS_OK) return;
   const uint32_t incl = gsd::warp_inclusive_scan(cnt);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 31) warp_pre[w] = incl;
@@ -308,11 +313,10 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   if (cnt == 0) return;
-  uint32_t off = block_offs[blockIdx.x] + warp_pre[w] + incl - cnt;
+  uint32_t off = boff + warp_pre[w] + incl - cnt;
   const VInst& I = bt.in[inst_of_gaussian(bt, i)];
   const VGrid& g = I.g;
   const uint32_t kbase = (uint32_t)I.key_off;
-  const short4 a = lo_in[i], b = hi_in[i];
   const int B = bt.brick;
   for (int bz = (a.z - g.lo[2]) / B; bz <= (b.z - g.lo[2]) / B; ++bz)
     for (int by = (a.y - g.lo[1]) / B; by <= (b.y - g.lo[1]) / B; ++by)
