@@ -163,6 +163,40 @@ def test_ssim3d_streaming(B, shape):
     assert abs(float(loss.item()) - val) <= 1e-6 * abs(val)
 
 
+def test_ssim3d_streaming_equals_separable_passes(B):
+    """The fused streaming kernels against the separable z + xy passes on one larger volume
+    (the separable path taken by handing the library x and y at a 4-byte offset, which the
+    streaming kernels' tile copies cannot start from): the same loss and accumulated gradient
+    up to FP32 rounding order, at a size the FP64 oracle would take minutes for."""
+    Lb = B.lib()
+    shape = (100, 70, 96)  # z, y, x: three 32-column tiles, 9 ragged 8-row tiles, 2 z chunks
+    g = torch.Generator(device="cuda").manual_seed(11)
+    y = torch.rand(shape, device="cuda", generator=g)
+    x = (y + 0.1 * torch.randn(shape, device="cuda", generator=g)).clamp_min(0)
+    n = x.numel()
+    ws = torch.empty(Lb.gs_ssim3d_workspace_size(n), dtype=torch.uint8, device="cuda")
+    # the same values one float past a 16-byte boundary
+    xs = torch.empty(n + 4, device="cuda")
+    ys = torch.empty(n + 4, device="cuda")
+    xs[1:n + 1] = x.reshape(-1)
+    ys[1:n + 1] = y.reshape(-1)
+    # a gradient to accumulate onto, of the size of the SSIM gradient itself (about 1e-6 here),
+    # so that the FP32 sum keeps the SSIM part's digits
+    base = 1e-6 * torch.randn(shape, device="cuda", generator=g)
+    out = []
+    for px, py in ((B.ptr(x), B.ptr(y)), (B.ptr(xs) + 4, B.ptr(ys) + 4)):
+        loss = torch.zeros(1, device="cuda")
+        grad = base.clone()
+        dz, dy, dx = shape
+        B.check(Lb.gs_ssim3d_loss(px, py, dx, dy, dz, 1.0, 0.5, B.ptr(loss), B.ptr(grad), 1,
+                                  B.ptr(ws), ws.numel(), _s()), "ssim3d")
+        torch.cuda.synchronize()
+        out.append((float(loss.item()), (grad - base).double().cpu().numpy()))
+    (l_f, g_f), (l_s, g_s) = out
+    assert abs(l_f - l_s) <= 1e-5 * abs(l_s)
+    assert np.abs(g_f - g_s).max() <= 1e-4 * np.abs(g_s).max()
+
+
 def test_adam_matches_oracle(B):
     rng = np.random.default_rng(4)
     n = 1000
