@@ -479,6 +479,7 @@ def run_ours(args, ws, rank, local):
             "compression": lambda: compression(device),
             "gemm": lambda: gemm_rate(device),
             "batched_small": lambda: batched_small_step(device),
+            "kernel_sweep": lambda: kernel_sweep(device),
         }
         chosen = list(legs) if args.extras == "all" else args.extras.split(",")
         for name in chosen:
@@ -1327,6 +1328,135 @@ def gemm_rate(device, M=118016, reps=20, warmup=3):
     return out
 
 
+SWEEP_SCALE = 0.01     # isotropic Gaussian scale of the kernel sweep (world units; cube side 2)
+SWEEP_N = 20000        # Gaussians of the resolution sweep
+SWEEP_SIDES = (256, 512, 1024, 2048)          # one cone view of side^2 pixels
+SWEEP_VOL_SIDES = (64, 128, 256, 512, 1024)   # side^3 voxels
+SWEEP_COUNTS = (5000, 10000, 20000, 40000, 80000, 160000, 320000)
+SWEEP_PX_SIDE, SWEEP_VOX_SIDE = 1024, 96      # about 1e6 pixels / voxels (96: whole bricks)
+
+
+def power_law(xs, ys):
+    """Least-squares exponent k and prefactor a of y = a x^k on a log-log scale."""
+    import numpy as np
+
+    lx, ly = np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float))
+    k, c = np.polyfit(lx, ly, 1)
+    return float(k), float(np.exp(c))
+
+
+def _graph_ms(fn, reps=10, warmup=3, replays=5):
+    """Device ms per call of fn: reps calls captured in one CUDA graph, the graph replayed and
+    timed with CUDA events (no host launch overhead inside the timed region)."""
+    import torch
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(replays):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (reps * replays)
+
+
+def kernel_sweep(device, seed=5):
+    """The paper's kernel micro-benchmark (Sec. 3.5, Fig. 3): Gaussians with zero rotation and
+    one isotropic scale (0.01 world units, the cube being [-1, 1]^3), centres uniform in the
+    radius-0.8 ball, densities U(0.05, 1); (a) 20k Gaussians with the resolution varied: one
+    cone view of side^2 pixels (the rasterizer) and a side^3 volume (the voxelizer); (b) about
+    1e6 outputs (one 1024^2 view, a 96^3 volume) with the Gaussian count varied.  Per point:
+    device ms of the forward (gs_project: projection, keys, sort, ranges, raster; gs_voxelize
+    likewise) and of the backward with the forward's lists, from CUDA graphs of back-to-back
+    calls; the in-cut evaluations; and the power-law exponent of each series (time ~ N^k)."""
+    import torch
+
+    import synth
+    import paper_2604_01844_gb300 as g
+
+    def gaussians(n):
+        mr, sc, qt = synth.gaussians(seed, n, radius=0.8, scale_median=SWEEP_SCALE,
+                                     scale_sigma_log=0.0, isotropic=True,
+                                     identity_rotation=True)
+        return [torch.from_numpy(a).to(device) for a in (mr, sc, qt)]
+
+    def raster_point(side, d):
+        proj = g.Projector(synth.cone_views(1, side, side), side, side, tile=16, device=device)
+        img = proj.forward(*d)
+        dimg = torch.randn(img.shape, device=device, generator=torch.Generator(
+            device=device).manual_seed(side))
+        grads = tuple(torch.empty_like(t) for t in d)
+        fwd = _graph_ms(lambda: proj.forward(*d, out=img))
+        bwd = _graph_ms(lambda: proj.backward(*d, dimg, grads=grads, reuse=True))
+        evals = proj.count_evals(*d)
+        ok = proj.status().code == 0
+        del proj, img, dimg, grads
+        return {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4), "evals": evals,
+                "evals_per_s_fwd": evals / (fwd * 1e-3), "status": 0 if ok else 1}
+
+    def voxel_point(side, d):
+        vox = g.Voxelizer(synth.cube_grid(side), device=device)
+        vol = vox.forward(*d)
+        dvol = torch.randn(vol.shape, device=device, generator=torch.Generator(
+            device=device).manual_seed(side))
+        grads = tuple(torch.empty_like(t) for t in d)
+        fwd = _graph_ms(lambda: vox.forward(*d, out=vol))
+        bwd = _graph_ms(lambda: vox.backward(*d, dvol, grads=grads, reuse=True))
+        evals = vox.count_evals(*d)
+        ok = vox.status().code == 0
+        del vox, vol, dvol, grads
+        torch.cuda.empty_cache()
+        return {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4), "evals": evals,
+                "evals_per_s_fwd": evals / (fwd * 1e-3), "status": 0 if ok else 1}
+
+    d = gaussians(SWEEP_N)
+    by_res_r = {str(s): raster_point(s, d) for s in SWEEP_SIDES}
+    by_res_v = {str(s): voxel_point(s, d) for s in SWEEP_VOL_SIDES}
+    by_n_r, by_n_v = {}, {}
+    for n in SWEEP_COUNTS:
+        dn = gaussians(n)
+        by_n_r[str(n)] = raster_point(SWEEP_PX_SIDE, dn)
+        by_n_v[str(n)] = voxel_point(SWEEP_VOX_SIDE, dn)
+
+    def fits(series, keys, xs):
+        out = {}
+        for key in ("fwd_ms", "bwd_ms"):
+            k, a = power_law(xs, [series[str(x)][key] for x in keys])
+            out[key] = {"exponent": round(k, 3), "prefactor_ms": a}
+        return out
+
+    return {
+        "workload": f"kernel micro-benchmark: identity rotation, isotropic scale {SWEEP_SCALE}, "
+                    "centres uniform in the radius-0.8 ball, rho U(0.05, 1); (a) "
+                    f"{SWEEP_N} Gaussians, one cone view of side^2 / a side^3 volume; (b) one "
+                    f"{SWEEP_PX_SIDE}^2 view / a {SWEEP_VOX_SIDE}^3 volume, Gaussian count varied",
+        "raster_by_side": by_res_r, "voxel_by_side": by_res_v,
+        "raster_by_gaussians": by_n_r, "voxel_by_gaussians": by_n_v,
+        "power_laws": {
+            "raster_vs_pixels": fits(by_res_r, SWEEP_SIDES, [s * s for s in SWEEP_SIDES]),
+            "voxel_vs_voxels": fits(by_res_v, SWEEP_VOL_SIDES, [s ** 3 for s in SWEEP_VOL_SIDES]),
+            "raster_vs_gaussians": fits(by_n_r, SWEEP_COUNTS, SWEEP_COUNTS),
+            "voxel_vs_gaussians": fits(by_n_v, SWEEP_COUNTS, SWEEP_COUNTS),
+        },
+        "paper_context": "rasterizer on one 2K image with 20k Gaussians: 9.3 ms on an RTX 4070 "
+                         "Ti SUPER (whether forward or forward + backward is not stated)",
+        "note": "device time from CUDA graphs of 10 back-to-back calls, each forward including "
+                "its projection, keys, sort and ranges; backward with the forward's lists",
+    }
+
+
 def read_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.txt:
     lines '<kernel> <bytes per launch> <source>'), or None."""
@@ -1440,7 +1570,8 @@ def main():
     ap.add_argument("--extras", default="all",
                     help="comma-separated study legs to run after the headline step "
                          "(time_to_psnr, learned_init, batched, fit_volume, scale_up, "
-                         "warm_start, adaptive_control, compression, gemm, batched_small) "
+                         "warm_start, adaptive_control, compression, gemm, batched_small, "
+                         "kernel_sweep) "
                          "or 'all'")
     ap.add_argument("--fit-side", type=int, default=1024)
     ap.add_argument("--fit-gaussians", type=int, default=500000)

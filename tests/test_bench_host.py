@@ -48,3 +48,13 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     # rank > 0 prints nothing
     bench.run_reference(argparse.Namespace(steps=2, warmup=1), 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_power_law_fit_recovers_exponent():
+    """The kernel sweep's time ~ a N^k fit: exact on a power law, and a sweep's grid sizes are
+    whole bricks (the voxelizer's sides are multiples of 16)."""
+    xs = [256 ** 2, 512 ** 2, 1024 ** 2, 2048 ** 2]
+    k, a = bench.power_law(xs, [3e-4 * x ** 0.75 for x in xs])
+    assert abs(k - 0.75) < 1e-9 and abs(a / 3e-4 - 1) < 1e-9
+    assert all(s % 16 == 0 for s in bench.SWEEP_VOL_SIDES + (bench.SWEEP_VOX_SIDE,))
+    assert bench.SWEEP_PX_SIDE ** 2 > 1e6 > 0.8 * bench.SWEEP_VOX_SIDE ** 3
