@@ -1477,9 +1477,9 @@ def read_traffic(kernel: str):
 # ------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
-def oracle_sample(model, views, n_views):
-    """Oracle forward + gradient (fwd+bwd) over the first n_views views with all Gaussians;
-    returns (in-cut evaluations, seconds)."""
+def oracle_sample(model, views, n_views, nthreads=0):
+    """Oracle forward + gradient (fwd+bwd) over the first n_views views with all Gaussians, on
+    nthreads host threads (0: all); returns (in-cut evaluations, seconds)."""
     import numpy as np
 
     import oracle
@@ -1488,9 +1488,9 @@ def oracle_sample(model, views, n_views):
     V = oracle.views64(views[:n_views])
     W, H = WORKLOAD["W"], WORKLOAD["H"]
     t0 = time.perf_counter()
-    img, n_eval = oracle.project(P, V, W, H)
+    img, n_eval = oracle.project(P, V, W, H, nthreads=nthreads)
     dimg = np.sign(img - 0.5 * img.mean())  # an L1-style upstream gradient
-    oracle.project_grad(P, V, W, H, dimg)
+    oracle.project_grad(P, V, W, H, dimg, nthreads=nthreads)
     return n_eval, time.perf_counter() - t0
 
 
@@ -1503,10 +1503,14 @@ def cpu_baseline(model, views, target_s=15.0):
     nv = int(min(len(views), max(2, round(2 * target_s / max(t, 1e-3)))))
     if nv > 2:
         n_eval, t = oracle_sample(model, views, nv)
+    n1, t1 = oracle_sample(model, views, 1, nthreads=1)
     return {"value": n_eval / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle fwd + dual-number bwd of all {WORKLOAD['gaussians']} Gaussians "
                       f"on {nv} of the 75 views (512^2), {n_eval} in-cut evaluations in {t:.1f} s, "
-                      f"OpenMP over {cores} host threads"}
+                      f"OpenMP over {cores} host threads",
+            "single_thread": {"value": n1 / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same on the first view, one host thread: {n1} "
+                                        f"in-cut evaluations in {t1:.1f} s"}}
 
 
 REF_BUDGET_S = 150.0  # seconds of timed oracle work in the reference arm
