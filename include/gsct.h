@@ -378,7 +378,7 @@ int gs_sse(const float* d_a, const float* d_b, int64_t n, double* d_out, void* s
 int gs_tv3d_loss(const float* d_vol, int nx, int ny, int nz, float weight, float* d_loss,
                  float* d_grad, int accumulate, void* stream);
 
-/* Scratch bytes of gs_ssim2d_loss for n_elems image pixels (3 maps). */
+/* Scratch bytes of gs_ssim2d_loss for n_elems image pixels (3 maps and a status word). */
 size_t gs_ssim_workspace_size(int64_t n_elems);
 
 /* Scratch bytes of gs_ssim3d_loss for n_voxels voxels: the 3 derivative maps plus 5 volumes
@@ -389,7 +389,14 @@ size_t gs_ssim3d_workspace_size(int64_t n_voxels);
 
 /* D-SSIM term of Eq. 5: weight * (1 - mean SSIM(x, y)) over n_img images of H x W, SSIM of
  * Wang et al. 2004 with an 11 x 11 Gaussian window (sigma 1.5), zero-padded 'same'
- * filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = data_range.  Gradient w.r.t. x. */
+ * filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = data_range.  Gradient w.r.t. x.
+ * d_x, d_y, d_grad, d_ws device arrays of n_img * H * W floats (d_ws: gs_ssim_workspace_size
+ * bytes, else GS_ERR_CAPACITY); n_img <= 65535.  Images with W a multiple of 4, W >= 48,
+ * H >= 42 and 16-byte aligned buffers run as two kernels whose tiles are staged by TMA;
+ * others stage through registers (same results up to rounding).  The TMA kernels wait for
+ * their copies with bounded waits: a copy that never arrives (a hardware fault, not
+ * expected) leaves GS_ERR_TIMEOUT in the workspace's status word (the int after the three
+ * maps), a NaN loss and, in the backward, a NaN gradient over the affected tile. */
 int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, float data_range,
                    float weight, float* d_loss, float* d_grad, int accumulate, void* d_ws,
                    size_t ws_bytes, void* stream);
@@ -408,8 +415,9 @@ int gs_l1_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int 
  * framework that owns the whole device memory budget and hands none to plug-ins, or a
  * latency-critical loop where an allocation's implicit device synchronisation is not
  * acceptable.  Such a caller passes only its inputs and outputs: the scratch (three per-pixel
- * maps) lives in a fixed device array inside the library, GS_SSIM2D_NOALLOC_MAX_PIXELS floats
- * x 3 (24 MiB), which every device that loads the library keeps until the process exits.
+ * maps and the status word) lives in a fixed device array inside the library,
+ * GS_SSIM2D_NOALLOC_MAX_PIXELS floats x 3 (24 MiB) plus 256 bytes, which every device that
+ * loads the library keeps until the process exits.
  *   - n_img * H * W above GS_SSIM2D_NOALLOC_MAX_PIXELS returns GS_ERR_CAPACITY (message in
  *     gs_last_error) before any launch.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,

@@ -851,6 +851,213 @@ __global__ void __launch_bounds__(kFThreads, 2)
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// SSIM 2D with TMA staging (image width a multiple of 4, 16-byte aligned buffers): one CTA
+// per 32 x 32 output tile of one image.  The halo boxes (48 x 42 elements, starting 8 columns
+// left of the tile so that every copy starts 16-byte aligned; zero fill outside the image)
+// arrive by TMA, so no thread spends instructions on staging.  A vertical pass (item: one
+// halo column and eight output rows, lanes over consecutive columns; 18 box rows serve the
+// eight outputs) filters the channels along y and stores one float4 per (output row, halo
+// column); a horizontal pass (item: four adjacent outputs of one row, lanes over rows, 14
+// float4 loads) filters along x.  Its results go through shared memory once more so that the
+// pixels are finished with eight consecutive lanes per 32-pixel row: every global load and
+// store of the outputs is then a whole 128-byte row segment.  Forward channels (x, y,
+// x^2 + y^2, x y) -> SSIM, the maps and the loss (plus the fused L1 sum); backward the maps
+// (m1, m2, m3) -> dL/dx.
+// ------------------------------------------------------------------------------------------
+constexpr int kTBoxX = 48;                // box columns: tile columns -8 .. 39
+constexpr int kTBox = kTBoxX * kIn2;      // elements per box (42 rows)
+constexpr int kTPitch = kIn2 + 1;         // float4 pitch of the y-filtered rows (odd: the
+                                          // horizontal pass's 8-lane phases hit distinct banks)
+constexpr int kXPitch = kT2 / kG + 1;     // float4 pitch of the exchanged rows (9)
+constexpr int kGV = 8;                    // output rows per vertical-pass item
+template <bool BWD>
+struct Tma2Shape {
+  // forward: X box, Y box; backward: the (m1, m2) pair box (two floats per pixel), m3 box
+  static constexpr uint32_t boxA = (BWD ? 2u : 1u) * kTBox * 4u;
+  static constexpr uint32_t boxB = kTBox * 4u;
+  static constexpr uint32_t txbytes = boxA + boxB;
+  static constexpr uint32_t offV = boxA + boxB;  // 16128 / 24192: multiples of 128
+  static constexpr size_t smem = 128 + offV + (size_t)kT2 * kTPitch * sizeof(float4);
+  static_assert(3 * kT2 * kXPitch <= kT2 * kTPitch, "the exchange fits in the filtered rows");
+};
+
+template <bool BWD>
+__global__ void __launch_bounds__(kSsimThreads, 4)
+    k_ssim2d_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ Win W, int nx, int ny, float C1, float C2,
+                 float gscale, float l1s, float* __restrict__ loss, float2* __restrict__ m12,
+                 float* __restrict__ m3, const float* __restrict__ X,
+                 const float* __restrict__ Y, float* __restrict__ grad, int accumulate,
+                 int* __restrict__ err) {
+  using S = Tma2Shape<BWD>;
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  // 128-byte aligned start, derived from the shared array itself (shared-space addressing)
+  unsigned char* base = dyn_raw + ((128u - (smem_u32(dyn_raw) & 127u)) & 127u);
+  const float* sA = reinterpret_cast<const float*>(base);
+  const float* sB = reinterpret_cast<const float*>(base + S::boxA);
+  float4* V = reinterpret_cast<float4*>(base + S::offV);
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kT2, y0 = blockIdx.y * kT2, img = blockIdx.z;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, S::txbytes);
+    tma_load_3d(&tmA, &bar, base, (BWD ? 2 : 1) * (x0 - 8), y0 - kR, img);
+    tma_load_3d(&tmB, &bar, base + S::boxA, x0 - 8, y0 - kR, img);
+  }
+  // the pixels a thread finishes: row cr, columns 4 cq .. 4 cq + 3 (eight lanes per row)
+  const int cq = tid & 7, cr = tid >> 3;
+  const int y = y0 + cr, xb = x0 + 4 * cq;
+  const bool own = y < ny && xb < nx;  // nx % 4 == 0: the four columns are all inside or out
+  const size_t o = ((size_t)img * ny + y) * nx + xb;
+  // backward: the pixels' x, y (and the gradient to add to) are requested now, so that their
+  // latency overlaps the copies and the filter passes
+  float4 xo = make_float4(0.f, 0.f, 0.f, 0.f), yo = xo, go = xo;
+  if (BWD && own) {
+    xo = *reinterpret_cast<const float4*>(X + o);
+    yo = *reinterpret_cast<const float4*>(Y + o);
+    if (accumulate) go = *reinterpret_cast<const float4*>(grad + o);
+  }
+  __syncthreads();  // the barrier is initialised before anyone waits on it
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    // a copy never arrived: report it and poison the result instead of using the boxes
+    if (tid == 0) {
+      atomicExch(err, GS_ERR_TIMEOUT);
+      if (!BWD && loss) atomicExch(loss, __int_as_float(0x7fc00000));
+      mbar_wait(&bar, 0);  // bounded: the copies in flight before shared memory goes away
+    }
+    if (BWD && own) {
+      const float nan = __int_as_float(0x7fc00000);
+      *reinterpret_cast<float4*>(grad + o) = make_float4(nan, nan, nan, nan);
+    }
+    return;
+  }
+  float2 w2[2 * kR + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * kR; ++k) w2[k] = make_float2(W.w[k], W.w[k]);
+  // ---- vertical pass: item (halo column c, output rows 8g .. 8g + 7); box rows 8g .. 8g + 17
+  // at box column c + 3 (image column x0 - 5 + c); 168 items, one round
+  for (int p = tid; p < kIn2 * (kT2 / kGV); p += kSsimThreads) {
+    const int c = p % kIn2, g = p / kIn2;
+    float2 a[kGV][2];
+#pragma unroll
+    for (int j = 0; j < kGV; ++j) a[j][0] = a[j][1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kGV + 2 * kR; ++i) {
+      const int e = (kGV * g + i) * kTBoxX + c + 3;
+      float2 u0, u1;
+      if constexpr (!BWD) {
+        const float xv = sA[e], yv = sB[e];
+        u0 = make_float2(xv, yv);
+        // second moments as (x^2 + y^2, x y): SSIM needs sigma_x^2 + sigma_y^2 only
+        u1 = make_float2(fmaf(xv, xv, yv * yv), xv * yv);
+      } else {
+        u0 = reinterpret_cast<const float2*>(sA)[e];
+        u1 = make_float2(sB[e], 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < kGV; ++j) {
+        const int k = i - j;
+        if (k < 0 || k > 2 * kR) continue;
+        a[j][0] = __ffma2_rn(w2[k], u0, a[j][0]);
+        if constexpr (!BWD) a[j][1] = __ffma2_rn(w2[k], u1, a[j][1]);
+        else a[j][1].x = fmaf(w2[k].x, u1.x, a[j][1].x);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kGV; ++j)
+      V[(kGV * g + j) * kTPitch + c] = make_float4(a[j][0].x, a[j][0].y, a[j][1].x, a[j][1].y);
+  }
+  __syncthreads();
+  // ---- horizontal pass: row r, outputs 4q .. 4q + 3 from halo columns 4q .. 4q + 13
+  const int r = tid & 31, q = tid >> 5;
+  float2 f[kG][2];
+#pragma unroll
+  for (int j = 0; j < kG; ++j) f[j][0] = f[j][1] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < kG + 2 * kR; ++i) {
+    const float4 v = V[r * kTPitch + 4 * q + i];
+    const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int k = i - j;
+      if (k < 0 || k > 2 * kR) continue;
+      f[j][0] = __ffma2_rn(w2[k], v0, f[j][0]);
+      if constexpr (!BWD) f[j][1] = __ffma2_rn(w2[k], v1, f[j][1]);
+      else f[j][1].x = fmaf(w2[k].x, v1.x, f[j][1].x);
+    }
+  }
+  // three float4 per thread to the finishing lanes: [channel][row][4-column group]
+  float4 t[3];
+  float contrib = 0.f;
+  if constexpr (BWD) {  // the filtered maps
+    t[0] = make_float4(f[0][0].x, f[1][0].x, f[2][0].x, f[3][0].x);
+    t[1] = make_float4(f[0][0].y, f[1][0].y, f[2][0].y, f[3][0].y);
+    t[2] = make_float4(f[0][1].x, f[1][1].x, f[2][1].x, f[3][1].x);
+  } else {  // SSIM and its maps (rows and columns past the image are never stored)
+    float mv[3][kG];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const float mx = f[j][0].x, my = f[j][0].y;
+      const float sxy = f[j][1].y - mx * my;
+      const float D = (f[j][1].x - mx * mx - my * my) + C2;  // sigma_x^2 + sigma_y^2 + C2
+      const float Am = 2.f * mx * my + C1, Bn = 2.f * sxy + C2;
+      const float C = mx * mx + my * my + C1;
+      const float inv = 1.f / (C * D);  // 1/C = D inv, 1/D = C inv
+      const float Sv = (Am * Bn) * inv;
+      const float dmu = (2.f * my * Bn) * inv - Sv * (2.f * mx) * (D * inv);
+      const float dsxx = -Sv * (C * inv);
+      const float dsxy = 2.f * Am * inv;
+      mv[0][j] = gscale * (dmu - 2.f * mx * dsxx - my * dsxy);
+      mv[1][j] = gscale * dsxx;
+      mv[2][j] = gscale * dsxy;
+      if (y0 + r < ny && x0 + 4 * q + j < nx) contrib += 1.f - Sv;
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) t[m] = make_float4(mv[m][0], mv[m][1], mv[m][2], mv[m][3]);
+  }
+  __syncthreads();  // every thread is done with the filtered rows
+  float4* Xc = V;   // the exchange, pitch 9 float4: the 8-lane phases of both sides are
+                    // conflict-free
+#pragma unroll
+  for (int m = 0; m < 3; ++m) Xc[(m * kT2 + r) * kXPitch + q] = t[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 3; ++m) t[m] = Xc[(m * kT2 + cr) * kXPitch + cq];
+  if constexpr (BWD) {
+    if (!own) return;
+    const float xs[4] = {xo.x, xo.y, xo.z, xo.w}, ys[4] = {yo.x, yo.y, yo.z, yo.w};
+    const float gs[4] = {go.x, go.y, go.z, go.w};
+    const float a1[4] = {t[0].x, t[0].y, t[0].z, t[0].w}, a2[4] = {t[1].x, t[1].y, t[1].z, t[1].w};
+    const float a3[4] = {t[2].x, t[2].y, t[2].z, t[2].w};
+    float gv[4];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      float g = a1[j] + 2.f * xs[j] * a2[j] + ys[j] * a3[j];
+      if (l1s != 0.f) g = l1s * sgnf(xs[j] - ys[j]) + g;  // fused L1 term
+      gv[j] = accumulate ? gs[j] + g : g;
+    }
+    *reinterpret_cast<float4*>(grad + o) = make_float4(gv[0], gv[1], gv[2], gv[3]);
+  } else {
+    float l1 = 0.f;
+    if (own) {
+      float4* m12o = reinterpret_cast<float4*>(m12 + o);  // o % 4 == 0: 32-byte aligned
+      m12o[0] = make_float4(t[0].x, t[1].x, t[0].y, t[1].y);
+      m12o[1] = make_float4(t[0].z, t[1].z, t[0].w, t[1].w);
+      *reinterpret_cast<float4*>(m3 + o) = t[2];
+      if (l1s != 0.f) {  // the pixels' own x, y from the staged boxes (box row cr + 5)
+        const int e = (cr + kR) * kTBoxX + 4 * cq + 8;
+        const float4 xv = *reinterpret_cast<const float4*>(sA + e);
+        const float4 yv = *reinterpret_cast<const float4*>(sB + e);
+        l1 = fabsf(xv.x - yv.x) + fabsf(xv.y - yv.y) + fabsf(xv.z - yv.z) + fabsf(xv.w - yv.w);
+      }
+    }
+    if (loss) block_add(contrib * (-gscale) + l1 * l1s, loss);
+  }
+}
+
 // 3D tensor map over an nx x ny x nz volume of elem-byte elements (elem 4: FP32, 8: FP32
 // pairs), box bx x by x 1, zero fill outside
 int volume_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int elem, int bx,
@@ -870,7 +1077,7 @@ int volume_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int e
          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_last_error_msg("cuTensorMapEncodeTiled failed for a 3D SSIM volume");
+    set_last_error_msg("cuTensorMapEncodeTiled failed for an SSIM image or volume");
     return GS_ERR_CUDA;
   }
   return GS_OK;
@@ -1020,6 +1227,27 @@ int ssim2d(const float* d_x, const float* d_y, int H, int W, dim3 grid, float C1
            int accumulate, float l1s, cudaStream_t s) {
   const Win Wn = host_window();
   const dim3 block(kSsimThreads);
+  // TMA-staged kernels when the copies' alignment rules hold (16-byte aligned buffers and
+  // rows: W a multiple of 4) and the image is at least one box wide and high; the word after
+  // the three maps records a copy that never arrived
+  if (W % 4 == 0 && W >= kTBoxX && H >= kIn2 && al16(d_x) && al16(d_y) && al16(maps) &&
+      al16(d_grad)) {
+    const int n = (int)grid.z;
+    float2* m12 = reinterpret_cast<float2*>(maps);
+    float* m3 = maps + 2 * plane;  // plane % 4 == 0: 16-byte aligned
+    int* err = reinterpret_cast<int*>(maps + 3 * plane);
+    CUtensorMap tmX, tmY, tmP, tmS;
+    GS_TRY(volume_map(&tmX, d_x, W, H, n, 4, kTBoxX, kIn2));
+    GS_TRY(volume_map(&tmY, d_y, W, H, n, 4, kTBoxX, kIn2));
+    GS_TRY(volume_map(&tmP, maps, 2 * W, H, n, 4, 2 * kTBoxX, kIn2));
+    GS_TRY(volume_map(&tmS, m3, W, H, n, 4, kTBoxX, kIn2));
+    GS_TRY(launch("ssim2d_fwd", k_ssim2d_tma<false>, grid, block, Tma2Shape<false>::smem, s,
+                  tmX, tmY, Wn, W, H, C1, C2, gscale, l1s, d_loss, m12, m3,
+                  (const float*)nullptr, (const float*)nullptr, (float*)nullptr, 0, err));
+    return launch("ssim2d_bwd", k_ssim2d_tma<true>, grid, block, Tma2Shape<true>::smem, s, tmP,
+                  tmS, Wn, W, H, C1, C2, gscale, l1s, (float*)nullptr, m12, m3, d_x, d_y,
+                  d_grad, accumulate, err);
+  }
   GS_TRY(launch("ssim2d_fwd", k_ssim_xy<0>, grid, block, XyShape<0>::smem, s, Wn, d_x, d_y,
                 plane, W, H, C1, C2, gscale, d_loss, maps, (const float*)nullptr,
                 (const float*)nullptr, (float*)nullptr, 0, l1s));
@@ -1105,11 +1333,11 @@ int gs_ssim2d_loss(const float* d_x, const float* d_y, int n_img, int H, int W, 
 
 // ------------------------------------------------------------------------------------------
 // SSIM 2D with a fixed scratch buffer, for callers that cannot allocate device memory.
-// The three per-pixel derivative maps live in this file-scope device array instead of a
-// caller workspace.  Every device that loads the library holds it (24 MiB) until the process
+// The three per-pixel derivative maps (and the TMA kernels' status word after them) live in
+// this file-scope device array instead of a caller workspace.  Every device that loads the library holds it (24 MiB) until the process
 // exits.
 // ------------------------------------------------------------------------------------------
-static __device__ __align__(256) float g_ssim2d_scratch[3 * (size_t)GS_SSIM2D_NOALLOC_MAX_PIXELS];
+static __device__ __align__(256) float g_ssim2d_scratch[3 * (size_t)GS_SSIM2D_NOALLOC_MAX_PIXELS + 64];
 
 namespace {
 std::mutex g_scratch_mu;

@@ -82,7 +82,13 @@ def test_tv3d(B):
     np.testing.assert_allclose(g, gw, rtol=1e-5, atol=1e-9)
 
 
-@pytest.mark.parametrize("shape", [(3, 37, 53), (2, 64, 64), (1, 5, 7)])
+# (3, 37, 53) and (1, 5, 7) take the register-staged kernels (width not a multiple of 4, or
+# smaller than one box); the others the TMA-staged ones, (2, 45, 52) and (1, 70, 100) with
+# ragged tiles
+SSIM2D_SHAPES = [(3, 37, 53), (2, 64, 64), (1, 5, 7), (2, 45, 52), (1, 70, 100)]
+
+
+@pytest.mark.parametrize("shape", SSIM2D_SHAPES)
 def test_ssim2d(B, shape):
     rng = np.random.default_rng(2)
     y = _x32(rng.random(shape))
@@ -95,7 +101,7 @@ def test_ssim2d(B, shape):
     assert np.abs(g - gw).max() <= 1e-3 * scale, float(np.abs(g - gw).max() / scale)
 
 
-@pytest.mark.parametrize("shape", [(3, 37, 53), (2, 64, 64), (1, 5, 7)])
+@pytest.mark.parametrize("shape", SSIM2D_SHAPES)
 def test_l1_ssim2d_fused(B, shape):
     """L1 + D-SSIM in the two SSIM kernels equals the oracle's sum of both terms, and the
     separate L1 and SSIM calls, value and gradient; accumulate adds onto the gradient."""
@@ -116,6 +122,37 @@ def test_l1_ssim2d_fused(B, shape):
     np.testing.assert_allclose(g, g2, rtol=1e-5, atol=1e-6 * scale)
     va, ga = _run_loss(B, "l1ssim2d", x, y, L, 0.6, weight=0.25, accumulate_into=np.ones_like(x))
     np.testing.assert_allclose(ga, g + 1.0, rtol=1e-6, atol=1e-7)
+
+
+def test_ssim2d_tma_equals_register_staging(B):
+    """The TMA-staged 2D kernels equal the register-staged ones (taken when a buffer is not
+    16-byte aligned) on the same images: L1 + D-SSIM value and the gradient accumulated onto
+    a non-zero one."""
+    L_ = B.lib()
+    rng = np.random.default_rng(11)
+    n, H, W = 3, 75, 136
+    y = rng.random((n, H, W), dtype=np.float32)
+    x = np.clip(y + 0.1 * rng.standard_normal((n, H, W)).astype(np.float32), 0, None)
+    # a base of the gradient's own size, so that its rounding does not hide the comparison
+    base = (1e-5 * rng.standard_normal((n, H, W))).astype(np.float32)
+    out = []
+    for off in (0, 1):  # a one-float offset breaks the 16-byte alignment
+        bufs = [torch.zeros(n * H * W + 4, device="cuda") for _ in range(3)]
+        xd, yd, gd = (t[off:off + n * H * W] for t in bufs)
+        xd.copy_(torch.from_numpy(x.ravel()))
+        yd.copy_(torch.from_numpy(y.ravel()))
+        gd.copy_(torch.from_numpy(base.ravel()))
+        loss = torch.zeros(1, device="cuda")
+        ws = torch.empty(L_.gs_ssim_workspace_size(n * H * W), dtype=torch.uint8, device="cuda")
+        B.check(L_.gs_l1_ssim2d_loss(B.ptr(xd), B.ptr(yd), n, H, W, float(y.max()), 0.6, 0.25,
+                                     B.ptr(loss), B.ptr(gd), 1, B.ptr(ws), ws.numel(), _s()),
+                "gs_l1_ssim2d_loss")
+        torch.cuda.synchronize()
+        out.append((float(loss.item()), gd.cpu().numpy().astype(np.float64)))
+    (v0, g0), (v1, g1) = out
+    assert abs(v0 - v1) <= 1e-6 * abs(v1)
+    scale = np.abs(g1 - base.ravel()).max()
+    assert np.abs(g0 - g1).max() <= 1e-5 * scale
 
 
 @pytest.mark.parametrize("shape", [(21, 19, 35), (12, 16, 16), (4, 40, 33), (1, 9, 70)])
