@@ -883,7 +883,7 @@ struct Tma2Shape {
 };
 
 template <bool BWD>
-__global__ void __launch_bounds__(kSsimThreads, 4)
+__global__ void __launch_bounds__(kSsimThreads, BWD ? 4 : 5)
     k_ssim2d_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ Win W, int nx, int ny, float C1, float C2,
                  float gscale, float l1s, float* __restrict__ loss, float2* __restrict__ m12,
