@@ -5,9 +5,10 @@
 //   tv3d     anisotropic TV with forward differences / n_vox and its sub-gradient, one pass
 //   ssim2d   Wang et al. 2004 SSIM, 11x11 Gaussian window (sigma 1.5), zero-padded 'same'
 //            filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2; loss term weight * (1 - mean SSIM).
-//            Two tiled kernels with separable filtering in shared memory: (1) the five local
+//            Two tiled kernels with separable filtering in shared memory: (1) the local
 //            moments, SSIM and three per-pixel partial-derivative maps; (2) the same window
-//            applied to the three maps, combined into dL/dx.
+//            applied to the three maps, combined into dL/dx.  Tiles are staged by TMA where
+//            the copies' alignment rules hold, else through registers.
 //   ssim3d   the same with an 11^3 window over a volume (Eq. 6): each thread owns one z-row
 //            and walks it with a ring buffer of filtered xy-planes.
 //   adam     Adam on raw parameters (log-scale, softplus-density, raw quaternion) with the
