@@ -1,5 +1,5 @@
-"""Full-size parity on sampled outputs, in the launch configuration the benchmark times
-(tile 16, all 75 views): the rasterizer at 75 cone views of 512^2 (50k Gaussians), 1024^2
+"""Full-size parity on sampled outputs, in the launch configurations the benchmark times
+(all 75 views; tile 16, and tile 32 where the autotuner picks it): the rasterizer at 75 cone views of 512^2 (50k Gaussians), 1024^2
 (200k) and 2048^2 (500k), the voxelizer at 1024^3 (500k), each against the FP64 oracle
 evaluated output by output with the same per-output guard-band allowance as the small tests
 (1e-4 of the peak plus the contributions of pairs within the band of the cut or a box edge);
@@ -43,13 +43,18 @@ def _check(got, want, allow, min_nonzero=0.3):
     assert (err <= bound).all(), (float((err / bound).max()), int((err > bound).sum()))
 
 
-@pytest.mark.parametrize("side,n,median", [(512, 50000, 0.012), (1024, 200000, 0.008),
-                                           (2048, 500000, 0.006)])
-def test_raster_full_size_sampled(orc, gsct, side, n, median):
+# tile 16 at 512^2 (the reconstruction step's tile), 16 and 32 (the autotuner's pick for the
+# 1024^2 and 2048^2 steps) at the larger detectors
+@pytest.mark.parametrize("side,n,median,tile", [(512, 50000, 0.012, 16),
+                                                (1024, 200000, 0.008, 16),
+                                                (1024, 200000, 0.008, 32),
+                                                (2048, 500000, 0.006, 16),
+                                                (2048, 500000, 0.006, 32)])
+def test_raster_full_size_sampled(orc, gsct, side, n, median, tile):
     mr, sc, qt = synth.gaussians(40 + side, n, radius=0.8, scale_median=median,
                                  scale_sigma_log=0.4)
     views = synth.cone_views(75, side, side)
-    proj = gsct.Projector(views, side, side, tile=16)
+    proj = gsct.Projector(views, side, side, tile=tile)
     img = proj.forward(*to_dev(mr, sc, qt))
     assert proj.status().code == 0
     pix = synth.pixel_samples(side, 75, side, side, N_SAMPLES)
@@ -81,17 +86,20 @@ def test_voxelize_1024_sampled(orc, gsct):
     _check(got, want, allow, min_nonzero=0.15)
 
 
-@pytest.mark.parametrize("side,n,median", [(512, 50000, 0.012), (1024, 200000, 0.008)])
-def test_raster_gradients_full_size_sampled(orc, gsct, side, n, median):
+# the 1024^2 step also runs at tile 32 with its lists rebuilt in the backward
+@pytest.mark.parametrize("side,n,median,tile,reuse", [(512, 50000, 0.012, 16, True),
+                                                      (1024, 200000, 0.008, 16, True),
+                                                      (1024, 200000, 0.008, 32, False)])
+def test_raster_gradients_full_size_sampled(orc, gsct, side, n, median, tile, reuse):
     mr, sc, qt = synth.gaussians(60 + side, n, radius=0.8, scale_median=median,
                                  scale_sigma_log=0.4)
     views = synth.cone_views(75, side, side)
     rng = np.random.default_rng(side)
     w = rng.standard_normal((75, side, side), dtype=np.float32)
-    proj = gsct.Projector(views, side, side, tile=16)
+    proj = gsct.Projector(views, side, side, tile=tile)
     d = to_dev(mr, sc, qt)
     proj.forward(*d)
-    got = grads11(*proj.backward(*d, torch.from_numpy(w).cuda(), reuse=True))
+    got = grads11(*proj.backward(*d, torch.from_numpy(w).cuda(), reuse=reuse))
     assert proj.status().code == 0
     del proj
     torch.cuda.empty_cache()

@@ -84,8 +84,8 @@ def test_tv3d(B):
 
 # (3, 37, 53) and (1, 5, 7) take the register-staged kernels (width not a multiple of 4, or
 # smaller than one box); the others the TMA-staged ones, (2, 45, 52) and (1, 70, 100) with
-# ragged tiles
-SSIM2D_SHAPES = [(3, 37, 53), (2, 64, 64), (1, 5, 7), (2, 45, 52), (1, 70, 100)]
+# ragged tiles, (2, 512, 512) at the reconstruction step's detector size
+SSIM2D_SHAPES = [(3, 37, 53), (2, 64, 64), (1, 5, 7), (2, 45, 52), (1, 70, 100), (2, 512, 512)]
 
 
 @pytest.mark.parametrize("shape", SSIM2D_SHAPES)
