@@ -5,7 +5,8 @@ evaluated output by output with the same per-output guard-band allowance as the 
 (1e-4 of the peak plus the contributions of pairs within the band of the cut or a box edge);
 and the per-Gaussian gradient of sampled Gaussians at 512^2 and 1024^2 against the oracle's
 dual-number gradient (a Gaussian's gradient needs only its own footprint, so the oracle runs
-on the sampled Gaussians alone against the full dL/dI)."""
+on the sampled Gaussians alone against the full dL/dI); the fused 3D SSIM's gradient at
+sampled voxels of a 1024^3 volume against the oracle on a crop around each."""
 import numpy as np
 import pytest
 import torch
@@ -186,3 +187,49 @@ def test_kernel_sweep_largest_points_sampled(orc, gsct):
     g = got[sel].copy()
     g[:, 6:10] = 0.0
     assert_grads_close(g, want, np.ones(len(sel), dtype=bool))
+
+
+def test_ssim3d_1024_sampled_gradient(gsct):
+    """The fused streaming 3D SSIM in the launch configuration of the 1024^3 volume fit: its
+    gradient at sampled interior voxels against the oracle's SSIM on the 21^3 crop around each
+    voxel (every voxel whose SSIM window holds the sampled one has its own window inside the
+    crop, so the crop's gradient there is the full volume's times the voxel-count ratio); and
+    the value at y = x, where every SSIM term is 1."""
+    from oracle import losses as OL
+    from paper_2604_01844_gb300 import binding as B
+
+    n, weight = 1024, 0.25
+    rng = np.random.default_rng(31)
+    y = rng.random((n, n, n), dtype=np.float32)
+    x = np.clip(y + 0.1 * rng.standard_normal((n, n, n), dtype=np.float32), 0, None)
+    L = float(y.max())
+    L_ = B.lib()
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = torch.empty(L_.gs_ssim3d_workspace_size(n ** 3), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(xd)
+    s = torch.cuda.current_stream().cuda_stream
+    B.check(L_.gs_ssim3d_loss(B.ptr(xd), B.ptr(yd), n, n, n, L, weight, B.ptr(loss), B.ptr(grad),
+                              0, B.ptr(ws), ws.numel(), s), "gs_ssim3d_loss")
+    same = torch.zeros(1, device="cuda")
+    B.check(L_.gs_ssim3d_loss(B.ptr(xd), B.ptr(xd), n, n, n, L, weight, B.ptr(same), None, 0,
+                              B.ptr(ws), ws.numel(), s), "gs_ssim3d_loss")
+    torch.cuda.synchronize()
+    assert abs(float(same.item())) <= 1e-5 * weight
+    pts = rng.integers(10, n - 10, size=(16, 3))
+    got = grad[torch.from_numpy(pts[:, 0]).cuda(), torch.from_numpy(pts[:, 1]).cuda(),
+               torch.from_numpy(pts[:, 2]).cuda()].cpu().numpy().astype(np.float64)
+    del xd, yd, ws, grad
+    torch.cuda.empty_cache()
+    want = np.empty(len(pts))
+    ratio = 21.0 ** 3 / float(n) ** 3
+    for k, (z, yy, xx) in enumerate(pts):
+        cx = x[z - 10:z + 11, yy - 10:yy + 11, xx - 10:xx + 11].astype(np.float64)
+        cy = y[z - 10:z + 11, yy - 10:yy + 11, xx - 10:xx + 11].astype(np.float64)
+        _, g = OL.value_and_grad(lambda a, b: -weight * ratio * OL.ssim3d(a, b, L), cx, cy)
+        want[k] = g[10, 10, 10]
+    scale = np.abs(want).max()
+    assert scale > 0
+    assert np.abs(got - want).max() <= 1e-3 * scale, float(np.abs(got - want).max() / scale)
+    big = np.abs(want) > 0.1 * scale
+    assert (np.abs(got - want)[big] <= 1e-2 * np.abs(want[big])).all()
