@@ -6,7 +6,8 @@ evaluated output by output with the same per-output guard-band allowance as the 
 and the per-Gaussian gradient of sampled Gaussians at 512^2 and 1024^2 against the oracle's
 dual-number gradient (a Gaussian's gradient needs only its own footprint, so the oracle runs
 on the sampled Gaussians alone against the full dL/dI); the fused 3D SSIM's gradient at
-sampled voxels of a 1024^3 volume against the oracle on a crop around each."""
+sampled voxels of a 1024^3 volume, and the step's L1 + D-SSIM gradient at sampled pixels of 75
+views of 512^2, against the oracle on a crop around each."""
 import numpy as np
 import pytest
 import torch
@@ -228,6 +229,46 @@ def test_ssim3d_1024_sampled_gradient(gsct):
         cy = y[z - 10:z + 11, yy - 10:yy + 11, xx - 10:xx + 11].astype(np.float64)
         _, g = OL.value_and_grad(lambda a, b: -weight * ratio * OL.ssim3d(a, b, L), cx, cy)
         want[k] = g[10, 10, 10]
+    scale = np.abs(want).max()
+    assert scale > 0
+    assert np.abs(got - want).max() <= 1e-3 * scale, float(np.abs(got - want).max() / scale)
+    big = np.abs(want) > 0.1 * scale
+    assert (np.abs(got - want)[big] <= 1e-2 * np.abs(want[big])).all()
+
+
+def test_l1_ssim2d_75x512_sampled_gradient(gsct):
+    """The reconstruction step's image loss (L1 + D-SSIM over 75 views of 512^2, TMA-staged
+    kernels): the gradient at sampled interior pixels against the oracle's SSIM on the 21^2
+    crop around each (scaled by the pixel-count ratio) plus the L1 term's sign gradient."""
+    from oracle import losses as OL
+    from paper_2604_01844_gb300 import binding as B
+
+    nv, n, l1w, sw = 75, 512, 0.8, 0.2
+    rng = np.random.default_rng(41)
+    y = rng.random((nv, n, n), dtype=np.float32)
+    x = np.clip(y + 0.1 * rng.standard_normal((nv, n, n), dtype=np.float32), 0, None)
+    L = float(y.max())
+    L_ = B.lib()
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ws = torch.empty(L_.gs_ssim_workspace_size(x.size), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(xd)
+    B.check(L_.gs_l1_ssim2d_loss(B.ptr(xd), B.ptr(yd), nv, n, n, L, l1w, sw, B.ptr(loss),
+                                 B.ptr(grad), 0, B.ptr(ws), ws.numel(),
+                                 torch.cuda.current_stream().cuda_stream), "gs_l1_ssim2d_loss")
+    torch.cuda.synchronize()
+    pts = np.stack([rng.integers(0, nv, 64), rng.integers(10, n - 10, 64),
+                    rng.integers(10, n - 10, 64)], axis=1)
+    got = grad[torch.from_numpy(pts[:, 0]).cuda(), torch.from_numpy(pts[:, 1]).cuda(),
+               torch.from_numpy(pts[:, 2]).cuda()].cpu().numpy().astype(np.float64)
+    N = float(x.size)
+    want = np.empty(len(pts))
+    for k, (v, yy, xx) in enumerate(pts):
+        cx = x[v:v + 1, yy - 10:yy + 11, xx - 10:xx + 11].astype(np.float64)
+        cy = y[v:v + 1, yy - 10:yy + 11, xx - 10:xx + 11].astype(np.float64)
+        _, g = OL.value_and_grad(lambda a, b: -sw * (21.0 ** 2 / n ** 2 / nv) * OL.ssim2d(a, b, L),
+                                 cx, cy)
+        want[k] = g[0, 10, 10] + l1w * np.sign(float(x[v, yy, xx]) - float(y[v, yy, xx])) / N
     scale = np.abs(want).max()
     assert scale > 0
     assert np.abs(got - want).max() <= 1e-3 * scale, float(np.abs(got - want).max() / scale)
