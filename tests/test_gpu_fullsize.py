@@ -274,3 +274,33 @@ def test_l1_ssim2d_75x512_sampled_gradient(gsct):
     assert np.abs(got - want).max() <= 1e-3 * scale, float(np.abs(got - want).max() / scale)
     big = np.abs(want) > 0.1 * scale
     assert (np.abs(got - want)[big] <= 1e-2 * np.abs(want[big])).all()
+
+
+def test_tv3d_512_value_and_sampled_gradient(gsct):
+    """TV on the 512^3 volume of the 1024^2 step: the value against the oracle's FP64 sum, the
+    sub-gradient at sampled interior voxels against the oracle on the 3^3 crop around each
+    (every difference that involves the voxel lies inside it)."""
+    from oracle import losses as OL
+    from paper_2604_01844_gb300 import binding as B
+
+    n, weight = 512, 0.05
+    rng = np.random.default_rng(51)
+    v = rng.random((n, n, n), dtype=np.float32)
+    vd = torch.from_numpy(v).cuda()
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(vd)
+    B.check(B.lib().gs_tv3d_loss(B.ptr(vd), n, n, n, weight, B.ptr(loss), B.ptr(grad), 0,
+                                 torch.cuda.current_stream().cuda_stream), "gs_tv3d_loss")
+    torch.cuda.synchronize()
+    want_v = weight * float(OL.tv3d(torch.from_numpy(v.astype(np.float64))))
+    # FP32 partial sums of about a thousand differences per thread, then block sums and atomics
+    assert abs(float(loss.item()) - want_v) <= 1e-4 * abs(want_v)
+    pts = rng.integers(1, n - 1, size=(64, 3))
+    got = grad[torch.from_numpy(pts[:, 0]).cuda(), torch.from_numpy(pts[:, 1]).cuda(),
+               torch.from_numpy(pts[:, 2]).cuda()].cpu().numpy().astype(np.float64)
+    want = np.empty(len(pts))
+    for k, (z, y, x) in enumerate(pts):
+        c = v[z - 1:z + 2, y - 1:y + 2, x - 1:x + 2].astype(np.float64)
+        _, g = OL.value_and_grad(lambda a: weight * (27.0 / n ** 3) * OL.tv3d(a), c)
+        want[k] = g[1, 1, 1]
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * np.abs(want).max())
