@@ -5,9 +5,11 @@ evaluated output by output with the same per-output guard-band allowance as the 
 (1e-4 of the peak plus the contributions of pairs within the band of the cut or a box edge);
 and the per-Gaussian gradient of sampled Gaussians at 512^2 and 1024^2 against the oracle's
 dual-number gradient (a Gaussian's gradient needs only its own footprint, so the oracle runs
-on the sampled Gaussians alone against the full dL/dI); the fused 3D SSIM's gradient at
-sampled voxels of a 1024^3 volume, and the step's L1 + D-SSIM gradient at sampled pixels of 75
-views of 512^2, against the oracle on a crop around each."""
+on the sampled Gaussians alone against the full dL/dI); the voxelizer's
+per-Gaussian gradient at 1024^3 (the oracle on a region holding each sampled Gaussian's box);
+the fused 3D SSIM's gradient at sampled voxels of a 1024^3 volume, the step's L1 + D-SSIM
+gradient at sampled pixels of 75 views of 512^2 and TV at 512^3, against the oracle on a crop
+around each."""
 import numpy as np
 import pytest
 import torch
@@ -304,3 +306,38 @@ def test_tv3d_512_value_and_sampled_gradient(gsct):
         _, g = OL.value_and_grad(lambda a: weight * (27.0 / n ** 3) * OL.tv3d(a), c)
         want[k] = g[1, 1, 1]
     np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * np.abs(want).max())
+
+
+def test_voxelize_backward_1024_sampled(orc, gsct):
+    """The voxelizer backward in the 1024^3 volume fit's configuration (500k Gaussians, 16-voxel
+    bricks, the forward's lists reused): the (N, 11) gradient of 100 sampled Gaussians outside
+    the guard band against the oracle's, each computed on a region of interest that holds the
+    Gaussian's whole 3-sigma box (so that it sees exactly the dL/dV the full volume gives it)."""
+    n, side = 500000, 1024
+    mr, sc, qt = synth.gaussians(77, n, scale_median=0.004, scale_sigma_log=0.4)
+    grid = synth.cube_grid(side)
+    rng = np.random.default_rng(61)
+    w = rng.standard_normal((side, side, side), dtype=np.float32)
+    vox = gsct.Voxelizer(grid)
+    d = to_dev(mr, sc, qt)
+    vox.forward(*d)
+    got = grads11(*vox.backward(*d, torch.from_numpy(w).cuda(), reuse=True))
+    assert vox.status().code == 0
+    del vox
+    torch.cuda.empty_cache()
+    P = orc.params64(mr, sc, qt)
+    cand = np.sort(rng.choice(n, 400, replace=False))
+    flags = orc.voxel_flags(P[cand], grid, (0, 0, 0), (side, side, side), REL_BAND, IDX_BAND)
+    sel = cand[flags == 0][:100]
+    assert len(sel) == 100
+    o, h = float(np.ravel(grid["origin"])[0]), float(np.ravel(grid["voxel"])[0])
+    want = np.empty((len(sel), 11))
+    for k, i in enumerate(sel):
+        r = 3.05 * float(sc[i, :3].max())  # the 3-sigma ellipsoid lies in this ball
+        lo = np.clip(np.floor((mr[i, :3] - r - o) / h - 1.0).astype(int), 0, side)
+        hi = np.clip(np.ceil((mr[i, :3] + r - o) / h + 1.0).astype(int), 0, side)
+        dim = hi - lo
+        crop = w[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        want[k] = orc.voxelize_grad(P[i:i + 1], grid, crop, roi_lo=tuple(int(a) for a in lo),
+                                    roi_dim=tuple(int(a) for a in dim))[0]
+    assert_grads_close(got[sel], want, np.ones(len(sel), dtype=bool))
