@@ -49,6 +49,30 @@ def test_gemm_matches_float64(B, M, N, K, relu):
     assert torch.allclose(c16.cpu().double(), got, rtol=1e-2, atol=1e-2)
 
 
+@pytest.mark.parametrize("M,N,K", [(118016, 256, 4096), (256, 4096, 118016)])
+def test_gemm_mlp_full_shapes_sampled(B, M, N, K):
+    """The benchmark's largest layer shapes (the first layer's forward over 118,016 bricks and
+    its weight gradient with K = 118,016), 512 sampled outputs against float64 dot products of
+    the same bf16-rounded rows."""
+    rng = np.random.default_rng(M + 7 * N)
+    a = _bf16(rng.standard_normal((M, K), dtype=np.float32))
+    b = _bf16(rng.standard_normal((N, K), dtype=np.float32))
+    da, db = a.cuda(), b.cuda()
+    c32 = torch.empty((M, N), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.check(B.lib().gs_gemm_bf16(B.ptr(da), B.ptr(db), M, N, K, None, 0, B.ptr(c32), None, N,
+                                 B.ptr(err), torch.cuda.current_stream().cuda_stream), "gemm")
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    i = rng.integers(0, M, 512)
+    j = rng.integers(0, N, 512)
+    got = c32[torch.from_numpy(i).cuda(), torch.from_numpy(j).cuda()].cpu().double()
+    ra, rb = a[torch.from_numpy(i)].double(), b[torch.from_numpy(j)].double()
+    want = (ra * rb).sum(dim=1)
+    bound = 2e-6 * K ** 0.5 * (ra.abs() * rb.abs()).sum(dim=1) + 1e-6
+    assert bool(((got - want).abs() <= bound).all()), float((got - want).abs().max())
+
+
 def test_gemm_rejects_bad_shapes(B):
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     x = torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda")
