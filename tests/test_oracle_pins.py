@@ -701,6 +701,59 @@ def test_tv_ramp_and_psnr():
     assert abs(losses.psnr(est, gt) - 10 * math.log10(4 / (0.01 / 10))) < 1e-12
 
 
+def test_loss_gradients_are_local_to_the_window():
+    """The locality the full-size loss checks rest on: a point's gradient of the whole SSIM
+    (2D over several images, 3D) equals the gradient of the SSIM of the crop of half-width
+    2 r (r = 5, the window radius) around it, scaled by the element-count ratio, and TV's the
+    gradient on the 3^3 crop; points away from the borders."""
+    from oracle import losses as OL
+
+    rng = np.random.default_rng(7)
+    y3 = rng.random((26, 27, 28))
+    x3 = np.clip(y3 + 0.1 * rng.standard_normal(y3.shape), 0, None)
+    L = float(y3.max())
+    _, g = OL.value_and_grad(lambda a, b: OL.ssim3d(a, b, L), x3, y3)
+    for (z, y, x) in [(10, 11, 17), (13, 16, 12)]:
+        cx, cy = (t[z - 10:z + 11, y - 10:y + 11, x - 10:x + 11] for t in (x3, y3))
+        _, gc = OL.value_and_grad(lambda a, b: (21.0 ** 3 / x3.size) * OL.ssim3d(a, b, L), cx, cy)
+        assert abs(gc[10, 10, 10] - g[z, y, x]) <= 1e-12 * abs(g[z, y, x])
+    y2 = rng.random((3, 33, 35))
+    x2 = np.clip(y2 + 0.1 * rng.standard_normal(y2.shape), 0, None)
+    _, g = OL.value_and_grad(lambda a, b: OL.ssim2d(a, b, L), x2, y2)
+    for (v, y, x) in [(0, 12, 20), (2, 22, 10)]:
+        cx, cy = (t[v:v + 1, y - 10:y + 11, x - 10:x + 11] for t in (x2, y2))
+        _, gc = OL.value_and_grad(lambda a, b: (21.0 ** 2 / x2.size) * OL.ssim2d(a, b, L), cx, cy)
+        assert abs(gc[0, 10, 10] - g[v, y, x]) <= 1e-12 * abs(g[v, y, x])
+    # a smaller crop misses windows: the identity needs the full 2 r half-width
+    cx, cy = (t[0:1, 3:20, 11:28] for t in (x2, y2))
+    _, gc = OL.value_and_grad(lambda a, b: (17.0 ** 2 / x2.size) * OL.ssim2d(a, b, L), cx, cy)
+    assert abs(gc[0, 8, 8] - g[0, 11, 19]) > 1e-6 * abs(g[0, 11, 19])
+    v3 = rng.random((9, 10, 11))
+    _, g = OL.value_and_grad(lambda a: OL.tv3d(a), v3)
+    _, gc = OL.value_and_grad(lambda a: (27.0 / v3.size) * OL.tv3d(a), v3[3:6, 4:7, 5:8])
+    assert abs(gc[1, 1, 1] - g[4, 5, 6]) <= 1e-12 * abs(g[4, 5, 6])
+
+
+def test_voxelize_grad_region_of_interest_holding_the_box(orc):
+    """The voxelizer gradient of one Gaussian on a region of interest that holds its 3-sigma
+    box (the full-size backward check's construction) equals its gradient on the whole grid."""
+    mr, sc, qt = synth.gaussians(77, 30, scale_median=0.04, scale_sigma_log=0.4)
+    side = 48
+    grid = synth.cube_grid(side)
+    w = np.random.default_rng(1).standard_normal((side,) * 3)
+    P = orc.params64(mr, sc, qt)
+    full = orc.voxelize_grad(P, grid, w)
+    o, h = float(np.ravel(grid["origin"])[0]), float(np.ravel(grid["voxel"])[0])
+    for i in range(30):
+        r = 3.05 * float(sc[i, :3].max())
+        lo = np.clip(np.floor((mr[i, :3] - r - o) / h - 1.0).astype(int), 0, side)
+        hi = np.clip(np.ceil((mr[i, :3] + r - o) / h + 1.0).astype(int), 0, side)
+        crop = w[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        g = orc.voxelize_grad(P[i:i + 1], grid, crop, roi_lo=tuple(int(a) for a in lo),
+                              roi_dim=tuple(int(a) for a in hi - lo))[0]
+        assert np.array_equal(g, full[i])
+
+
 def test_adam_reference_special_cases():
     """With beta1 = beta2 = 0 and no bias correction left, Adam moves every raw parameter by
     lr * g / (|g| + eps); the activations are softplus/exp as stated (against numpy's
